@@ -1,0 +1,275 @@
+"""Pins for the CPU oracle against things other than itself.
+
+Each test checks the oracle against a library routine, a closed form, an
+invariant stated by the paper, or a brute-force dense computation, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.transform import Rotation
+
+import oracle
+from scenes import make_scene
+
+
+def _rand_cam(rng, big_rotation=True):
+    w = rng.normal(0, 1.0 if big_rotation else 1e-3, 3)
+    t = rng.normal(0, 0.3, 3) + np.array([0.0, 0.0, -6.0])
+    return np.concatenate([w, t, [rng.uniform(500, 1500), rng.normal(0, 0.05), rng.normal(0, 0.05)]])
+
+
+def _rand_point_in_front(rng, cam):
+    # pick a camera-frame point with negative depth and map it back to the world
+    R = Rotation.from_rotvec(cam[:3]).as_matrix()
+    Pc = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(-8, -4)])
+    return R.T @ (Pc - cam[3:6])
+
+
+def _bal_pixel_scipy(cam, X):
+    """BAL projection with the rotation from scipy (library routine)."""
+    P = Rotation.from_rotvec(cam[:3]).apply(X) + cam[3:6]
+    p = -P[:2] / P[2]
+    r2 = p @ p
+    return cam[6] * (1 + cam[7] * r2 + cam[8] * r2 * r2) * p
+
+
+def _bal_pixel_torch(theta, X):
+    """Differentiable BAL projection through torch.linalg.matrix_exp (no Rodrigues)."""
+    w, t, f, k1, k2 = theta[0:3], theta[3:6], theta[6], theta[7], theta[8]
+    zero = torch.zeros((), dtype=theta.dtype)
+    K = torch.stack([torch.stack([zero, -w[2], w[1]]), torch.stack([w[2], zero, -w[0]]),
+                     torch.stack([-w[1], w[0], zero])])
+    R = torch.linalg.matrix_exp(K)
+    P = R @ X + t
+    p = -P[:2] / P[2]
+    r2 = (p * p).sum()
+    return f * (1 + k1 * r2 + k2 * r2 * r2) * p
+
+
+@pytest.mark.parametrize("big", [True, False])
+def test_projection_matches_library_rotation(big):
+    rng = np.random.default_rng(10 + big)
+    for _ in range(50):
+        cam = _rand_cam(rng, big)
+        X = _rand_point_in_front(rng, cam)
+        np.testing.assert_allclose(oracle.project(cam, X), _bal_pixel_scipy(cam, X), rtol=1e-12, atol=1e-9)
+
+
+def test_first_order_branch_and_pinhole_special_case():
+    rng = np.random.default_rng(3)
+    # w = 0 exactly takes the first-order branch; with k1 = k2 = 0 it is the
+    # textbook pinhole -f P_xy / P_z with P = X + t.
+    cam = np.array([0, 0, 0, 0.1, -0.2, -5.0, 800.0, 0.0, 0.0])
+    X = rng.normal(0, 0.5, 3)
+    P = X + cam[3:6]
+    np.testing.assert_allclose(oracle.project(cam, X), -800.0 * P[:2] / P[2], rtol=1e-14)
+    # tiny rotation (theta^2 < DBL_EPSILON) agrees with the library rotation to first order
+    cam2 = cam.copy()
+    cam2[:3] = [1e-9, -2e-9, 5e-10]
+    np.testing.assert_allclose(oracle.project(cam2, X), _bal_pixel_scipy(cam2, X), rtol=1e-12)
+
+
+def test_jacobian_central_differences():
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        cam = _rand_cam(rng)
+        X = _rand_point_in_front(rng, cam)
+        u = oracle.project(cam, X) + rng.normal(0, 1, 2)
+        e, Jc, Jp = oracle.residual_jacobian(cam, X, u)
+        np.testing.assert_allclose(e, oracle.project(cam, X) - u, rtol=1e-13, atol=1e-10)
+        theta = np.concatenate([cam, X])
+        J = np.concatenate([Jc, Jp], axis=1)
+        for a in range(12):
+            h = 1e-6 * max(1.0, abs(theta[a]))
+            tp, tm = theta.copy(), theta.copy()
+            tp[a] += h
+            tm[a] -= h
+            fd = (_bal_pixel_scipy(tp[:9], tp[9:]) - _bal_pixel_scipy(tm[:9], tm[9:])) / (2 * h)
+            scale = max(1.0, np.abs(J[:, a]).max())
+            np.testing.assert_allclose(J[:, a], fd, atol=2e-6 * scale, rtol=1e-6)
+
+
+@pytest.mark.parametrize("big", [True, False])
+def test_jacobian_matches_autodiff_of_matrix_exponential(big):
+    rng = np.random.default_rng(5 + big)
+    for _ in range(20):
+        cam = _rand_cam(rng, big)
+        X = _rand_point_in_front(rng, cam)
+        u = rng.normal(0, 100, 2)
+        _, Jc, Jp = oracle.residual_jacobian(cam, X, u)
+        tc = torch.tensor(cam, dtype=torch.float64)
+        tX = torch.tensor(X, dtype=torch.float64)
+        Jc_ad = torch.func.jacfwd(lambda th: _bal_pixel_torch(th, tX))(tc).numpy()
+        Jp_ad = torch.func.jacfwd(lambda x: _bal_pixel_torch(tc, x))(tX).numpy()
+        np.testing.assert_allclose(Jc, Jc_ad, rtol=1e-9, atol=1e-9 * np.abs(Jc_ad).max())
+        np.testing.assert_allclose(Jp, Jp_ad, rtol=1e-9, atol=1e-9 * np.abs(Jp_ad).max())
+
+
+def test_huber_loss_properties():
+    delta = 2.0
+    for s in [0.0, 0.5, 3.99, 4.0, 4.01, 100.0]:
+        rho, w = oracle.loss("huber", delta, s)
+        r_plain, w_plain = oracle.loss("none", delta, s)
+        assert (r_plain, w_plain) == (s, 1.0)
+        if s <= delta ** 2:
+            assert (rho, w) == (s, 1.0)
+        else:
+            # closed form and derivative rho'(s) = delta / sqrt(s) by central difference
+            assert rho == pytest.approx(2 * delta * math.sqrt(s) - delta ** 2, rel=1e-15)
+            h = 1e-6 * s
+            d = (oracle.loss("huber", delta, s + h)[0] - oracle.loss("huber", delta, s - h)[0]) / (2 * h)
+            assert w == pytest.approx(d, rel=1e-7)
+    # continuity at s = delta^2
+    assert oracle.loss("huber", delta, 4.0 + 1e-12)[0] == pytest.approx(4.0, abs=1e-11)
+    # a huge delta reduces Huber to the plain loss on a whole scene
+    sc = make_scene(4, 30, sigma=1.0, seed=7)
+    c1 = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, "huber", 1e9)[0]
+    c0 = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, "none")[0]
+    assert c1 == c0
+
+
+def test_stable_sort_matches_numpy():
+    rng = np.random.default_rng(6)
+    keys = rng.integers(0, 37, size=2000).astype(np.int32)
+    perm, ptr = oracle.stable_sort(keys, 40)
+    np.testing.assert_array_equal(perm, np.argsort(keys, kind="stable"))
+    np.testing.assert_array_equal(ptr, np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=40))]))
+
+
+def _dense_system(sc, loss="none", delta=0.0):
+    """Dense J (2n x (9nc+3np)), W per residual row and e, from per-observation oracle terms."""
+    cost, e, Jc, Jp, W = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, loss, delta)
+    n, nc, np_ = sc.n, sc.nc, sc.np_
+    J = np.zeros((2 * n, 9 * nc + 3 * np_))
+    for k in range(n):
+        i, j = sc.cam_idx[k], sc.pt_idx[k]
+        J[2 * k:2 * k + 2, 9 * i:9 * i + 9] = Jc[k]
+        J[2 * k:2 * k + 2, 9 * nc + 3 * j:9 * nc + 3 * j + 3] = Jp[k]
+    Wr = np.repeat(W, 2)
+    return J, Wr, e.reshape(-1), cost
+
+
+@pytest.mark.parametrize("loss", ["none", "huber"])
+def test_blocks_equal_dense_normal_equations(loss):
+    sc = make_scene(3, 10, sigma=3.0, seed=8, outlier_frac=0.2)
+    J, Wr, e, _ = _dense_system(sc, loss, 2.0)
+    H = J.T @ (Wr[:, None] * J)
+    g = -J.T @ (Wr * e)
+    Hpp, v, Hll, w, E = oracle.blocks(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0,
+                                      with_E=True)
+    nc = sc.nc
+    sc_ = 1e-13 * np.abs(H).max()
+    for i in range(nc):
+        np.testing.assert_allclose(Hpp[i], H[9 * i:9 * i + 9, 9 * i:9 * i + 9], atol=sc_)
+        np.testing.assert_allclose(v[i], g[9 * i:9 * i + 9], atol=1e-13 * np.abs(g).max())
+    for j in range(sc.np_):
+        o = 9 * nc + 3 * j
+        np.testing.assert_allclose(Hll[j], H[o:o + 3, o:o + 3], atol=sc_)
+        np.testing.assert_allclose(w[j], g[o:o + 3], atol=1e-13 * np.abs(g).max())
+    # off-diagonal camera-point blocks: sum of per-edge E_k
+    Eb = np.zeros((9 * nc, 3 * sc.np_))
+    for k in range(sc.n):
+        i, j = sc.cam_idx[k], sc.pt_idx[k]
+        Eb[9 * i:9 * i + 9, 3 * j:3 * j + 3] += E[k]
+    np.testing.assert_allclose(Eb, H[:9 * nc, 9 * nc:], atol=sc_)
+    # camera-camera and point-point off-diagonal blocks of H are zero (B, C block diagonal)
+    for i in range(nc):
+        for i2 in range(nc):
+            if i2 != i:
+                assert np.all(H[9 * i:9 * i + 9, 9 * i2:9 * i2 + 9] == 0)
+
+
+def _damped_dense(sc, mu, damping="diag", loss="none", delta=0.0):
+    J, Wr, e, _ = _dense_system(sc, loss, delta)
+    H = J.T @ (Wr[:, None] * J)
+    g = -J.T @ (Wr * e)
+    d = np.clip(np.diag(H), 1e-6, 1e32) if damping == "diag" else np.ones(H.shape[0])
+    return H + mu * np.diag(d), g, J, Wr, e
+
+
+@pytest.mark.parametrize("damping", ["diag", "identity"])
+def test_schur_step_equals_direct_solve(damping):
+    sc = make_scene(4, 25, sigma=1.0, seed=9)
+    mu = 1e-3
+    Hd, g, *_ = _damped_dense(sc, mu, damping)
+    dx = np.linalg.solve(Hd, g)
+    nc = sc.nc
+    for mode, tol in [("dense", 1e-9), ("explicit_pcg", 1e-7), ("implicit_pcg", 1e-7)]:
+        r = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, damping=damping,
+                        schur=mode, pcg_max=500, pcg_tol=1e-15)
+        got = np.concatenate([r["dc"].reshape(-1), r["dp"].reshape(-1)])
+        np.testing.assert_allclose(got, dx, atol=tol * np.abs(dx).max(), err_msg=mode)
+        assert r["dc"].shape == (nc, 9)
+
+
+def test_implicit_schur_product_equals_dense_complement():
+    sc = make_scene(4, 25, sigma=1.0, seed=11)
+    mu = 0.1
+    Hd, g, *_ = _damped_dense(sc, mu)
+    m = 9 * sc.nc
+    B, E, Cm = Hd[:m, :m], Hd[:m, m:], Hd[m:, m:]
+    S = B - E @ np.linalg.solve(Cm, E.T)
+    rhs = g[:m] - E @ np.linalg.solve(Cm, g[m:])
+    x = np.random.default_rng(1).normal(size=m)
+    r = oracle.schur(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, x=x, dense=True)
+    np.testing.assert_allclose(r["y"], S @ x, atol=1e-10 * np.abs(S @ x).max())
+    np.testing.assert_allclose(r["rhs"], rhs, atol=1e-10 * np.abs(rhs).max())
+    np.testing.assert_allclose(r["S"], S, atol=1e-10 * np.abs(S).max())
+    # symmetric positive definite
+    np.testing.assert_allclose(S, S.T, atol=1e-9 * np.abs(S).max())
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+
+
+def test_model_decrease_matches_quadratic_model():
+    sc = make_scene(4, 25, sigma=2.0, seed=12, outlier_frac=0.1)
+    mu = 1e-2
+    r = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, loss="huber", delta=2.0,
+                    schur="dense")
+    _, _, J, Wr, e = _damped_dense(sc, mu, loss="huber", delta=2.0)
+    dx = np.concatenate([r["dc"].reshape(-1), r["dp"].reshape(-1)])
+    f = e + J @ dx
+    ref = 0.5 * np.sum(Wr * (e * e - f * f))
+    assert r["model_dec"] == pytest.approx(ref, rel=1e-10)
+
+
+def test_split_sum_invariant():
+    """H = sum_k H_k over any edge partition (Sec. 4.1)."""
+    sc = make_scene(5, 40, sigma=1.0, seed=13)
+    full = oracle.blocks(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    K = 3
+    parts = np.array_split(np.arange(sc.n), K)
+    acc = [np.zeros_like(a) for a in full]
+    for p in parts:
+        sub = oracle.blocks(sc.cameras, sc.points, sc.observations[p], sc.cam_idx[p], sc.pt_idx[p])
+        for a, b in zip(acc, sub):
+            a += b
+    for a, b in zip(acc, full):
+        np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, np.abs(b).max()))
+
+
+def test_noise_free_scene_reaches_zero_cost():
+    sc = make_scene(6, 200, sigma=0.0, seed=14)
+    # the generator's ideal pixels are exactly the oracle's projections at the truth
+    c_true = oracle.evaluate(sc.cameras_true, sc.points_true, sc.observations, sc.cam_idx, sc.pt_idx)[0]
+    assert c_true < 1e-18 * sc.n
+    r = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=30, pcg_max=200,
+                        pcg_tol=1e-14)
+    assert r["trace"][0]["cost"] > 1.0
+    assert r["final_cost"] < 1e-16 * sc.n
+
+
+def test_accepted_cost_is_monotone_and_reaches_noise_floor():
+    sc = make_scene(16, 2000, sigma=0.5, seed=0)
+    r = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=10, pcg_max=50)
+    costs = [t["cost"] for t in r["trace"]] + [r["final_cost"]]
+    assert all(b <= a for a, b in zip(costs, costs[1:]))
+    for t in r["trace"]:
+        if t["accepted"]:
+            assert t["cost_new"] < t["cost"]
+    # least-squares noise floor: E[sum |e|^2] = sigma^2 (2n - dof)
+    dof = 9 * sc.nc + 3 * sc.np_
+    expected = 0.5 * 0.25 * (2 * sc.n - dof)
+    assert r["final_cost"] == pytest.approx(expected, rel=0.05)
