@@ -1,0 +1,599 @@
+// api.cu -- host side of the C ABI declared in include/mba.h: problem creation
+// (one device pool sized up front), the solve driver that issues the LM
+// iterations without host round trips, and the inspection entry points.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mba_internal.cuh"
+
+
+using namespace mba;
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr int kTraceCap = 4096;
+constexpr int64_t kEvalSlice = 1 << 18;
+constexpr long long kDefaultSpin = 4000000;
+
+mba_status fail(mba_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(MBA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Carve {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename X>
+    X *take(size_t count) {
+        X *p = base ? reinterpret_cast<X *>(base + off) : nullptr;
+        off += al(sizeof(X) * (count ? count : 1));
+        return p;
+    }
+};
+
+}  // namespace
+
+struct mba_problem {
+    Prob P;
+    cudaStream_t stream = nullptr;
+    void *pool = nullptr;
+    size_t pool_bytes = 0;
+    int32_t *cfirst = nullptr;      // per camera first chunk (device)
+    int32_t *orig_cam = nullptr, *orig_pt = nullptr;
+    double2 *orig_uv = nullptr;
+    double *eval_stage = nullptr;   // kEvalSlice x 26 doubles
+    double *part_a = nullptr, *part_b = nullptr;
+    double *scalar = nullptr;       // 8 doubles of scratch results
+    int nb_chunk = 0, nb_cost = 0;
+    int pcg_grid = 0;
+    mba_iteration *trace_dev = nullptr;
+};
+
+extern "C" {
+
+void mba_problem_options_default(mba_problem_options *o) {
+    if (!o) return;
+    o->precision = MBA_FP64;
+    o->loss = MBA_LOSS_NONE;
+    o->huber_delta = 0.0;
+    o->cuda_stream = nullptr;
+}
+
+void mba_solver_options_default(mba_solver_options *o) {
+    if (!o) return;
+    o->max_iter = 10;
+    o->pcg_max_iter = 100;
+    o->pcg_rel_tol = 1e-10;
+    o->damping = MBA_DAMP_DIAG;
+    o->initial_radius = 1e4;
+    o->min_relative_decrease = 1e-3;
+    o->function_tol = 0.0;
+    o->barrier_spin_limit = 0;
+    o->collect_timing = 0;
+}
+
+const char *mba_status_string(mba_status s) {
+    switch (s) {
+        case MBA_OK: return "MBA_OK";
+        case MBA_ERR_INVALID_ARG: return "MBA_ERR_INVALID_ARG";
+        case MBA_ERR_OOM: return "MBA_ERR_OOM";
+        case MBA_ERR_CUDA: return "MBA_ERR_CUDA";
+        case MBA_ERR_NONFINITE: return "MBA_ERR_NONFINITE";
+        case MBA_ERR_TIMEOUT: return "MBA_ERR_TIMEOUT";
+        case MBA_ERR_NOT_CONVERGED: return "MBA_ERR_NOT_CONVERGED";
+    }
+    return "MBA_ERR_UNKNOWN";
+}
+
+const char *mba_last_error(void) { return g_err.c_str(); }
+
+void mba_problem_destroy(mba_problem *pr) {
+    if (!pr) return;
+    if (pr->stream) cudaStreamSynchronize(pr->stream);
+    if (pr->pool) cudaFree(pr->pool);
+    delete pr;
+}
+
+mba_status mba_problem_create(const double *cameras, int32_t nc, const double *points, int32_t np,
+                              const double *observations, const int32_t *cam_idx, const int32_t *pt_idx, int64_t n,
+                              const mba_problem_options *opt, mba_problem **out) {
+    g_err.clear();
+    if (!out) return fail(MBA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cameras || !points || !observations || !cam_idx || !pt_idx)
+        return fail(MBA_ERR_INVALID_ARG, "a required input pointer is NULL");
+    if (nc < 1 || np < 1 || n < 1) return fail(MBA_ERR_INVALID_ARG, "nc, np and n must be >= 1");
+    if (n >= (int64_t(1) << 31) - 4096) return fail(MBA_ERR_INVALID_ARG, "n must be below 2^31 - 4096");
+    mba_problem_options o;
+    mba_problem_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != MBA_FP64 && o.precision != MBA_FP32_MIXED) return fail(MBA_ERR_INVALID_ARG, "bad precision");
+    if (o.loss != MBA_LOSS_NONE && o.loss != MBA_LOSS_HUBER) return fail(MBA_ERR_INVALID_ARG, "bad loss");
+    if (o.loss == MBA_LOSS_HUBER && !(o.huber_delta > 0.0)) return fail(MBA_ERR_INVALID_ARG, "huber_delta must be > 0");
+
+    mba_problem *pr = new mba_problem();
+    Prob &P = pr->P;
+    std::memset(&P, 0, sizeof(P));
+    pr->stream = (cudaStream_t)o.cuda_stream;
+    cudaStream_t s = pr->stream;
+    P.nc = nc;
+    P.np = np;
+    P.n = n;
+    P.npad = ((n + 63) / 64) * 64 + 64;
+    P.fp32 = o.precision == MBA_FP32_MIXED;
+    P.loss = o.loss;
+    P.delta = o.huber_delta;
+    const size_t w = P.fp32 ? 4 : 8;
+    const int64_t pbound = (n + 512) / 513 + 2;                 // point chunks (stride >= 513)
+    const int64_t cbound = n / kCamChunk + (int64_t)nc + 2;     // camera chunks
+    pr->pcg_grid = 0;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+        pr->nb_chunk = sms * 4;
+    }
+    pr->nb_cost = cost_grid(P);
+    const int red_len = 3 * 8192;
+    const int64_t stage = n < kEvalSlice ? n : kEvalSlice;
+
+    auto layout = [&](Carve &c) {
+        P.cams = c.take<double>(9 * (size_t)nc);
+        P.cams_new = c.take<double>(9 * (size_t)nc);
+        P.cams0 = c.take<double>(9 * (size_t)nc);
+        P.pts = c.take<double>(3 * (size_t)np);
+        P.pts_new = c.take<double>(3 * (size_t)np);
+        P.pts0 = c.take<double>(3 * (size_t)np);
+        P.pm_cam = c.take<int32_t>(n);
+        P.pm_pt = c.take<int32_t>(n);
+        P.pm_orig = c.take<int32_t>(n);
+        P.pm_uv = c.take<double2>(n);
+        P.pt_ptr = c.take<int32_t>((size_t)np + 1);
+        P.cm_pt = c.take<int32_t>(n);
+        P.cm_orig = c.take<int32_t>(n);
+        P.cm_uv = c.take<double2>(n);
+        P.cam_ptr = c.take<int32_t>((size_t)nc + 1);
+        P.pchunk = c.take<int32_t>(pbound + 1);
+        P.cchunk_cam = c.take<int32_t>(cbound);
+        P.cchunk_beg = c.take<int32_t>(cbound + 1);
+        pr->cfirst = c.take<int32_t>((size_t)nc + 1);
+        pr->orig_cam = c.take<int32_t>(n);
+        pr->orig_pt = c.take<int32_t>(n);
+        pr->orig_uv = c.take<double2>(n);
+        P.J = c.take<char>(24 * (size_t)P.npad * w);
+        P.res = c.take<char>(2 * (size_t)P.npad * w);
+        P.camtab = c.take<char>((size_t)nc * kCamTab * w);
+        P.camtab64 = c.take<double>((size_t)nc * kCamTab);
+        P.Hpp = c.take<double>(45 * (size_t)nc);
+        P.v = c.take<double>(9 * (size_t)nc);
+        P.Hll = c.take<double>(6 * (size_t)np);
+        P.w = c.take<double>(3 * (size_t)np);
+        P.cpart = c.take<double>(54 * (size_t)cbound);
+        P.Bd = c.take<double>(81 * (size_t)nc);
+        P.Binv = c.take<double>(81 * (size_t)nc);
+        P.Cinv = c.take<char>(6 * (size_t)np * w);
+        P.x = c.take<double>((size_t)nc * kVec);
+        P.r = c.take<double>((size_t)nc * kVec);
+        P.z = c.take<double>((size_t)nc * kVec);
+        P.p = c.take<double>((size_t)nc * kVec);
+        P.q = c.take<double>((size_t)nc * kVec);
+        P.g = c.take<double>((size_t)nc * kVec);
+        P.pT = c.take<char>((size_t)nc * kVec * w);
+        P.cacc = c.take<char>(2 * (size_t)nc * kVec * w);
+        P.dp = c.take<double>(3 * (size_t)np);
+        P.red = c.take<double>(red_len);
+        pr->part_a = c.take<double>(8192);
+        pr->part_b = c.take<double>(8192);
+        pr->scalar = c.take<double>(8);
+        P.st = c.take<DevState>(1);
+        pr->trace_dev = c.take<mba_iteration>(kTraceCap);
+        pr->eval_stage = c.take<double>(26 * (size_t)stage);
+    };
+    Carve sizing;
+    layout(sizing);
+    pr->pool_bytes = sizing.off;
+    P.red_len = red_len;
+    if (cudaMalloc(&pr->pool, pr->pool_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete pr;
+        return fail(MBA_ERR_OOM, "device pool of " + std::to_string(pr->pool_bytes) + " bytes");
+    }
+    Carve real;
+    real.base = (char *)pr->pool;
+    layout(real);
+
+    // temporary buffers for the set-up only
+    const size_t sort_tmp = stable_sort_tmp_bytes(n, np > nc ? np : nc);
+    void *tmp = nullptr;
+    if (cudaMalloc(&tmp, sort_tmp + al(sizeof(double) * 2 * (size_t)n) + 256) != cudaSuccess) {
+        cudaGetLastError();
+        mba_problem_destroy(pr);
+        return fail(MBA_ERR_OOM, "set-up scratch");
+    }
+    double *obs_d = (double *)((char *)tmp + sort_tmp);
+    int32_t *flags = (int32_t *)pr->scalar;  // 4 ints
+
+    auto cleanup_fail = [&](mba_status st, const std::string &m) {
+        cudaFree(tmp);
+        mba_problem_destroy(pr);
+        return fail(st, m);
+    };
+#define CKC(call)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return cleanup_fail(MBA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+    CKC(cudaMemcpyAsync(P.cams, cameras, sizeof(double) * 9 * (size_t)nc, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemcpyAsync(P.pts, points, sizeof(double) * 3 * (size_t)np, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemcpyAsync(obs_d, observations, sizeof(double) * 2 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemcpyAsync(pr->orig_cam, cam_idx, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemcpyAsync(pr->orig_pt, pt_idx, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, s));
+    CKC(validate_inputs(P.cams, nc, P.pts, np, obs_d, pr->orig_cam, pr->orig_pt, n, flags, s));
+    int32_t hflags[4];
+    CKC(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(s));
+    if (hflags[0] & 1) return cleanup_fail(MBA_ERR_INVALID_ARG, "camera or point index out of range");
+    if (hflags[0] & 2) return cleanup_fail(MBA_ERR_NONFINITE, "non-finite camera, point or observation value");
+
+    CKC(stable_sort_by_key(pr->orig_pt, n, np, P.pm_orig, P.pt_ptr, tmp, sort_tmp, s));
+    CKC(stable_sort_by_key(pr->orig_cam, n, nc, P.cm_orig, P.cam_ptr, tmp, sort_tmp, s));
+    CKC(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, s));
+    CKC(gather_layout(P, obs_d, pr->orig_cam, pr->orig_pt, nullptr, flags, s));
+    // keep the observations in input order too (for mba_evaluate)
+    {
+        // interleaved copy obs_d (n x 2) -> orig_uv (double2): same bytes
+        CKC(cudaMemcpyAsync(pr->orig_uv, obs_d, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    std::vector<int32_t> cam_ptr((size_t)nc + 1);
+    CKC(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    CKC(cudaMemcpyAsync(cam_ptr.data(), P.cam_ptr, sizeof(int32_t) * ((size_t)nc + 1), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(s));
+    if ((hflags[0] & 4) || (hflags[2] & 4))
+        return cleanup_fail(MBA_ERR_INVALID_ARG, "a camera or point has no observations");
+    const int max_track = hflags[1];
+    if (max_track > kMaxTrack)
+        return cleanup_fail(MBA_ERR_INVALID_ARG,
+                            "a point has " + std::to_string(max_track) + " observations; at most 1024 are supported");
+    P.cap = max_track <= 512 ? 1024 : 2048;
+    const int stride = P.cap - max_track + 1;
+    P.n_pchunks = (int)((n + stride - 1) / stride);
+    if (P.n_pchunks > pbound) return cleanup_fail(MBA_ERR_INVALID_ARG, "internal: point chunk bound");
+    CKC(build_point_chunks(P, stride, s));
+
+    // camera chunks (host: nc is small)
+    {
+        std::vector<int32_t> ccam, cbeg, cfirst((size_t)nc + 1);
+        for (int32_t i = 0; i < nc; ++i) {
+            cfirst[i] = (int32_t)ccam.size();
+            for (int32_t b = cam_ptr[i]; b < cam_ptr[i + 1]; b += kCamChunk) {
+                ccam.push_back(i);
+                cbeg.push_back(b);
+            }
+        }
+        cfirst[nc] = (int32_t)ccam.size();
+        cbeg.push_back((int32_t)n);
+        P.n_cchunks = (int)ccam.size();
+        if (P.n_cchunks > cbound) return cleanup_fail(MBA_ERR_INVALID_ARG, "internal: camera chunk bound");
+        // chunks are contiguous in the camera-major order: chunk c is [cbeg[c], cbeg[c+1])
+        CKC(cudaMemcpyAsync(P.cchunk_cam, ccam.data(), sizeof(int32_t) * ccam.size(), cudaMemcpyHostToDevice, s));
+        CKC(cudaMemcpyAsync(P.cchunk_beg, cbeg.data(), sizeof(int32_t) * cbeg.size(), cudaMemcpyHostToDevice, s));
+        CKC(cudaMemcpyAsync(pr->cfirst, cfirst.data(), sizeof(int32_t) * cfirst.size(), cudaMemcpyHostToDevice, s));
+        CKC(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
+    CKC(cudaMemcpyAsync(P.cams0, P.cams, sizeof(double) * 9 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
+    CKC(cudaMemcpyAsync(P.pts0, P.pts, sizeof(double) * 3 * (size_t)np, cudaMemcpyDeviceToDevice, s));
+    CKC(cudaMemsetAsync(P.st, 0, sizeof(DevState), s));
+    CKC(cudaMemsetAsync(P.J, 0, 24 * (size_t)P.npad * w, s));
+    CKC(cudaMemsetAsync(P.res, 0, 2 * (size_t)P.npad * w, s));
+    CKC(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+#undef CKC
+    pr->pcg_grid = pcg_grid_size(P);
+    if (3 * pr->pcg_grid > red_len) {
+        mba_problem_destroy(pr);
+        return fail(MBA_ERR_INVALID_ARG, "internal: reduction buffer");
+    }
+    P.trace = pr->trace_dev;
+    P.trace_cap = kTraceCap;
+    *out = pr;
+    return MBA_OK;
+}
+
+mba_status mba_problem_info(const mba_problem *pr, int32_t *nc, int32_t *np, int64_t *n, size_t *bytes) {
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    if (nc) *nc = pr->P.nc;
+    if (np) *np = pr->P.np;
+    if (n) *n = pr->P.n;
+    if (bytes) *bytes = pr->pool_bytes;
+    return MBA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+mba_status check_device_state(mba_problem *pr, DevState *hs) {
+    CK(cudaMemcpyAsync(hs, pr->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, pr->stream));
+    CK(cudaStreamSynchronize(pr->stream));
+    if (hs->err == MBA_ERR_TIMEOUT) return fail(MBA_ERR_TIMEOUT, "a grid barrier of the persistent PCG kernel timed out");
+    if (hs->err == MBA_ERR_NONFINITE) return fail(MBA_ERR_NONFINITE, "a damped block is not positive definite");
+    if (hs->err != 0) return fail((mba_status)hs->err, "device error");
+    return MBA_OK;
+}
+
+// linearise at the current parameters with mu, and form the damped blocks
+mba_status prepare_step(mba_problem *pr, double mu, int damping) {
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    CK(launch_state_init(P, 1.0, mu, 0, s));
+    CK(launch_camera_tables_forced(P, P.cams, s));
+    CK(launch_linearize_impl(P, pr->cfirst, 1, s));
+    CK(launch_damp(P, damping, s));
+    CK(cudaMemsetAsync(P.cacc, 0, 2 * (size_t)P.nc * kVec * (P.fp32 ? 4 : 8), s));
+    return MBA_OK;
+}
+
+bool valid_solver_opts(const mba_solver_options &o) {
+    return o.max_iter >= 0 && o.pcg_max_iter >= 0 && o.pcg_rel_tol >= 0.0 &&
+           (o.damping == MBA_DAMP_DIAG || o.damping == MBA_DAMP_IDENTITY) && o.initial_radius > 0.0 &&
+           o.function_tol >= 0.0 && o.barrier_spin_limit >= 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+mba_status mba_evaluate(mba_problem *pr, double *cost, double *residuals, double *jac_cam, double *jac_pt) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    CK(launch_camera_tables_forced(P, P.cams, s));
+    if (cost) {
+        CK(launch_cost_impl(P, P.pts, pr->part_b, pr->scalar, nullptr, 0, s));
+        CK(cudaMemcpyAsync(cost, pr->scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (residuals || jac_cam || jac_pt) {
+        const int64_t slice = P.n < kEvalSlice ? P.n : kEvalSlice;
+        double *e_d = pr->eval_stage, *jc_d = e_d + 2 * slice, *jp_d = jc_d + 18 * slice;
+        for (int64_t k0 = 0; k0 < P.n; k0 += slice) {
+            const int64_t m = (P.n - k0) < slice ? (P.n - k0) : slice;
+            CK(launch_evaluate_slice(P, pr->orig_cam + k0, pr->orig_pt + k0, pr->orig_uv + k0, m, e_d, jc_d, jp_d, s));
+            if (residuals) CK(cudaMemcpyAsync(residuals + 2 * k0, e_d, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
+            if (jac_cam) CK(cudaMemcpyAsync(jac_cam + 18 * k0, jc_d, sizeof(double) * 18 * m, cudaMemcpyDeviceToHost, s));
+            if (jac_pt) CK(cudaMemcpyAsync(jac_pt + 6 * k0, jp_d, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    return MBA_OK;
+}
+
+mba_status mba_get_parameters(const mba_problem *pr, double *cameras, double *points) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    const Prob &P = pr->P;
+    if (cameras) CK(cudaMemcpyAsync(cameras, P.cams, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyDeviceToHost, pr->stream));
+    if (points) CK(cudaMemcpyAsync(points, P.pts, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyDeviceToHost, pr->stream));
+    CK(cudaStreamSynchronize(pr->stream));
+    return MBA_OK;
+}
+
+mba_status mba_set_parameters(mba_problem *pr, const double *cameras, const double *points) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    const Prob &P = pr->P;
+    if (cameras) CK(cudaMemcpyAsync(P.cams, cameras, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyHostToDevice, pr->stream));
+    if (points) CK(cudaMemcpyAsync(P.pts, points, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyHostToDevice, pr->stream));
+    CK(cudaStreamSynchronize(pr->stream));
+    return MBA_OK;
+}
+
+mba_status mba_reset(mba_problem *pr) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    const Prob &P = pr->P;
+    CK(cudaMemcpyAsync(P.cams, P.cams0, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyDeviceToDevice, pr->stream));
+    CK(cudaMemcpyAsync(P.pts, P.pts0, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyDeviceToDevice, pr->stream));
+    CK(cudaStreamSynchronize(pr->stream));
+    return MBA_OK;
+}
+
+mba_status mba_get_ordering(const mba_problem *pr, int32_t *pt_perm, int32_t *pt_ptr, int32_t *cam_perm,
+                            int32_t *cam_ptr) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    const Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    if (pt_perm) CK(cudaMemcpyAsync(pt_perm, P.pm_orig, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost, s));
+    if (pt_ptr) CK(cudaMemcpyAsync(pt_ptr, P.pt_ptr, sizeof(int32_t) * ((size_t)P.np + 1), cudaMemcpyDeviceToHost, s));
+    if (cam_perm) CK(cudaMemcpyAsync(cam_perm, P.cm_orig, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost, s));
+    if (cam_ptr) CK(cudaMemcpyAsync(cam_ptr, P.cam_ptr, sizeof(int32_t) * ((size_t)P.nc + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MBA_OK;
+}
+
+mba_status mba_linear_system(mba_problem *pr, double mu, int32_t damping, double *Hpp, double *v, double *Hll,
+                             double *w, double *rhs) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    if (!(mu >= 0.0) || (damping != MBA_DAMP_DIAG && damping != MBA_DAMP_IDENTITY))
+        return fail(MBA_ERR_INVALID_ARG, "mu must be >= 0 and damping valid");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    mba_status st = prepare_step(pr, mu, damping);
+    if (st) return st;
+    if (rhs) CK(launch_pcg(P, PCG_RHS_ONLY, 0, 0.0, kDefaultSpin, pr->pcg_grid, s));
+    DevState hs;
+    st = check_device_state(pr, &hs);
+    if (st) return st;
+    if (Hpp) {
+        std::vector<double> h(45 * (size_t)P.nc);
+        CK(cudaMemcpy(h.data(), P.Hpp, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < P.nc; ++i)
+            for (int a = 0; a < 9; ++a)
+                for (int b = 0; b < 9; ++b) Hpp[81 * (size_t)i + a * 9 + b] = h[45 * (size_t)i + sym9(a, b)];
+    }
+    if (v) CK(cudaMemcpy(v, P.v, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyDeviceToHost));
+    if (Hll) {
+        std::vector<double> h(6 * (size_t)P.np);
+        CK(cudaMemcpy(h.data(), P.Hll, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        for (int32_t j = 0; j < P.np; ++j)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) Hll[9 * (size_t)j + a * 3 + b] = h[6 * (size_t)j + sym3(a, b)];
+    }
+    if (w) CK(cudaMemcpy(w, P.w, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyDeviceToHost));
+    if (rhs) {
+        std::vector<double> g((size_t)P.nc * kVec);
+        CK(cudaMemcpy(g.data(), P.g, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < P.nc; ++i)
+            for (int a = 0; a < 9; ++a) rhs[9 * (size_t)i + a] = g[(size_t)i * kVec + a];
+    }
+    return MBA_OK;
+}
+
+mba_status mba_schur_matvec(mba_problem *pr, double mu, int32_t damping, const double *x, double *y) {
+    g_err.clear();
+    if (!pr || !x || !y) return fail(MBA_ERR_INVALID_ARG, "NULL argument");
+    if (!(mu >= 0.0) || (damping != MBA_DAMP_DIAG && damping != MBA_DAMP_IDENTITY))
+        return fail(MBA_ERR_INVALID_ARG, "mu must be >= 0 and damping valid");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    mba_status st = prepare_step(pr, mu, damping);
+    if (st) return st;
+    std::vector<double> buf((size_t)P.nc * kVec, 0.0);
+    for (int32_t i = 0; i < P.nc; ++i)
+        for (int a = 0; a < 9; ++a) buf[(size_t)i * kVec + a] = x[9 * (size_t)i + a];
+    CK(cudaMemcpyAsync(P.p, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s));
+    CK(launch_pcg(P, PCG_MATVEC, 0, 0.0, kDefaultSpin, pr->pcg_grid, s));
+    DevState hs;
+    st = check_device_state(pr, &hs);
+    if (st) return st;
+    CK(cudaMemcpy(buf.data(), P.q, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < P.nc; ++i)
+        for (int a = 0; a < 9; ++a) y[9 * (size_t)i + a] = buf[(size_t)i * kVec + a];
+    return MBA_OK;
+}
+
+mba_status mba_step(mba_problem *pr, double mu, const mba_solver_options *opt, double *dc, double *dp,
+                    int32_t *pcg_iters, double *model_decrease) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    mba_solver_options o;
+    mba_solver_options_default(&o);
+    if (opt) o = *opt;
+    if (!valid_solver_opts(o) || !(mu >= 0.0)) return fail(MBA_ERR_INVALID_ARG, "bad solver options or mu");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    mba_status st = prepare_step(pr, mu, o.damping);
+    if (st) return st;
+    const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
+    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+    CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
+    DevState hs;
+    st = check_device_state(pr, &hs);
+    if (st) return st;
+    if (dc) {
+        std::vector<double> buf((size_t)P.nc * kVec);
+        CK(cudaMemcpy(buf.data(), P.x, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < P.nc; ++i)
+            for (int a = 0; a < 9; ++a) dc[9 * (size_t)i + a] = buf[(size_t)i * kVec + a];
+    }
+    if (dp) CK(cudaMemcpy(dp, P.dp, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyDeviceToHost));
+    if (pcg_iters) *pcg_iters = hs.pcg_iters;
+    if (model_decrease) *model_decrease = hs.model_dec;
+    return MBA_OK;
+}
+
+mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary *summary) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    mba_solver_options o;
+    mba_solver_options_default(&o);
+    if (opt) o = *opt;
+    if (!valid_solver_opts(o)) return fail(MBA_ERR_INVALID_ARG, "bad solver options");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
+    const bool timing = o.collect_timing != 0;
+    const int ne = timing ? 4 * o.max_iter + 2 : 0;
+    std::vector<cudaEvent_t> ev(ne);
+    for (int i = 0; i < ne; ++i) CK(cudaEventCreate(&ev[i]));
+    auto rec = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+
+    CK(rec(0));
+    CK(launch_state_init(P, o.initial_radius, -1.0, 0, s));
+    CK(launch_camera_tables(P, P.cams, false, s));
+    CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s));
+    const size_t cacc_bytes = 2 * (size_t)P.nc * kVec * (P.fp32 ? 4 : 8);
+    for (int it = 0; it < o.max_iter; ++it) {
+        CK(rec(1 + 4 * it));
+        CK(launch_camera_tables(P, P.cams, true, s));
+        CK(launch_linearize_impl(P, pr->cfirst, 0, s));
+        CK(rec(2 + 4 * it));
+        CK(launch_damp(P, o.damping, s));
+        CK(cudaMemsetAsync(P.cacc, 0, cacc_bytes, s));
+        CK(rec(3 + 4 * it));
+        CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+        CK(rec(4 + 4 * it));
+        CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
+        CK(launch_camera_tables(P, P.cams_new, false, s));
+        CK(launch_cost_impl(P, P.pts_new, pr->part_b, &P.st->cost_new, nullptr, 1, s));
+        CK(launch_lm_update(P, o, s));
+        CK(launch_accept(P, s));
+    }
+    CK(rec(ne > 0 ? ne - 1 : 0));
+    DevState hs;
+    mba_status st = check_device_state(pr, &hs);
+    if (summary) {
+        summary->iterations = hs.iter;
+        summary->accepted = hs.accepted_total;
+        summary->pcg_iters_total = hs.pcg_total;
+        summary->status = st;
+        summary->initial_cost = hs.initial_cost;
+        summary->final_cost = hs.cost;
+        summary->final_radius = hs.radius;
+        summary->final_mu = 1.0 / hs.radius;
+        summary->ms_total = summary->ms_linearize = summary->ms_pcg = summary->ms_other = 0.0;
+        if (timing) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[0], ev[ne - 1]);
+            summary->ms_total = t;
+            double lin = 0, pcg = 0;
+            for (int it = 0; it < o.max_iter; ++it) {
+                cudaEventElapsedTime(&t, ev[1 + 4 * it], ev[2 + 4 * it]);
+                lin += t;
+                cudaEventElapsedTime(&t, ev[3 + 4 * it], ev[4 + 4 * it]);
+                pcg += t;
+            }
+            summary->ms_linearize = lin;
+            summary->ms_pcg = pcg;
+            summary->ms_other = summary->ms_total - lin - pcg;
+        }
+        if (summary->trace && summary->trace_capacity > 0) {
+            int cnt = hs.iter < summary->trace_capacity ? hs.iter : summary->trace_capacity;
+            if (cnt > kTraceCap) cnt = kTraceCap;
+            if (cnt > 0)
+                CK(cudaMemcpy(summary->trace, pr->trace_dev, sizeof(mba_iteration) * cnt, cudaMemcpyDeviceToHost));
+        }
+    }
+    for (int i = 0; i < ne; ++i) cudaEventDestroy(ev[i]);
+    return st;
+}
+
+}  // extern "C"

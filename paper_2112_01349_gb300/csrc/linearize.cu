@@ -1,0 +1,301 @@
+// linearize.cu -- residuals, analytic Jacobians and the Hessian blocks
+// (Alg. 1: residual/Jacobian step and linear-system step; Sec. 3 Eq. 2).
+//
+// * camera_table_kernel: per camera, R(w) and the rotation-Jacobian factor M
+//   in FP64 (rounded to T for the FP32-mixed form).
+// * lin_point_kernel: point-major; per observation e, Jc, Jp and the IRLS
+//   weight W, stored sqrt(W)-scaled as structure-of-arrays in point-major order
+//   (the layout every later pass streams); per point C = sum Jp~^T Jp~ and
+//   w = -sum Jp~^T e~ reduced in shared memory in a fixed order.
+// * lin_camera_kernel: camera-major chunks; recomputes Jc (cheaper than
+//   re-reading it in another order) and reduces B = sum Jc~^T Jc~ and
+//   v = -sum Jc~^T e~ per chunk; cam_finalize sums the chunks of each camera
+//   in order.
+// * cost kernels: F = 1/2 sum rho(|e|^2) in FP64 for accept/reject.
+#include "mba_internal.cuh"
+
+namespace mba {
+
+namespace {
+
+inline unsigned grid_for(int64_t n, int per = kBlock) {
+    int64_t g = (n + per - 1) / per;
+    if (g > 152 * 16) g = 152 * 16;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+__global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc, T *__restrict__ tab,
+                                    double *__restrict__ tab64, const DevState *st, int gate) {
+    if (gate == 1 && (st->done || !st->relin)) return;
+    if (gate == 2 && st->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        double row[kCamTab];
+        camera_table_row(cams + 9 * (int64_t)i, row);
+        if (tab)
+#pragma unroll
+            for (int q = 0; q < kCamTab; ++q) tab[(int64_t)i * kCamTab + q] = (T)row[q];
+        if (tab64)
+#pragma unroll
+            for (int q = 0; q < kCamTab; ++q) tab64[(int64_t)i * kCamTab + q] = row[q];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
+    if (!force && (P.st->done || !P.st->relin)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *slot = reinterpret_cast<T *>(smem_raw);  // [9][cap]
+    const T *__restrict__ camtab = (const T *)P.camtab;
+    T *__restrict__ J = (T *)P.J;
+    T *__restrict__ res = (T *)P.res;
+    const int64_t np_ = P.npad;
+    const int cap = P.cap;
+    const T delta = (T)P.delta;
+    for (int c = blockIdx.x; c < P.n_pchunks; c += gridDim.x) {
+        const int j0 = P.pchunk[c], j1 = P.pchunk[c + 1];
+        if (j0 == j1) continue;
+        const int o0 = P.pt_ptr[j0], m = P.pt_ptr[j1] - o0;
+        for (int k = threadIdx.x; k < m; k += kBlock) {
+            const int64_t o = (int64_t)o0 + k;
+            const int cam = P.pm_cam[o], pt = P.pm_pt[o];
+            const double2 uv = P.pm_uv[o];
+            T e[2], Jc[18], Jp[6];
+            project<T, true>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
+                             (T)P.pts[3 * (int64_t)pt + 1], (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc,
+                             Jp);
+            T rho, W;
+            loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+            const T sw = sqrt(W);
+#pragma unroll
+            for (int q = 0; q < 18; ++q) {
+                Jc[q] *= sw;
+                J[q * np_ + o] = Jc[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                Jp[q] *= sw;
+                J[(18 + q) * np_ + o] = Jp[q];
+            }
+            e[0] *= sw;
+            e[1] *= sw;
+            res[o] = e[0];
+            res[np_ + o] = e[1];
+            // C terms (packed upper 3x3) and w terms
+            slot[0 * cap + k] = Jp[0] * Jp[0] + Jp[3] * Jp[3];
+            slot[1 * cap + k] = Jp[0] * Jp[1] + Jp[3] * Jp[4];
+            slot[2 * cap + k] = Jp[0] * Jp[2] + Jp[3] * Jp[5];
+            slot[3 * cap + k] = Jp[1] * Jp[1] + Jp[4] * Jp[4];
+            slot[4 * cap + k] = Jp[1] * Jp[2] + Jp[4] * Jp[5];
+            slot[5 * cap + k] = Jp[2] * Jp[2] + Jp[5] * Jp[5];
+            slot[6 * cap + k] = -(Jp[0] * e[0] + Jp[3] * e[1]);
+            slot[7 * cap + k] = -(Jp[1] * e[0] + Jp[4] * e[1]);
+            slot[8 * cap + k] = -(Jp[2] * e[0] + Jp[5] * e[1]);
+        }
+        __syncthreads();
+        for (int j = j0 + threadIdx.x; j < j1; j += kBlock) {
+            const int b = P.pt_ptr[j] - o0, e_ = P.pt_ptr[j + 1] - o0;
+            T acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[q] = T(0);
+            for (int s = b; s < e_; ++s)
+#pragma unroll
+                for (int q = 0; q < 9; ++q) acc[q] += slot[q * cap + s];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) P.Hll[6 * (int64_t)j + q] = (double)acc[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) P.w[3 * (int64_t)j + q] = (double)acc[6 + q];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
+    if (!force && (P.st->done || !P.st->relin)) return;
+    __shared__ T ctab[kCamTab];
+    __shared__ double red[kWarps][54];
+    const T *__restrict__ camtab = (const T *)P.camtab;
+    const T delta = (T)P.delta;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = blockIdx.x; c < P.n_cchunks; c += gridDim.x) {
+        const int cam = P.cchunk_cam[c];
+        const int b0 = P.cchunk_beg[c], b1 = P.cchunk_beg[c + 1];
+        __syncthreads();
+        if (threadIdx.x < kCamTab) ctab[threadIdx.x] = camtab[(int64_t)cam * kCamTab + threadIdx.x];
+        __syncthreads();
+        T acc[54];
+#pragma unroll
+        for (int q = 0; q < 54; ++q) acc[q] = T(0);
+        for (int s = b0 + threadIdx.x; s < b1; s += kBlock) {
+            const int pt = P.cm_pt[s];
+            const double2 uv = P.cm_uv[s];
+            T e[2], Jc[18], Jp[6];
+            project<T, true>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+                             (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+            T rho, W;
+            loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+            const T sw = sqrt(W);
+#pragma unroll
+            for (int q = 0; q < 18; ++q) Jc[q] *= sw;
+            e[0] *= sw;
+            e[1] *= sw;
+            int idx = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = a; b < 9; ++b) acc[idx++] += Jc[a] * Jc[b] + Jc[9 + a] * Jc[9 + b];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[45 + a] -= Jc[a] * e[0] + Jc[9 + a] * e[1];
+        }
+#pragma unroll
+        for (int q = 0; q < 54; ++q) {
+            T v = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[wid][q] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 54) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+            P.cpart[54 * (int64_t)c + threadIdx.x] = s;
+        }
+    }
+}
+
+__global__ void cam_finalize_kernel(Prob P, const int32_t *__restrict__ cfirst, int force) {
+    if (!force && (P.st->done || !P.st->relin)) return;
+    const int64_t total = (int64_t)P.nc * 54;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / 54), q = (int)(t % 54);
+        double s = 0.0;
+        for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) s += P.cpart[54 * (int64_t)c + q];
+        if (q < 45) P.Hpp[45 * (int64_t)i + q] = s;
+        else P.v[9 * (int64_t)i + (q - 45)] = s;
+    }
+}
+
+// FP64 cost over the point-major observations; fixed grid and order.
+__global__ void __launch_bounds__(kBlock) cost_partial_kernel(Prob P, const double *__restrict__ pts,
+                                                               double *__restrict__ partial, int gate) {
+    __shared__ double sred[kWarps];
+    if (gate && P.st->done) return;
+    double acc = 0.0;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < P.n; o += (int64_t)gridDim.x * blockDim.x) {
+        const int cam = P.pm_cam[o], pt = P.pm_pt[o];
+        const double2 uv = P.pm_uv[o];
+        double e[2];
+        project<double, false>(P.camtab64 + (int64_t)cam * kCamTab, pts[3 * (int64_t)pt], pts[3 * (int64_t)pt + 1],
+                               pts[3 * (int64_t)pt + 2], uv.x, uv.y, e, nullptr, nullptr);
+        double rho, W;
+        loss_weight<double>(P.loss, P.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+        acc += rho;
+    }
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void cost_final_kernel(const double *__restrict__ partial, int nb, double *out, double *out2,
+                                  const DevState *st, int gate) {
+    __shared__ double sred[kWarps];
+    if (gate && st->done) return;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) {
+        *out = 0.5 * s;
+        if (out2) *out2 = 0.5 * s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) evaluate_slice_kernel(Prob P, const int32_t *__restrict__ ci,
+                                                                 const int32_t *__restrict__ pi,
+                                                                 const double2 *__restrict__ uvs, int64_t m,
+                                                                 double *__restrict__ eo, double *__restrict__ jco,
+                                                                 double *__restrict__ jpo) {
+    const T *__restrict__ camtab = (const T *)P.camtab;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int cam = ci[k], pt = pi[k];
+        const double2 uv = uvs[k];
+        T e[2], Jc[18], Jp[6];
+        project<T, true>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+                         (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+        eo[2 * k] = (double)e[0];
+        eo[2 * k + 1] = (double)e[1];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) jco[18 * k + q] = (double)Jc[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) jpo[6 * k + q] = (double)Jp[q];
+    }
+}
+
+}  // namespace
+
+int cost_grid(const Prob &P) { return (int)grid_for(P.n); }
+
+cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin, cudaStream_t s) {
+    const unsigned g = grid_for(P.nc, 128);
+    if (for_lin) {
+        if (P.fp32)
+            camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, nullptr, P.st, 1);
+        else
+            camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, nullptr, P.st, 1);
+    } else {
+        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, nullptr, P.camtab64, P.st, 2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaStream_t s) {
+    const unsigned g = grid_for(P.nc, 128);
+    if (P.fp32)
+        camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, P.camtab64, P.st, 0);
+    else
+        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, P.camtab64, P.st, 0);
+    return cudaGetLastError();
+}
+
+static bool g_attr_done[2] = {false, false};
+
+cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s) {
+    const int nb = 152 * 4;
+    if (P.fp32) {
+        const size_t sm = sizeof(float) * 9 * (size_t)P.cap;
+        if (!g_attr_done[0]) {
+            cudaFuncSetAttribute(lin_point_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 4 * 2048);
+            g_attr_done[0] = true;
+        }
+        lin_point_kernel<float><<<nb, kBlock, sm, s>>>(P, force);
+        lin_camera_kernel<float><<<nb, kBlock, 0, s>>>(P, force);
+    } else {
+        const size_t sm = sizeof(double) * 9 * (size_t)P.cap;
+        if (!g_attr_done[1]) {
+            cudaFuncSetAttribute(lin_point_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 8 * 2048);
+            g_attr_done[1] = true;
+        }
+        lin_point_kernel<double><<<nb, kBlock, sm, s>>>(P, force);
+        lin_camera_kernel<double><<<nb, kBlock, 0, s>>>(P, force);
+    }
+    cam_finalize_kernel<<<grid_for((int64_t)P.nc * 54), kBlock, 0, s>>>(P, cfirst, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, double *out, double *out2, int gate,
+                             cudaStream_t s) {
+    const int nb = cost_grid(P);
+    cost_partial_kernel<<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
+    cost_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, out, out2, P.st, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_t *pi, const double2 *uv, int64_t m,
+                                  double *e, double *jc, double *jp, cudaStream_t s) {
+    const unsigned g = grid_for(m);
+    if (P.fp32) evaluate_slice_kernel<float><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+    else evaluate_slice_kernel<double><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+    return cudaGetLastError();
+}
+
+}  // namespace mba

@@ -1,0 +1,315 @@
+// mba_internal.cuh -- device data layout, camera model and shared device helpers
+// of the GB300 bundle-adjustment library.  Everything here is internal to
+// libmba.so; the public interface is include/mba.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cfloat>
+
+#include "../../include/mba.h"
+
+namespace mba {
+
+constexpr int kBlock = 256;          // threads per CTA for every kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kCamTab = 28;          // values per camera in the camera table
+constexpr int kVec = 12;             // padded stride of 9-vectors per camera (16-B aligned rows)
+constexpr int kCamChunk = 1024;      // observations per camera-major chunk
+constexpr int kMaxTrack = 1024;      // longest supported point track
+
+// Device-resident LM / PCG control state.  All LM decisions are made on the
+// device so a whole solve is issued without host round trips.
+struct DevState {
+    double radius, factor, mu;
+    double cost;          // F(x) at the current parameters
+    double initial_cost;
+    double cost_new, model_dec, gain;
+    double pcg_rel_res;
+    double mu_override;   // >= 0: use this mu instead of 1/radius
+    int32_t relin;        // 1: the linearisation must be rebuilt before the next solve
+    int32_t accepted;     // decision of the last iteration
+    int32_t done;         // 1: stop issuing work (function_tol met or error)
+    int32_t iter;
+    int32_t err;          // mba_status raised on the device
+    int32_t pcg_iters;
+    int32_t accepted_total, pcg_total;
+    uint32_t barrier;     // arrival counter of the persistent kernel's grid barrier
+    int32_t pad;
+};
+
+// Everything a kernel needs, as plain device pointers.  Sized at creation.
+struct Prob {
+    int32_t nc, np;
+    int64_t n, npad;       // observations, padded stride of SoA arrays
+    int32_t fp32;          // 1: FP32-mixed
+    int32_t loss;
+    double delta;
+    int32_t cap;           // max observations in a point chunk (smem slots)
+    int32_t n_pchunks, n_cchunks;
+
+    // parameters (FP64, row-major)
+    double *cams, *pts;            // current
+    double *cams_new, *pts_new;    // candidate
+    double *cams0, *pts0;          // as given at creation
+
+    // observations, point-major order (stable by point, then input index)
+    int32_t *pm_cam, *pm_pt, *pm_orig;
+    double2 *pm_uv;
+    int32_t *pt_ptr;               // np + 1
+    // observations, camera-major order
+    int32_t *cm_pt, *cm_orig;
+    double2 *cm_uv;
+    int32_t *cam_ptr;              // nc + 1
+    // chunk tables
+    int32_t *pchunk;               // n_pchunks + 1 point indices
+    int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
+
+    // per-linearisation data (T = float in FP32-mixed, double otherwise)
+    void *J;        // [24][npad] sqrt(W)-scaled Jacobian, point-major
+    void *res;      // [2][npad]  sqrt(W)-scaled residual
+    void *camtab;   // [nc][kCamTab] camera table in T (lin kernels)
+    double *camtab64;  // [nc][kCamTab] FP64 camera table (cost evaluation)
+    double *Hpp;    // [nc][45] packed upper triangle of B
+    double *v;      // [nc][9]
+    double *Hll;    // [np][6] packed upper triangle of C
+    double *w;      // [np][3]
+    double *cpart;  // [n_cchunks][54] camera-chunk partial sums
+    // per-solve data
+    double *Bd;     // [nc][81] damped B~
+    double *Binv;   // [nc][81] inverse of B~ (block-Jacobi preconditioner)
+    void *Cinv;     // [np][6] packed inverse of damped C~, T
+    // PCG vectors, [nc][kVec] FP64
+    double *x, *r, *z, *p, *q, *g;
+    void *pT;       // [nc][kVec] search direction in T
+    void *cacc;     // 2 x [nc][kVec] camera accumulators in T
+    double *dp;     // [np][3] point step
+    double *red;    // reduction partials: per-CTA p.q, r.z and r.r of the persistent kernel
+    int32_t red_len;
+    DevState *st;
+    mba_iteration *trace;  // device trace, max_iter entries (set per solve)
+    int32_t trace_cap;
+};
+
+// ---------------------------------------------------------------------------
+// packed symmetric indexing
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int sym9(int a, int b) {
+    if (a > b) { int t = a; a = b; b = t; }
+    return a * 9 - (a * (a - 1)) / 2 + (b - a);
+}
+__host__ __device__ __forceinline__ int sym3(int a, int b) {
+    if (a > b) { int t = a; a = b; b = t; }
+    return a * 3 - (a * (a - 1)) / 2 + (b - a);
+}
+
+// ---------------------------------------------------------------------------
+// BAL camera model.  Per camera (once per linearisation) the rotation R(w) and
+// the factor M of dP/dw = -R [X]_x M, M = (w w^T + (R^T - I)[w]_x) / |w|^2
+// (Gallego & Yezzi 2015) are tabulated in FP64; for |w|^2 <= DBL_EPSILON the
+// first-order form P = X + w x X + t is used (R = I + [w]_x, dP/dw = -[X]_x).
+// Table row: R[9] M[9] t[3] f k1 k2 small pad...
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void camera_table_row(const double *c, double *o) {
+    const double w0 = c[0], w1 = c[1], w2 = c[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double R[9], M[9];
+    double small;
+    if (th2 > DBL_EPSILON) {
+        const double th = sqrt(th2);
+        double s, co;
+        sincos(th, &s, &co);
+        const double k0 = w0 / th, k1 = w1 / th, k2 = w2 / th;
+        const double oc = 1.0 - co;
+        R[0] = co + oc * k0 * k0;      R[1] = -s * k2 + oc * k0 * k1; R[2] = s * k1 + oc * k0 * k2;
+        R[3] = s * k2 + oc * k1 * k0;  R[4] = co + oc * k1 * k1;      R[5] = -s * k0 + oc * k1 * k2;
+        R[6] = -s * k1 + oc * k2 * k0; R[7] = s * k0 + oc * k2 * k1;  R[8] = co + oc * k2 * k2;
+        // (R^T - I) [w]_x, then add w w^T and divide by th^2
+        const double A[9] = {R[0] - 1.0, R[3], R[6], R[1], R[4] - 1.0, R[7], R[2], R[5], R[8] - 1.0};
+        const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+        const double wv[3] = {w0, w1, w2};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double acc = A[i * 3 + 0] * W[0 * 3 + j] + A[i * 3 + 1] * W[1 * 3 + j] + A[i * 3 + 2] * W[2 * 3 + j];
+                M[i * 3 + j] = (acc + wv[i] * wv[j]) / th2;
+            }
+        small = 0.0;
+    } else {
+        R[0] = 1.0; R[1] = -w2; R[2] = w1;
+        R[3] = w2;  R[4] = 1.0; R[5] = -w0;
+        R[6] = -w1; R[7] = w0;  R[8] = 1.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) M[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        small = 1.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { o[i] = R[i]; o[9 + i] = M[i]; }
+    o[18] = c[3]; o[19] = c[4]; o[20] = c[5];
+    o[21] = c[6]; o[22] = c[7]; o[23] = c[8];
+    o[24] = small; o[25] = 0.0; o[26] = 0.0; o[27] = 0.0;
+}
+
+// Residual e = pi(c, X) - u and, if JAC, the analytic Jacobians Jc (2x9, row
+// major: w, t, f, k1, k2) and Jp (2x3) by the chain rule, in precision T.
+template <typename T, bool JAC>
+__device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T X2, T u0, T u1, T *e, T *Jc,
+                                        T *Jp) {
+    const T R0 = ct[0], R1 = ct[1], R2 = ct[2], R3 = ct[3], R4 = ct[4], R5 = ct[5], R6 = ct[6], R7 = ct[7],
+            R8 = ct[8];
+    const T P0 = R0 * X0 + R1 * X1 + R2 * X2 + ct[18];
+    const T P1 = R3 * X0 + R4 * X1 + R5 * X2 + ct[19];
+    const T P2 = R6 * X0 + R7 * X1 + R8 * X2 + ct[20];
+    const T iz = T(1) / P2;
+    const T px = -P0 * iz, py = -P1 * iz;
+    const T f = ct[21], k1 = ct[22], k2 = ct[23];
+    const T r2 = px * px + py * py;
+    const T d = T(1) + k1 * r2 + k2 * r2 * r2;
+    e[0] = f * d * px - u0;
+    e[1] = f * d * py - u1;
+    if (!JAC) return;
+    const T dd = T(2) * k1 + T(4) * k2 * r2;
+    // A = d(pixel)/dp = f (d I + dd p p^T); D = A dp/dP
+    const T a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
+    T D[6];
+    D[0] = -a00 * iz; D[1] = -a01 * iz; D[2] = -(a00 * px + a01 * py) * iz;
+    D[3] = -a01 * iz; D[4] = -a11 * iz; D[5] = -(a01 * px + a11 * py) * iz;
+    // Jp = D R
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        Jp[r * 3 + 0] = D[r * 3] * R0 + D[r * 3 + 1] * R3 + D[r * 3 + 2] * R6;
+        Jp[r * 3 + 1] = D[r * 3] * R1 + D[r * 3 + 1] * R4 + D[r * 3 + 2] * R7;
+        Jp[r * 3 + 2] = D[r * 3] * R2 + D[r * 3 + 1] * R5 + D[r * 3 + 2] * R8;
+    }
+    const bool small = ct[24] != T(0);
+    // rotation block: row r = (X x b_r)^T M with b = D R (or D in the first-order branch)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const T b0 = small ? D[r * 3] : Jp[r * 3];
+        const T b1 = small ? D[r * 3 + 1] : Jp[r * 3 + 1];
+        const T b2 = small ? D[r * 3 + 2] : Jp[r * 3 + 2];
+        const T v0 = X1 * b2 - X2 * b1, v1 = X2 * b0 - X0 * b2, v2 = X0 * b1 - X1 * b0;
+        Jc[r * 9 + 0] = v0 * ct[9] + v1 * ct[12] + v2 * ct[15];
+        Jc[r * 9 + 1] = v0 * ct[10] + v1 * ct[13] + v2 * ct[16];
+        Jc[r * 9 + 2] = v0 * ct[11] + v1 * ct[14] + v2 * ct[17];
+        Jc[r * 9 + 3] = D[r * 3];
+        Jc[r * 9 + 4] = D[r * 3 + 1];
+        Jc[r * 9 + 5] = D[r * 3 + 2];
+        const T pr = r == 0 ? px : py;
+        Jc[r * 9 + 6] = d * pr;
+        Jc[r * 9 + 7] = f * r2 * pr;
+        Jc[r * 9 + 8] = f * r2 * r2 * pr;
+    }
+}
+
+// Loss: rho(s) and IRLS weight rho'(s).  Plain: s, 1.  Huber: s, 1 for
+// s <= delta^2, else 2 delta sqrt(s) - delta^2, delta / sqrt(s).
+template <typename T>
+__device__ __forceinline__ void loss_weight(int loss, T delta, T s, T *rho, T *weight) {
+    if (loss == MBA_LOSS_HUBER && s > delta * delta) {
+        const T r = sqrt(s);
+        *rho = T(2) * delta * r - delta * delta;
+        *weight = delta / r;
+    } else {
+        *rho = s;
+        *weight = T(1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2-coherent loads/stores for data that other CTAs write inside the same
+// persistent launch (L1 is not coherent across SMs).
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+template <typename T> __device__ __forceinline__ void stcg(T *p, T v) { __stcg(p, v); }
+
+// Block-wide sum of one double per thread in a fixed tree order; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sbuf /* >= kWarps */) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWarps; ++i) s += sbuf[i];
+    }
+    return s;
+}
+
+// Bounded grid barrier for cooperative (co-resident) launches.  Arrivals
+// increment a monotone counter; the k-th barrier completes when it reaches
+// k * gridDim.x.  A CTA that polls more than `limit` times, or sees the error
+// flag raised, records MBA_ERR_TIMEOUT and returns false; the caller must
+// then leave the kernel.  Returns true when every CTA has arrived.
+__device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    epoch += 1;
+    if (threadIdx.x == 0) {
+        const uint32_t target = epoch * gridDim.x;
+        __threadfence();
+        unsigned int *ctr = reinterpret_cast<unsigned int *>(&st->barrier);
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        long long polls = 0;
+        for (;;) {
+            unsigned int seen;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
+            if ((int)(seen - target) >= 0) break;
+            int e;
+            asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(&st->err) : "memory");
+            if (e != 0 || ++polls > limit) {
+                atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// sort.cu
+cudaError_t stable_sort_by_key(const int32_t *keys_in, int64_t n, int32_t nkeys, int32_t *perm_out,
+                               int32_t *ptr_out, void *tmp, size_t tmp_bytes, cudaStream_t s);
+size_t stable_sort_tmp_bytes(int64_t n, int32_t nkeys);
+cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, int32_t np, const double *obs,
+                            const int32_t *ci, const int32_t *pi, int64_t n, int32_t *flags, cudaStream_t s);
+cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
+                          int32_t *tmp_i, cudaStream_t s);
+cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s);
+
+// linearize.cu
+cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin, cudaStream_t s);
+cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaStream_t s);
+cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s);
+cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, double *out, double *out2, int gate,
+                             cudaStream_t s);
+int cost_grid(const Prob &P);
+cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_t *pi, const double2 *uv, int64_t m,
+                                  double *e, double *jc, double *jp, cudaStream_t s);
+
+// pcg.cu
+enum PcgMode { PCG_SOLVE = 0, PCG_RHS_ONLY = 1, PCG_MATVEC = 2 };
+cudaError_t launch_damp(const Prob &P, int damping, cudaStream_t s);
+cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
+                       cudaStream_t s);
+int pcg_grid_size(const Prob &P);
+cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s);
+
+// lm.cu
+cudaError_t launch_state_init(const Prob &P, double radius, double mu_override, int keep_cost, cudaStream_t s);
+cudaError_t launch_lm_update(const Prob &P, const mba_solver_options &o, cudaStream_t s);
+cudaError_t launch_accept(const Prob &P, cudaStream_t s);
+
+}  // namespace mba

@@ -1,0 +1,337 @@
+"""Python binding of the C ABI in include/mba.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arrays and structures; all computation runs in the CUDA
+kernels of ``_build/libmba.so``.  There is no fallback: if the library is not
+built, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+MBA_OK, MBA_ERR_INVALID_ARG, MBA_ERR_OOM, MBA_ERR_CUDA = 0, 1, 2, 3
+MBA_ERR_NONFINITE, MBA_ERR_TIMEOUT, MBA_ERR_NOT_CONVERGED = 4, 5, 6
+MBA_FP64, MBA_FP32_MIXED = 0, 1
+MBA_LOSS_NONE, MBA_LOSS_HUBER = 0, 1
+MBA_DAMP_DIAG, MBA_DAMP_IDENTITY = 0, 1
+
+PRECISION = {"fp64": MBA_FP64, "fp32": MBA_FP32_MIXED, "fp32_mixed": MBA_FP32_MIXED}
+LOSS = {"none": MBA_LOSS_NONE, "huber": MBA_LOSS_HUBER}
+DAMPING = {"diag": MBA_DAMP_DIAG, "identity": MBA_DAMP_IDENTITY}
+
+
+class MbaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+class ProblemOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("loss", C.c_int32), ("huber_delta", C.c_double),
+                ("cuda_stream", C.c_void_p)]
+
+
+class SolverOptions(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("pcg_max_iter", C.c_int32), ("pcg_rel_tol", C.c_double),
+                ("damping", C.c_int32), ("initial_radius", C.c_double), ("min_relative_decrease", C.c_double),
+                ("function_tol", C.c_double), ("barrier_spin_limit", C.c_int64), ("collect_timing", C.c_int32)]
+
+
+class Iteration(C.Structure):
+    _fields_ = [("cost", C.c_double), ("cost_new", C.c_double), ("model_decrease", C.c_double),
+                ("mu", C.c_double), ("gain", C.c_double), ("accepted", C.c_int32), ("pcg_iters", C.c_int32),
+                ("pcg_rel_residual", C.c_double)]
+
+
+class Summary(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("pcg_iters_total", C.c_int32),
+                ("status", C.c_int32), ("initial_cost", C.c_double), ("final_cost", C.c_double),
+                ("final_mu", C.c_double), ("final_radius", C.c_double), ("ms_total", C.c_double),
+                ("ms_linearize", C.c_double), ("ms_pcg", C.c_double), ("ms_other", C.c_double),
+                ("trace", C.POINTER(Iteration)), ("trace_capacity", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmba.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first (__graft_entry__.build())")
+        lib = C.CDLL(_build.LIB)
+        P, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "mba_problem_options_default": (None, [P]),
+            "mba_solver_options_default": (None, [P]),
+            "mba_problem_create": (C.c_int, [P, i32, P, i32, P, P, P, i64, P, P]),
+            "mba_problem_destroy": (None, [P]),
+            "mba_problem_info": (C.c_int, [P, P, P, P, P]),
+            "mba_evaluate": (C.c_int, [P, P, P, P, P]),
+            "mba_solve": (C.c_int, [P, P, P]),
+            "mba_get_parameters": (C.c_int, [P, P, P]),
+            "mba_set_parameters": (C.c_int, [P, P, P]),
+            "mba_reset": (C.c_int, [P]),
+            "mba_get_ordering": (C.c_int, [P, P, P, P, P]),
+            "mba_linear_system": (C.c_int, [P, dbl, i32, P, P, P, P, P]),
+            "mba_schur_matvec": (C.c_int, [P, dbl, i32, P, P]),
+            "mba_step": (C.c_int, [P, dbl, P, P, P, P, P]),
+            "mba_status_string": (C.c_char_p, [C.c_int]),
+            "mba_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().mba_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover
+        return f"status {status}"
+
+
+def _check(status: int):
+    if status != MBA_OK:
+        raise MbaError(status, load().mba_last_error().decode())
+
+
+def _ptr(a, dtype):
+    """Host pointer of a contiguous numpy array or CPU torch tensor of the given dtype."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+
+        want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.is_cuda or a.dtype != want or not a.is_contiguous():
+            raise ValueError("host tensor must be a contiguous CPU tensor of the right dtype")
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(C.c_void_p), arr
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def mba_problem_options_default() -> ProblemOptions:
+    o = ProblemOptions()
+    load().mba_problem_options_default(C.byref(o))
+    return o
+
+
+def mba_solver_options_default() -> SolverOptions:
+    o = SolverOptions()
+    load().mba_solver_options_default(C.byref(o))
+    return o
+
+
+def mba_problem_create(cameras, points, observations, cam_idx, pt_idx, precision="fp64", loss="none",
+                       huber_delta=0.0, stream=None) -> C.c_void_p:
+    lib = load()
+    pc, ac = _ptr(cameras, np.float64)
+    pp, ap = _ptr(points, np.float64)
+    po, ao = _ptr(observations, np.float64)
+    pci, aci = _ptr(cam_idx, np.int32)
+    ppi, api = _ptr(pt_idx, np.int32)
+    nc, np_ = int(len(ac)), int(len(ap))
+    n = int(len(ao))
+    if int(np.prod(ac.shape)) != 9 * nc or int(np.prod(ap.shape)) != 3 * np_ or int(np.prod(ao.shape)) != 2 * n:
+        raise ValueError("cameras must be (nc, 9), points (np, 3), observations (n, 2)")
+    if len(aci) != n or len(api) != n:
+        raise ValueError("cam_idx and pt_idx must have one entry per observation")
+    o = mba_problem_options_default()
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
+    o.huber_delta = float(huber_delta)
+    o.cuda_stream = _stream_handle(stream)
+    h = C.c_void_p()
+    _check(lib.mba_problem_create(pc, nc, pp, np_, po, pci, ppi, n, C.byref(o), C.byref(h)))
+    return h
+
+
+def mba_problem_destroy(h):
+    if h:
+        load().mba_problem_destroy(h)
+
+
+def mba_problem_info(h):
+    nc, np_, n, b = C.c_int32(), C.c_int32(), C.c_int64(), C.c_size_t()
+    _check(load().mba_problem_info(h, C.byref(nc), C.byref(np_), C.byref(n), C.byref(b)))
+    return dict(nc=nc.value, np=np_.value, n=n.value, device_bytes=b.value)
+
+
+def mba_evaluate(h, residuals=True, jacobians=True):
+    info = mba_problem_info(h)
+    n = info["n"]
+    cost = C.c_double()
+    e = np.zeros((n, 2)) if residuals else None
+    jc = np.zeros((n, 2, 9)) if jacobians else None
+    jp = np.zeros((n, 2, 3)) if jacobians else None
+    f = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(load().mba_evaluate(h, C.byref(cost), f(e), f(jc), f(jp)))
+    return cost.value, e, jc, jp
+
+
+def solver_options(**kw) -> SolverOptions:
+    o = mba_solver_options_default()
+    for k, v in kw.items():
+        if k == "damping" and isinstance(v, str):
+            v = DAMPING[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown solver option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def mba_solve(h, trace_capacity=0, **opts):
+    o = solver_options(**opts)
+    s = Summary()
+    tr = None
+    if trace_capacity > 0:
+        tr = (Iteration * trace_capacity)()
+        s.trace = C.cast(tr, C.POINTER(Iteration))
+        s.trace_capacity = trace_capacity
+    st = load().mba_solve(h, C.byref(o), C.byref(s))
+    out = {f: getattr(s, f) for f, _ in Summary._fields_ if f not in ("trace", "trace_capacity")}
+    if tr is not None:
+        out["trace"] = [{f: getattr(tr[i], f) for f, _ in Iteration._fields_}
+                        for i in range(min(s.iterations, trace_capacity))]
+    _check(st)
+    return out
+
+
+def mba_get_parameters(h, cameras=None, points=None):
+    info = mba_problem_info(h)
+    cams = np.zeros((info["nc"], 9)) if cameras is None else cameras
+    pts = np.zeros((info["np"], 3)) if points is None else points
+    pc, _ = _ptr(cams, np.float64)
+    pp, _ = _ptr(pts, np.float64)
+    _check(load().mba_get_parameters(h, pc, pp))
+    return cams, pts
+
+
+def mba_set_parameters(h, cameras=None, points=None):
+    pc, ac = _ptr(cameras, np.float64)
+    pp, ap = _ptr(points, np.float64)
+    _check(load().mba_set_parameters(h, pc, pp))
+
+
+def mba_reset(h):
+    _check(load().mba_reset(h))
+
+
+def mba_get_ordering(h):
+    info = mba_problem_info(h)
+    n, nc, np_ = info["n"], info["nc"], info["np"]
+    pt_perm, pt_ptr = np.zeros(n, np.int32), np.zeros(np_ + 1, np.int32)
+    cam_perm, cam_ptr = np.zeros(n, np.int32), np.zeros(nc + 1, np.int32)
+    f = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(load().mba_get_ordering(h, f(pt_perm), f(pt_ptr), f(cam_perm), f(cam_ptr)))
+    return pt_perm, pt_ptr, cam_perm, cam_ptr
+
+
+def mba_linear_system(h, mu, damping="diag"):
+    info = mba_problem_info(h)
+    nc, np_ = info["nc"], info["np"]
+    Hpp, v = np.zeros((nc, 9, 9)), np.zeros((nc, 9))
+    Hll, w = np.zeros((np_, 3, 3)), np.zeros((np_, 3))
+    rhs = np.zeros((nc, 9))
+    f = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(load().mba_linear_system(h, float(mu), DAMPING[damping], f(Hpp), f(v), f(Hll), f(w), f(rhs)))
+    return dict(Hpp=Hpp, v=v, Hll=Hll, w=w, rhs=rhs)
+
+
+def mba_schur_matvec(h, mu, x, damping="diag"):
+    info = mba_problem_info(h)
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(info["nc"], 9)
+    y = np.zeros_like(xx)
+    _check(load().mba_schur_matvec(h, float(mu), DAMPING[damping], xx.ctypes.data_as(C.c_void_p),
+                                   y.ctypes.data_as(C.c_void_p)))
+    return y
+
+
+def mba_step(h, mu, **opts):
+    info = mba_problem_info(h)
+    o = solver_options(**opts)
+    dc, dp = np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
+    it, md = C.c_int32(), C.c_double()
+    _check(load().mba_step(h, float(mu), C.byref(o), dc.ctypes.data_as(C.c_void_p), dp.ctypes.data_as(C.c_void_p),
+                           C.byref(it), C.byref(md)))
+    return dict(dc=dc, dp=dp, pcg_iters=it.value, model_dec=md.value)
+
+
+class Problem:
+    """Owning wrapper over one mba_problem handle."""
+
+    def __init__(self, cameras, points, observations, cam_idx, pt_idx, precision="fp64", loss="none",
+                 huber_delta=0.0, stream=None):
+        self.handle = mba_problem_create(cameras, points, observations, cam_idx, pt_idx, precision, loss,
+                                         huber_delta, stream)
+        self.info = mba_problem_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            mba_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def evaluate(self, residuals=True, jacobians=True):
+        return mba_evaluate(self.handle, residuals, jacobians)
+
+    def solve(self, trace_capacity=0, **opts):
+        return mba_solve(self.handle, trace_capacity, **opts)
+
+    def parameters(self):
+        return mba_get_parameters(self.handle)
+
+    def set_parameters(self, cameras=None, points=None):
+        mba_set_parameters(self.handle, cameras, points)
+
+    def reset(self):
+        mba_reset(self.handle)
+
+    def ordering(self):
+        return mba_get_ordering(self.handle)
+
+    def linear_system(self, mu, damping="diag"):
+        return mba_linear_system(self.handle, mu, damping)
+
+    def schur_matvec(self, mu, x, damping="diag"):
+        return mba_schur_matvec(self.handle, mu, x, damping)
+
+    def step(self, mu, **opts):
+        return mba_step(self.handle, mu, **opts)

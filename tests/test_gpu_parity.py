@@ -1,0 +1,219 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: index work bit-exact; FP64 residuals/Jacobians 1e-9 relative;
+FP64 blocks and Schur products 1e-9 per parameter column; final cost after a
+fixed number of LM iterations 1e-6 (FP64) and 1e-4 (FP32-mixed) relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from scenes import config_scene, make_scene
+from tests.gpu_util import rel_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mba():
+    from paper_2112_01349_gb300 import _build, mba as m
+
+    _build.build()
+    m.load()
+    return m
+
+
+def _scene(kind):
+    if kind == "small":
+        return make_scene(6, 400, sigma=0.5, seed=21)
+    if kind == "ragged":  # many point chunks, geometric tracks, ragged tail
+        return make_scene(40, 9001, track=("geom", 0.25), sigma=1.0, seed=22)
+    if kind == "huber":
+        return make_scene(12, 3001, track=("geom", 0.25), sigma=1.0, outlier_frac=0.05, seed=23)
+    if kind == "cfg1":
+        return config_scene(1)
+    if kind == "longtrack":  # heavy-tailed tracks up to 300 observations
+        return make_scene(320, 3000, track=("lognormal", 6.5, 300), sigma=1.0, seed=24)
+    raise KeyError(kind)
+
+
+def _problem(m, sc, precision="fp64", loss="none", delta=0.0):
+    return m.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision, loss=loss,
+                     huber_delta=delta)
+
+
+def _colwise(got, ref, rtol, what):
+    got, ref = np.asarray(got).reshape(-1, got.shape[-1]), np.asarray(ref).reshape(-1, ref.shape[-1])
+    for a in range(ref.shape[1]):
+        rel_close(got[:, a], ref[:, a], rtol, f"{what}[:, {a}]")
+
+
+@pytest.mark.parametrize("kind", ["small", "ragged", "longtrack"])
+def test_ordering_is_bit_exact(mba, kind):
+    sc = _scene(kind)
+    with _problem(mba, sc) as pr:
+        pt_perm, pt_ptr, cam_perm, cam_ptr = pr.ordering()
+    rp, rpp = oracle.stable_sort(sc.pt_idx, sc.np_)
+    rc, rcp = oracle.stable_sort(sc.cam_idx, sc.nc)
+    np.testing.assert_array_equal(pt_perm, rp)
+    np.testing.assert_array_equal(pt_ptr, rpp)
+    np.testing.assert_array_equal(cam_perm, rc)
+    np.testing.assert_array_equal(cam_ptr, rcp)
+
+
+@pytest.mark.parametrize("kind", ["small", "ragged"])
+def test_evaluate_fp64(mba, kind):
+    sc = _scene(kind)
+    with _problem(mba, sc) as pr:
+        cost, e, jc, jp = pr.evaluate()
+    rcost, re, rjc, rjp, _ = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    assert cost == pytest.approx(rcost, rel=1e-12)
+    rel_close(e, re, 1e-9, "residual")
+    _colwise(jc.reshape(-1, 9), rjc.reshape(-1, 9), 1e-9, "Jc")
+    _colwise(jp.reshape(-1, 3), rjp.reshape(-1, 3), 1e-9, "Jp")
+
+
+def test_evaluate_fp32_mixed(mba):
+    sc = _scene("ragged")
+    with _problem(mba, sc, "fp32") as pr:
+        cost, e, jc, jp = pr.evaluate()
+    rcost, re, rjc, rjp, _ = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    assert cost == pytest.approx(rcost, rel=1e-12)  # the cost is FP64 in both forms
+    rel_close(e, re, 1e-4, "residual")
+    _colwise(jc.reshape(-1, 9), rjc.reshape(-1, 9), 1e-4, "Jc")
+    _colwise(jp.reshape(-1, 3), rjp.reshape(-1, 3), 1e-4, "Jp")
+
+
+@pytest.mark.parametrize("kind,loss", [("small", "none"), ("ragged", "none"), ("huber", "huber")])
+def test_linear_system_fp64(mba, kind, loss):
+    sc = _scene(kind)
+    mu = 1e-3
+    with _problem(mba, sc, loss=loss, delta=2.0) as pr:
+        ls = pr.linear_system(mu)
+    Hpp, v, Hll, w = oracle.blocks(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0)
+    rhs = oracle.schur(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, loss=loss,
+                       delta=2.0)["rhs"].reshape(-1, 9)
+    _colwise(ls["Hpp"].reshape(-1, 9), Hpp.reshape(-1, 9), 1e-9, "Hpp")
+    _colwise(ls["v"], v, 1e-9, "v")
+    _colwise(ls["Hll"].reshape(-1, 3), Hll.reshape(-1, 3), 1e-9, "Hll")
+    _colwise(ls["w"], w, 1e-9, "w")
+    _colwise(ls["rhs"], rhs, 1e-8, "rhs")
+
+
+@pytest.mark.parametrize("kind,damping", [("small", "diag"), ("ragged", "diag"), ("ragged", "identity"),
+                                          ("longtrack", "diag")])
+def test_schur_matvec_fp64(mba, kind, damping):
+    sc = _scene(kind)
+    mu = 1e-2
+    x = np.random.default_rng(5).normal(size=(sc.nc, 9))
+    with _problem(mba, sc) as pr:
+        y = pr.schur_matvec(mu, x, damping)
+    ref = oracle.schur(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, x=x.reshape(-1),
+                       damping=damping)["y"].reshape(-1, 9)
+    _colwise(y, ref, 1e-9, "Sx")
+
+
+def test_schur_matvec_fp32_mixed(mba):
+    sc = _scene("ragged")
+    mu = 1e-2
+    x = np.random.default_rng(6).normal(size=(sc.nc, 9))
+    with _problem(mba, sc, "fp32") as pr:
+        y = pr.schur_matvec(mu, x)
+    ref = oracle.schur(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu,
+                       x=x.reshape(-1))["y"].reshape(-1, 9)
+    rel_close(y, ref, 1e-4, "Sx fp32")
+
+
+@pytest.mark.parametrize("kind", ["small", "ragged"])
+def test_step_fp64(mba, kind):
+    sc = _scene(kind)
+    mu = 1e-3
+    with _problem(mba, sc) as pr:
+        st = pr.step(mu, pcg_max_iter=40, pcg_rel_tol=1e-10)
+    ref = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, pcg_max=40, pcg_tol=1e-10)
+    assert st["pcg_iters"] == ref["pcg_iters"]
+    _colwise(st["dc"], ref["dc"], 1e-6, "dc")
+    _colwise(st["dp"], ref["dp"], 1e-6, "dp")
+    assert st["model_dec"] == pytest.approx(ref["model_dec"], rel=1e-6)
+
+
+@pytest.mark.parametrize("kind,loss,iters,pcg", [("cfg1", "none", 10, 50), ("ragged", "none", 6, 40),
+                                                 ("huber", "huber", 6, 40), ("longtrack", "none", 5, 30)])
+def test_solve_fp64_final_cost(mba, kind, loss, iters, pcg):
+    sc = _scene(kind)
+    ref = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=iters, pcg_max=pcg,
+                          loss=loss, delta=2.0)
+    with _problem(mba, sc, loss=loss, delta=2.0) as pr:
+        s = pr.solve(trace_capacity=iters, max_iter=iters, pcg_max_iter=pcg)
+        cams, pts = pr.parameters()
+    assert s["iterations"] == iters
+    assert s["initial_cost"] == pytest.approx(ref["trace"][0]["cost"], rel=1e-12)
+    assert s["final_cost"] == pytest.approx(ref["final_cost"], rel=1e-6)
+    # the early, decisive iterations follow the same trajectory
+    for t, r in list(zip(s["trace"], ref["trace"]))[:3]:
+        assert t["accepted"] == r["accepted"]
+        assert t["cost_new"] == pytest.approx(r["cost_new"], rel=1e-6)
+    # the returned parameters carry the reported cost
+    rc = oracle.evaluate(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0, jacobians=False)[0]
+    assert rc == pytest.approx(s["final_cost"], rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,loss", [("cfg1", "none"), ("huber", "huber")])
+def test_solve_fp32_mixed_final_cost(mba, kind, loss):
+    sc = _scene(kind)
+    ref = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=10, pcg_max=50,
+                          loss=loss, delta=2.0)
+    with _problem(mba, sc, "fp32", loss=loss, delta=2.0) as pr:
+        s = pr.solve(max_iter=10, pcg_max_iter=50)
+    assert s["final_cost"] == pytest.approx(ref["final_cost"], rel=1e-4)
+
+
+def test_degenerate_minimal_problem(mba):
+    # two cameras, one point each seen once or twice: singular undamped blocks, damping makes them definite
+    cams = np.array([[0.1, -0.2, 0.05, 0.0, 0.0, -5.0, 800.0, 0.0, 0.0],
+                     [-0.05, 0.1, 0.0, 0.2, 0.0, -6.0, 900.0, 0.01, 0.0]])
+    pts = np.array([[0.1, 0.2, -0.1], [0.0, -0.1, 0.3], [0.2, 0.0, 0.0]])
+    cam_idx = np.array([0, 1, 0, 1], np.int32)
+    pt_idx = np.array([0, 0, 1, 2], np.int32)
+    obs = np.array([oracle.project(cams[c], pts[p]) for c, p in zip(cam_idx, pt_idx)]) + 0.5
+    ref = oracle.lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=4, pcg_max=20)
+    with mba.Problem(cams, pts, obs, cam_idx, pt_idx) as pr:
+        s = pr.solve(max_iter=4, pcg_max_iter=20)
+    assert s["final_cost"] == pytest.approx(ref["final_cost"], rel=1e-6, abs=1e-12)
+
+
+def test_invalid_inputs_are_rejected(mba):
+    sc = _scene("small")
+    bad = sc.cam_idx.copy()
+    bad[3] = sc.nc
+    with pytest.raises(mba.MbaError) as ei:
+        mba.Problem(sc.cameras, sc.points, sc.observations, bad, sc.pt_idx)
+    assert ei.value.status == mba.MBA_ERR_INVALID_ARG
+    obs = sc.observations.copy()
+    obs[7, 1] = np.nan
+    with pytest.raises(mba.MbaError) as ei:
+        mba.Problem(sc.cameras, sc.points, obs, sc.cam_idx, sc.pt_idx)
+    assert ei.value.status == mba.MBA_ERR_NONFINITE
+    # an extra camera nobody observes
+    cams = np.concatenate([sc.cameras, sc.cameras[:1]])
+    with pytest.raises(mba.MbaError) as ei:
+        mba.Problem(cams, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    assert ei.value.status == mba.MBA_ERR_INVALID_ARG
+
+
+def test_track_longer_than_supported_is_rejected(mba):
+    sc = make_scene(1100, 2, track=("fixed", 1100), sigma=1.0, seed=3)
+    with pytest.raises(mba.MbaError) as ei:
+        mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    assert ei.value.status == mba.MBA_ERR_INVALID_ARG
+
+
+def test_barrier_timeout_returns_status_and_context_survives(mba):
+    sc = _scene("ragged")
+    with _problem(mba, sc) as pr:
+        with pytest.raises(mba.MbaError) as ei:
+            pr.solve(max_iter=2, pcg_max_iter=10, barrier_spin_limit=1)
+        assert ei.value.status == mba.MBA_ERR_TIMEOUT
+        pr.reset()
+        s = pr.solve(max_iter=2, pcg_max_iter=10)
+        assert s["status"] == 0 and s["iterations"] == 2
