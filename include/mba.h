@@ -100,6 +100,7 @@ typedef struct {
     double ms_linearize;       /* residual/Jacobian/Hessian-block kernels */
     double ms_pcg;             /* persistent PCG kernel (incl. Schur right-hand side) */
     double ms_other;           /* damping, back-substitution, cost, LM control */
+    int32_t kernel_launches;   /* CUDA kernels this solve launched (gated-off ones included) */
     mba_iteration *trace;      /* optional caller buffer of trace_capacity entries (host) */
     int32_t trace_capacity;
 } mba_summary;

@@ -157,9 +157,10 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.pts = c.take<double>(3 * (size_t)np);
         P.pts_new = c.take<double>(3 * (size_t)np);
         P.pts0 = c.take<double>(3 * (size_t)np);
-        P.pm_cam = c.take<int32_t>(n);
+        P.pm_cam = c.take<int32_t>(n + 64);  // slack for 16-byte-rounded bulk copies
         P.pm_pt = c.take<int32_t>(n);
         P.pm_orig = c.take<int32_t>(n);
+        P.pm_pc = c.take<int2>(n);
         P.pm_uv = c.take<double2>(n);
         P.pt_ptr = c.take<int32_t>((size_t)np + 1);
         P.cm_pt = c.take<int32_t>(n);
@@ -167,6 +168,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.cm_uv = c.take<double2>(n);
         P.cam_ptr = c.take<int32_t>((size_t)nc + 1);
         P.pchunk = c.take<int32_t>(pbound + 1);
+        P.wchunk = c.take<int2>((size_t)np + 2);
         P.cchunk_cam = c.take<int32_t>(cbound);
         P.cchunk_beg = c.take<int32_t>(cbound + 1);
         pr->cfirst = c.take<int32_t>((size_t)nc + 1);
@@ -295,6 +297,28 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         CKC(cudaMemcpyAsync(pr->cfirst, cfirst.data(), sizeof(int32_t) * cfirst.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaStreamSynchronize(s));  // host vectors go out of scope
     }
+    // warp chunks of the PCG point pass: greedy runs of whole points with at
+    // most 32 observations; a point with a longer track forms its own chunk
+    {
+        std::vector<int32_t> pp((size_t)np + 1);
+        CKC(cudaMemcpyAsync(pp.data(), P.pt_ptr, sizeof(int32_t) * pp.size(), cudaMemcpyDeviceToHost, s));
+        CKC(cudaStreamSynchronize(s));
+        std::vector<int2> wc;
+        wc.reserve((size_t)np / 4 + 16);
+        int32_t p = 0;
+        while (p < np) {
+            const int32_t o = pp[p];
+            int32_t q = p + 1;
+            if (pp[p + 1] - o <= 32)
+                while (q < np && pp[q + 1] - o <= 32) ++q;
+            wc.push_back(make_int2(p, o));
+            p = q;
+        }
+        wc.push_back(make_int2(np, (int32_t)n));
+        P.n_wchunks = (int32_t)wc.size() - 1;
+        CKC(cudaMemcpyAsync(P.wchunk, wc.data(), sizeof(int2) * wc.size(), cudaMemcpyHostToDevice, s));
+        CKC(cudaStreamSynchronize(s));
+    }
     CKC(cudaMemcpyAsync(P.cams0, P.cams, sizeof(double) * 9 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
     CKC(cudaMemcpyAsync(P.pts0, P.pts, sizeof(double) * 3 * (size_t)np, cudaMemcpyDeviceToDevice, s));
     CKC(cudaMemsetAsync(P.st, 0, sizeof(DevState), s));
@@ -303,6 +327,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     CKC(cudaStreamSynchronize(s));
     cudaFree(tmp);
 #undef CKC
+    plan_pcg_smem(P);
     pr->pcg_grid = pcg_grid_size(P);
     if (3 * pr->pcg_grid > red_len) {
         mba_problem_destroy(pr);
@@ -558,6 +583,10 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         CK(launch_accept(P, s));
     }
     CK(rec(ne > 0 ? ne - 1 : 0));
+    // state_init, camera table, 2 cost kernels; per iteration: camera table, 3
+    // linearisation, 2 damping, PCG, 3 back-substitution, camera table, 2 cost,
+    // LM update, accept
+    const int launches = 4 + 15 * o.max_iter;
     DevState hs;
     mba_status st = check_device_state(pr, &hs);
     if (summary) {
@@ -570,6 +599,7 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         summary->final_radius = hs.radius;
         summary->final_mu = 1.0 / hs.radius;
         summary->ms_total = summary->ms_linearize = summary->ms_pcg = summary->ms_other = 0.0;
+        summary->kernel_launches = launches;
         if (timing) {
             float t = 0.f;
             cudaEventElapsedTime(&t, ev[0], ev[ne - 1]);

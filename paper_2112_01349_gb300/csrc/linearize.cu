@@ -44,7 +44,7 @@ __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc,
 template <typename T>
 __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *slot = reinterpret_cast<T *>(smem_raw);  // [9][cap]
     const T *__restrict__ camtab = (const T *)P.camtab;
     T *__restrict__ J = (T *)P.J;

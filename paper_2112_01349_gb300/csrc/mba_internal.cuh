@@ -14,6 +14,7 @@ namespace mba {
 
 constexpr int kBlock = 256;          // threads per CTA for every kernel
 constexpr int kWarps = kBlock / 32;
+constexpr int kPcgBlock = 256;      // threads per CTA of the persistent PCG kernel
 constexpr int kCamTab = 28;          // values per camera in the camera table
 constexpr int kVec = 12;             // padded stride of 9-vectors per camera (16-B aligned rows)
 constexpr int kCamChunk = 1024;      // observations per camera-major chunk
@@ -48,6 +49,12 @@ struct Prob {
     double delta;
     int32_t cap;           // max observations in a point chunk (smem slots)
     int32_t n_pchunks, n_cchunks;
+    // warp chunks: wchunk[w] = (first point, first observation); runs of whole
+    // points with <= 32 observations, or a single point with a longer track
+    int32_t n_wchunks;
+    int2 *wchunk;          // n_wchunks + 1
+    int32_t pcg_use_ps;    // 1: the search direction is copied into shared memory per pass
+    int32_t pcg_smem;      // dynamic shared memory of the PCG kernel
 
     // parameters (FP64, row-major)
     double *cams, *pts;            // current
@@ -56,6 +63,7 @@ struct Prob {
 
     // observations, point-major order (stable by point, then input index)
     int32_t *pm_cam, *pm_pt, *pm_orig;
+    int2 *pm_pc;                   // (point, camera) per observation
     double2 *pm_uv;
     int32_t *pt_ptr;               // np + 1
     // observations, camera-major order
@@ -225,8 +233,9 @@ __device__ __forceinline__ void loss_weight(int loss, T delta, T s, T *rho, T *w
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void stcg(T *p, T v) { __stcg(p, v); }
 
-// Block-wide sum of one double per thread in a fixed tree order; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double *sbuf /* >= kWarps */) {
+// Block-wide sum of one double per thread in a fixed tree order; result valid
+// in thread 0.  sbuf holds one double per warp (up to 32).
+__device__ __forceinline__ double block_sum(double v, double *sbuf) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -235,9 +244,45 @@ __device__ __forceinline__ double block_sum(double v, double *sbuf /* >= kWarps 
     __syncthreads();
     double s = 0.0;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kWarps; ++i) s += sbuf[i];
+        const int nw = blockDim.x >> 5;
+        for (int i = 0; i < nw; ++i) s += sbuf[i];
     }
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies (global -> shared) completed on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for an mbarrier phase; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i <= limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // Bounded grid barrier for cooperative (co-resident) launches.  Arrivals
@@ -305,6 +350,7 @@ cudaError_t launch_damp(const Prob &P, int damping, cudaStream_t s);
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
                        cudaStream_t s);
 int pcg_grid_size(const Prob &P);
+void plan_pcg_smem(Prob &P);
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s);
 
 // lm.cu

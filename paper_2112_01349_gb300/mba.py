@@ -54,6 +54,7 @@ class Summary(C.Structure):
                 ("status", C.c_int32), ("initial_cost", C.c_double), ("final_cost", C.c_double),
                 ("final_mu", C.c_double), ("final_radius", C.c_double), ("ms_total", C.c_double),
                 ("ms_linearize", C.c_double), ("ms_pcg", C.c_double), ("ms_other", C.c_double),
+                ("kernel_launches", C.c_int32),
                 ("trace", C.POINTER(Iteration)), ("trace_capacity", C.c_int32)]
 
 
