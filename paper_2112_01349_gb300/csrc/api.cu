@@ -139,11 +139,13 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     const int64_t pbound = (n + 512) / 513 + 2;                 // point chunks (stride >= 513)
     const int64_t cbound = n / kCamChunk + (int64_t)nc + 2;     // camera chunks
     pr->pcg_grid = 0;
+    int sms = 0;
     {
-        int dev = 0, sms = 0;
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
+        if (sms > 4096) sms = 4096;
         pr->nb_chunk = sms * 4;
     }
     pr->nb_cost = cost_grid(P);
@@ -194,7 +196,15 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.q = c.take<double>((size_t)nc * kVec);
         P.g = c.take<double>((size_t)nc * kVec);
         P.pT = c.take<char>((size_t)nc * kVec * w);
-        P.cacc = c.take<char>(2 * (size_t)nc * kVec * w);
+        P.p2 = c.take<double>((size_t)nc * kVec);
+        P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
+        P.cta_cam = c.take<int32_t>(4096 + 1);
+        P.cm2pm = c.take<int32_t>(n);
+        P.Xcm = P.fp32 ? c.take<float4>((size_t)P.npad) : nullptr;
+        P.zT = P.fp32 ? c.take<float>((size_t)nc * kVec) : nullptr;
+        P.pT2 = c.take<char>((size_t)nc * kVec * w);
+        P.swc = (P.fp32 && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
+        P.Jcm = P.fp32 ? nullptr : c.take<double>(18 * (size_t)P.npad);
         P.dp = c.take<double>(3 * (size_t)np);
         P.red = c.take<double>(red_len);
         pr->part_a = c.take<double>(8192);
@@ -216,6 +226,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     Carve real;
     real.base = (char *)pr->pool;
     layout(real);
+    P.cfirst = pr->cfirst;
 
     // temporary buffers for the set-up only
     const size_t sort_tmp = stable_sort_tmp_bytes(n, np > nc ? np : nc);
@@ -256,6 +267,9 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     CKC(stable_sort_by_key(pr->orig_cam, n, nc, P.cm_orig, P.cam_ptr, tmp, sort_tmp, s));
     CKC(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, s));
     CKC(gather_layout(P, obs_d, pr->orig_cam, pr->orig_pt, nullptr, flags, s));
+    // camera-major position -> point-major position, via the inverse of the
+    // point-major permutation (set-up scratch)
+    CKC(build_cm_map(P, (int32_t *)tmp, s));
     // keep the observations in input order too (for mba_evaluate)
     {
         // interleaved copy obs_d (n x 2) -> orig_uv (double2): same bytes
@@ -277,12 +291,44 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     if (P.n_pchunks > pbound) return cleanup_fail(MBA_ERR_INVALID_ARG, "internal: point chunk bound");
     CKC(build_point_chunks(P, stride, s));
 
-    // camera chunks (host: nc is small)
+    // PCG camera partition: one group of whole cameras per CTA (one CTA per SM),
+    // cut at the camera boundaries nearest to equal observation counts; then
+    // camera chunks (the smallest power-of-two multiple of kCamChunk for which
+    // the busiest CTA's chunk sums fit its shared-memory slots)
     {
+        const int G = sms;
+        std::vector<int32_t> cta((size_t)G + 1);
+        cta[0] = 0;
+        cta[G] = nc;
+        for (int k = 1; k < G; ++k) {
+            const int64_t t = (int64_t)k * n / G;
+            int32_t lo = cta[k - 1], hi = nc;  // first camera index i >= lo with cam_ptr[i] >= t
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                if (cam_ptr[mid] < t) lo = mid + 1;
+                else hi = mid;
+            }
+            int32_t i = lo;
+            if (i > cta[k - 1] && i <= nc && t - cam_ptr[i - 1] < (int64_t)cam_ptr[i] - t) --i;
+            cta[k] = i < cta[k - 1] ? cta[k - 1] : i;
+        }
+        int chunk = kCamChunk;
+        int max_chunks = 0;
+        for (;;) {
+            max_chunks = 0;
+            for (int k = 0; k < G; ++k) {
+                int64_t c = 0;
+                for (int32_t i = cta[k]; i < cta[k + 1]; ++i) c += (cam_ptr[i + 1] - cam_ptr[i] + chunk - 1) / chunk;
+                if (c > max_chunks) max_chunks = (int)c;
+            }
+            if ((int64_t)max_chunks * 9 * 8 <= 96 * 1024 || chunk >= (1 << 24)) break;
+            chunk *= 2;
+        }
+        P.pcg_max_cta_chunks = max_chunks;
         std::vector<int32_t> ccam, cbeg, cfirst((size_t)nc + 1);
         for (int32_t i = 0; i < nc; ++i) {
             cfirst[i] = (int32_t)ccam.size();
-            for (int32_t b = cam_ptr[i]; b < cam_ptr[i + 1]; b += kCamChunk) {
+            for (int32_t b = cam_ptr[i]; b < cam_ptr[i + 1]; b += chunk) {
                 ccam.push_back(i);
                 cbeg.push_back(b);
             }
@@ -295,6 +341,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         CKC(cudaMemcpyAsync(P.cchunk_cam, ccam.data(), sizeof(int32_t) * ccam.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaMemcpyAsync(P.cchunk_beg, cbeg.data(), sizeof(int32_t) * cbeg.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaMemcpyAsync(pr->cfirst, cfirst.data(), sizeof(int32_t) * cfirst.size(), cudaMemcpyHostToDevice, s));
+        CKC(cudaMemcpyAsync(P.cta_cam, cta.data(), sizeof(int32_t) * cta.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaStreamSynchronize(s));  // host vectors go out of scope
     }
     // warp chunks of the PCG point pass: greedy runs of whole points with at
@@ -329,6 +376,10 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
 #undef CKC
     plan_pcg_smem(P);
     pr->pcg_grid = pcg_grid_size(P);
+    if (pr->pcg_grid != sms) {
+        mba_problem_destroy(pr);
+        return fail(MBA_ERR_INVALID_ARG, "the PCG kernel does not fit one CTA per SM for this problem shape");
+    }
     if (3 * pr->pcg_grid > red_len) {
         mba_problem_destroy(pr);
         return fail(MBA_ERR_INVALID_ARG, "internal: reduction buffer");
@@ -369,7 +420,6 @@ mba_status prepare_step(mba_problem *pr, double mu, int damping) {
     CK(launch_camera_tables_forced(P, P.cams, s));
     CK(launch_linearize_impl(P, pr->cfirst, 1, s));
     CK(launch_damp(P, damping, s));
-    CK(cudaMemsetAsync(P.cacc, 0, 2 * (size_t)P.nc * kVec * (P.fp32 ? 4 : 8), s));
     return MBA_OK;
 }
 
@@ -565,14 +615,12 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
     CK(launch_state_init(P, o.initial_radius, -1.0, 0, s));
     CK(launch_camera_tables(P, P.cams, false, s));
     CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s));
-    const size_t cacc_bytes = 2 * (size_t)P.nc * kVec * (P.fp32 ? 4 : 8);
     for (int it = 0; it < o.max_iter; ++it) {
         CK(rec(1 + 4 * it));
         CK(launch_camera_tables(P, P.cams, true, s));
         CK(launch_linearize_impl(P, pr->cfirst, 0, s));
         CK(rec(2 + 4 * it));
         CK(launch_damp(P, o.damping, s));
-        CK(cudaMemsetAsync(P.cacc, 0, cacc_bytes, s));
         CK(rec(3 + 4 * it));
         CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
         CK(rec(4 + 4 * it));

@@ -140,6 +140,15 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             for (int q = 0; q < 18; ++q) Jc[q] *= sw;
             e[0] *= sw;
             e[1] *= sw;
+            // copies the PCG camera pass reads in camera-major order
+            if (sizeof(T) == 8 && P.Jcm) {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) P.Jcm[(int64_t)q * P.npad + s] = (double)Jc[q];
+            }
+            if (sizeof(T) == 4 && P.swc) ((float *)P.swc)[s] = (float)sw;
+            if (sizeof(T) == 4 && P.Xcm)
+                ((float4 *)P.Xcm)[s] = make_float4((float)P.pts[3 * (int64_t)pt], (float)P.pts[3 * (int64_t)pt + 1],
+                                                   (float)P.pts[3 * (int64_t)pt + 2], 0.f);
             int idx = 0;
 #pragma unroll
             for (int a = 0; a < 9; ++a)

@@ -14,11 +14,17 @@ namespace mba {
 
 constexpr int kBlock = 256;          // threads per CTA for every kernel
 constexpr int kWarps = kBlock / 32;
-constexpr int kPcgBlock = 256;      // threads per CTA of the persistent PCG kernel
 constexpr int kCamTab = 28;          // values per camera in the camera table
 constexpr int kVec = 12;             // padded stride of 9-vectors per camera (16-B aligned rows)
-constexpr int kCamChunk = 1024;      // observations per camera-major chunk
+constexpr int kCamChunk = 256;       // observations per camera-major chunk (at least)
 constexpr int kMaxTrack = 1024;      // longest supported point track
+
+// Threads per CTA of the persistent PCG kernel (one CTA per SM): the FP32 form
+// fits 64 registers per thread, the FP64 form needs up to 128.
+template <typename T>
+struct PcgBlock {
+    static constexpr int value = sizeof(T) == 4 ? 1024 : 512;
+};
 
 // Device-resident LM / PCG control state.  All LM decisions are made on the
 // device so a whole solve is issued without host round trips.
@@ -70,9 +76,14 @@ struct Prob {
     int32_t *cm_pt, *cm_orig;
     double2 *cm_uv;
     int32_t *cam_ptr;              // nc + 1
+    int32_t *cm2pm;                // per camera-major position: its point-major position
     // chunk tables
     int32_t *pchunk;               // n_pchunks + 1 point indices
     int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
+    int32_t *cfirst;               // nc + 1: first camera chunk of each camera
+    int32_t *cta_cam;              // grid + 1: cameras owned by each PCG CTA (balanced by observations)
+    int32_t pcg_max_cta_chunks;    // most camera chunks any PCG CTA owns
+    int32_t pcg_ps_bytes;          // shared-memory bytes of the search-direction copy
 
     // per-linearisation data (T = float in FP32-mixed, double otherwise)
     void *J;        // [24][npad] sqrt(W)-scaled Jacobian, point-major
@@ -83,15 +94,20 @@ struct Prob {
     double *v;      // [nc][9]
     double *Hll;    // [np][6] packed upper triangle of C
     double *w;      // [np][3]
-    double *cpart;  // [n_cchunks][54] camera-chunk partial sums
+    double *cpart;  // [n_cchunks][54] camera-chunk partial sums (the PCG reuses [n_cchunks][9])
+    void *Xcm;      // FP32-mixed: [npad] float4 point of each observation, camera-major
+    void *zT;       // FP32-mixed: [nc][kVec] float copy of z
+    void *pT2;      // FP32-mixed: second float search-direction buffer (alternate iterations)
+    void *swc;      // FP32-mixed with a loss: [npad] sqrt(W) in camera-major order
+    double *Jcm;    // FP64: [18][npad] sqrt(W)-scaled camera Jacobian, camera-major
     // per-solve data
     double *Bd;     // [nc][81] damped B~
     double *Binv;   // [nc][81] inverse of B~ (block-Jacobi preconditioner)
     void *Cinv;     // [np][6] packed inverse of damped C~, T
     // PCG vectors, [nc][kVec] FP64
-    double *x, *r, *z, *p, *q, *g;
-    void *pT;       // [nc][kVec] search direction in T
-    void *cacc;     // 2 x [nc][kVec] camera accumulators in T
+    double *x, *r, *z, *p, *p2, *q, *g;  // p, p2: search directions of alternate iterations
+    void *pT;       // [nc][kVec] search direction in T (point pass gathers when not in shared memory)
+    void *sbuf;     // [npad] per observation s = Jp~ b (2 x T), point-major, written by the point pass
     double *dp;     // [np][3] point step
     double *red;    // reduction partials: per-CTA p.q, r.z and r.r of the persistent kernel
     int32_t red_len;
@@ -160,6 +176,10 @@ __device__ __forceinline__ void camera_table_row(const double *c, double *o) {
     o[24] = small; o[25] = 0.0; o[26] = 0.0; o[27] = 0.0;
 }
 
+// Correctly rounded reciprocal (the same value as 1 / x, without the divide routine).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // Residual e = pi(c, X) - u and, if JAC, the analytic Jacobians Jc (2x9, row
 // major: w, t, f, k1, k2) and Jp (2x3) by the chain rule, in precision T.
 template <typename T, bool JAC>
@@ -170,7 +190,7 @@ __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T 
     const T P0 = R0 * X0 + R1 * X1 + R2 * X2 + ct[18];
     const T P1 = R3 * X0 + R4 * X1 + R5 * X2 + ct[19];
     const T P2 = R6 * X0 + R7 * X1 + R8 * X2 + ct[20];
-    const T iz = T(1) / P2;
+    const T iz = rcp_rn(P2);
     const T px = -P0 * iz, py = -P1 * iz;
     const T f = ct[21], k1 = ct[22], k2 = ct[23];
     const T r2 = px * px + py * py;
@@ -233,8 +253,9 @@ __device__ __forceinline__ void loss_weight(int loss, T delta, T s, T *rho, T *w
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void stcg(T *p, T v) { __stcg(p, v); }
 
-// Block-wide sum of one double per thread in a fixed tree order; result valid
-// in thread 0.  sbuf holds one double per warp (up to 32).
+// Block-wide sum of one double per thread in a fixed tree order (shuffles in
+// each warp, then across the warp sums in warp 0); result valid in thread 0.
+// sbuf holds one double per warp (up to 32).
 __device__ __forceinline__ double block_sum(double v, double *sbuf) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -243,9 +264,10 @@ __device__ __forceinline__ double block_sum(double v, double *sbuf) {
     if (lane == 0) sbuf[wid] = v;
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int i = 0; i < nw; ++i) s += sbuf[i];
+    if (wid == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? sbuf[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
     return s;
 }
@@ -333,6 +355,7 @@ cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, i
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
                           int32_t *tmp_i, cudaStream_t s);
 cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s);
+cudaError_t build_cm_map(Prob &P, int32_t *tmp_n, cudaStream_t s);
 
 // linearize.cu
 cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin, cudaStream_t s);

@@ -119,14 +119,14 @@ __device__ __forceinline__ void load_jac(const T *__restrict__ J, int64_t npad, 
     for (int q = 0; q < 6; ++q) Jp[q] = __ldg(J + (18 + q) * npad + o);
 }
 
-__device__ __forceinline__ void acc_camera(float *row, const float *y) {
-    atomicAdd(reinterpret_cast<float4 *>(row), make_float4(y[0], y[1], y[2], y[3]));
-    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(y[4], y[5], y[6], y[7]));
-    atomicAdd(row + 8, y[8]);
-}
-__device__ __forceinline__ void acc_camera(double *row, const double *y) {
+// Streaming variant: evict-first loads, so the once-per-pass Jacobian stream
+// does not push the per-observation s vectors and camera data out of L2.
+template <typename T>
+__device__ __forceinline__ void load_jac_stream(const T *__restrict__ J, int64_t npad, int64_t o, T *Jc, T *Jp) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) atomicAdd(row + q, y[q]);
+    for (int q = 0; q < 18; ++q) Jc[q] = __ldcs(J + q * npad + o);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Jp[q] = __ldcs(J + (18 + q) * npad + o);
 }
 
 template <typename T>
@@ -139,13 +139,30 @@ __device__ __forceinline__ void sym3_apply(const T *__restrict__ C, T a0, T a1, 
 }
 
 // ---------------------------------------------------------------------------
-// Warp-granular point pass.  The point-major observation stream is cut, at
-// creation, into warp chunks: runs of whole points with at most 32
-// observations (one lane per observation), or one point with a longer track
-// on its own.  A warp owns its chunks outright, so the per-point sums need
-// only shuffles (a segmented scan keyed by point) and no block barriers; other
-// warps on the SM hide each chunk's load latency.
+// The implicit Schur product S p = B~ p - E C~^-1 E^T p in two passes per PCG
+// iteration, neither of which writes to a shared accumulator:
+//  * point pass (point-major, warp chunks of whole points, <= 32
+//    observations): b_j = C~_j^-1 sum_k Jp~_k^T Jc~_k p_i(k) by a segmented
+//    shuffle scan, then s_k = Jp~_k b_j is stored per observation;
+//  * camera pass (camera-major, one warp per camera chunk of <= 1024
+//    observations): the chunk's sum of Jc~_k^T s_k; the last warp to finish a
+//    camera adds that camera's chunk sums in a fixed order and forms
+//    q_i = B~_i p_i - c_i (or the right-hand side g_i = v_i - c_i).
+// In FP32-mixed the camera pass recomputes Jc~ from the camera table and the
+// point (camera-uniform per warp, cheaper than streaming 72 bytes again); the
+// FP64 form streams a camera-major copy written at linearisation.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+};
+template <>
+struct V2<double> {
+    using type = double2;
+};
+
 template <typename T>
 __device__ __forceinline__ void gather_p(const T *ps, const T *pT, int cam, T *pa) {
     if (ps) {
@@ -172,17 +189,6 @@ __device__ __forceinline__ void et_p(const T *Jc, const T *Jp, const T *pa, T *u
     u[2] = Jp[2] * t0 + Jp[5] * t1;
 }
 
-// E b contribution of one observation, added into its camera: y = Jc^T (Jp b)
-template <typename T>
-__device__ __forceinline__ void e_b(const T *Jc, const T *Jp, const T *b, T *acc_row) {
-    const T s0 = Jp[0] * b[0] + Jp[1] * b[1] + Jp[2] * b[2];
-    const T s1 = Jp[3] * b[0] + Jp[4] * b[1] + Jp[5] * b[2];
-    T y[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) y[a] = Jc[a] * s0 + Jc[9 + a] * s1;
-    acc_camera(acc_row, y);
-}
-
 template <typename T>
 __device__ __forceinline__ void load_sym3(const T *__restrict__ C, T *c) {
 #pragma unroll
@@ -195,14 +201,17 @@ __device__ __forceinline__ void apply_sym3(const T *c, T a0, T a1, T a2, T *b) {
     b[2] = c[2] * a0 + c[4] * a1 + c[5] * a2;
 }
 
-// One pass of the implicit Schur product over the warp chunks of this CTA.
-// RHS: b_j = C~_j^-1 w_j.  Otherwise b_j = C~_j^-1 sum_k Jp~_k^T Jc~_k p_i(k).
-// Then Jc~_k^T Jp~_k b_j is added into acc[i(k)].  Per chunk the dependent
-// loads are: (point, camera) of each lane, then Jacobian, C~^-1 of the lane's
-// point and the camera's p together; the next chunk's table entries are
-// fetched one chunk ahead.
+template <typename T>
+__device__ __forceinline__ void store_s(typename V2<T>::type *sbuf, int64_t o, const T *Jp, const T *b) {
+    typename V2<T>::type v;
+    v.x = Jp[0] * b[0] + Jp[1] * b[1] + Jp[2] * b[2];
+    v.y = Jp[3] * b[0] + Jp[4] * b[1] + Jp[5] * b[2];
+    sbuf[o] = v;
+}
+
+// Point pass.  RHS: b_j = C~_j^-1 w_j.  Otherwise b_j = C~_j^-1 sum_k u_k.
 template <typename T, bool RHS>
-__device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
+__device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<T>::type *sbuf) {
     const T *__restrict__ J = (const T *)P.J;
     const T *__restrict__ Cinv = (const T *)P.Cinv;
     const int64_t npad = P.npad;
@@ -230,14 +239,17 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
             const int2 pc = act ? P.pm_pc[o] : make_int2(-1 - lane, 0);
             const int pt = pc.x, cam = pc.y;
             T Jc[18], Jp[6], ci[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Jp[q] = ci[q] = T(0);
+#pragma unroll
+            for (int q = 0; q < 18; ++q) Jc[q] = T(0);
             if (act) {
-                load_jac(J, npad, o, Jc, Jp);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) Jp[q] = __ldcs(J + (18 + q) * npad + o);
+                if (!RHS)
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) Jc[q] = __ldcs(J + q * npad + o);
                 load_sym3(Cinv + 6 * (int64_t)pt, ci);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 18; ++q) Jc[q] = T(0);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) Jp[q] = ci[q] = T(0);
             }
             T b[3] = {T(0), T(0), T(0)};
             if (RHS) {
@@ -274,7 +286,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
                 b[1] = __shfl_sync(full, bt[1], src);
                 b[2] = __shfl_sync(full, bt[2], src);
             }
-            if (act) e_b(Jc, Jp, b, acc + (int64_t)cam * kVec);
+            if (act) store_s<T>(sbuf, o, Jp, b);
         } else {
             // one point with a long track: two sweeps over 32-observation slices
             const int pt = c0.x;
@@ -288,7 +300,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
                     if (base + lane < m) {
                         const int64_t o = (int64_t)o0 + base + lane;
                         T Jc[18], Jp[6], pa[9], u[3];
-                        load_jac(J, npad, o, Jc, Jp);
+                        load_jac_stream(J, npad, o, Jc, Jp);
                         gather_p(ps, pT, P.pm_pc[o].y, pa);
                         et_p(Jc, Jp, pa, u);
                         a[0] += u[0];
@@ -307,9 +319,10 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
             for (int base = 0; base < m; base += 32) {
                 if (base + lane < m) {
                     const int64_t o = (int64_t)o0 + base + lane;
-                    T Jc[18], Jp[6];
-                    load_jac(J, npad, o, Jc, Jp);
-                    e_b(Jc, Jp, b, acc + (int64_t)P.pm_pc[o].y * kVec);
+                    T Jp[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) Jp[q] = __ldcs(J + (18 + q) * npad + o);
+                    store_s<T>(sbuf, o, Jp, b);
                 }
             }
         }
@@ -318,176 +331,401 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, T *acc) {
     }
 }
 
-// Copy the search direction into shared memory (dense nc x 9).
+// y = Jc~^T s for one camera-major observation.  FP32: from the camera table and
+// the observation's point by the transposed chain rule, without forming Jc:
+// v = D^T s is the translation block (D = d(pixel)/dP), y_w = M^T (X x (R^T v))
+// (X x v in the first-order branch), y_f = d (p.s), y_k1 = f |p|^2 (p.s),
+// y_k2 = f |p|^4 (p.s); s is scaled by sqrt(W) first.  FP64: the stored
+// camera-major Jacobian.
 template <typename T>
-__device__ void stage_p(const Prob &P, const T *pT, T *ps) {
+__device__ __forceinline__ void camera_y(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *y);
+template <>
+__device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
+                                                float *y) {
+    const float4 X = __ldcs((const float4 *)P.Xcm + s);
+    if (P.loss != MBA_LOSS_NONE) {
+        const float sw = __ldcs((const float *)P.swc + s);
+        s0 *= sw;
+        s1 *= sw;
+    }
+    const float P0 = ct[0] * X.x + ct[1] * X.y + ct[2] * X.z + ct[18];
+    const float P1 = ct[3] * X.x + ct[4] * X.y + ct[5] * X.z + ct[19];
+    const float P2 = ct[6] * X.x + ct[7] * X.y + ct[8] * X.z + ct[20];
+    const float iz = __frcp_rn(P2);
+    const float px = -P0 * iz, py = -P1 * iz;
+    const float f = ct[21], k1 = ct[22], k2 = ct[23];
+    const float r2 = px * px + py * py;
+    const float d = 1.f + k1 * r2 + k2 * r2 * r2;
+    const float dd = 2.f * k1 + 4.f * k2 * r2;
+    const float a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
+    // v = D^T s with D = A dp/dP, A = [[a00, a01], [a01, a11]]
+    const float g0 = -(a00 * s0 + a01 * s1) * iz, g1 = -(a01 * s0 + a11 * s1) * iz;  // (A s) scaled
+    const float v0 = g0, v1 = g1, v2 = g0 * px + g1 * py;
+    y[3] = v0;
+    y[4] = v1;
+    y[5] = v2;
+    float w0 = v0, w1 = v1, w2 = v2;
+    const bool small = ct[24] != 0.f;
+    if (!small) {
+        w0 = ct[0] * v0 + ct[3] * v1 + ct[6] * v2;
+        w1 = ct[1] * v0 + ct[4] * v1 + ct[7] * v2;
+        w2 = ct[2] * v0 + ct[5] * v1 + ct[8] * v2;
+    }
+    const float u0 = X.y * w2 - X.z * w1, u1 = X.z * w0 - X.x * w2, u2 = X.x * w1 - X.y * w0;
+    y[0] = ct[9] * u0 + ct[12] * u1 + ct[15] * u2;
+    y[1] = ct[10] * u0 + ct[13] * u1 + ct[16] * u2;
+    y[2] = ct[11] * u0 + ct[14] * u1 + ct[17] * u2;
+    const float pss = px * s0 + py * s1;
+    y[6] = d * pss;
+    y[7] = f * r2 * pss;
+    y[8] = f * r2 * r2 * pss;
+}
+template <>
+__device__ __forceinline__ void camera_y<double>(const Prob &P, const double *ct, int64_t s, double s0, double s1,
+                                                 double *y) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) y[a] = __ldcs(P.Jcm + a * P.npad + s) * s0 + __ldcs(P.Jcm + (9 + a) * P.npad + s) * s1;
+}
+
+enum CamMode { CAM_RHS = 0, CAM_ITER = 1, CAM_MATVEC = 2 };
+
+__device__ __forceinline__ double2 block_sum2_all(double x, double y, double *sb);
+
+// 9-vector held by lanes 0..8 of a warp: element b
+__device__ __forceinline__ double lane9(double v, int b) { return __shfl_sync(0xffffffffu, v, b); }
+
+// Camera pass.  Each CTA owns a contiguous run of whole cameras
+// [cta_cam[b], cta_cam[b+1]), balanced by observation count at creation; its
+// warps reduce the run's camera chunks into shared-memory slots, then, after a
+// block barrier, each camera's chunk sums are added in chunk order and the
+// camera is finalised.  No global atomics or fences; results do not depend on
+// timing.  CAM_RHS: g = v - c, x = 0, r = g, z = B~^-1 g; returns this CTA's
+// (r.r, r.z).  CAM_ITER: p = z + beta p_prev (p = z first), q = B~ p - c;
+// returns (p.q, 0).  CAM_MATVEC: q = B~ p - c with p given.
+template <typename T, int MODE>
+__device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, const double *p_prev, double *p_cur,
+                               T *pT_cur, double beta, bool first, double *cslot, double *sb) {
+    using T2 = typename V2<T>::type;
+    constexpr int U = 4;
+    __shared__ T cts[32][kCamTab];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
+    const T *camtab = (const T *)P.camtab;
+    T *ct = cts[wid];
+    __shared__ int next_chunk;
+    const int cb = P.cta_cam[blockIdx.x], ce = P.cta_cam[blockIdx.x + 1];
+    const int k0 = P.cfirst[cb], k1 = P.cfirst[ce];
+    if (threadIdx.x == 0) next_chunk = k0 + nwarp;
+    __syncthreads();
+    int loaded = -1;
+    // warps claim chunks dynamically; each chunk's sum goes to its own slot, so
+    // the result does not depend on which warp took it
+    for (int k = k0 + wid; k < k1;) {
+        const int cam = P.cchunk_cam[k];
+        const int b0 = P.cchunk_beg[k], b1 = P.cchunk_beg[k + 1];
+        if (sizeof(T) == 4 && cam != loaded) {
+            __syncwarp();
+            if (lane < kCamTab) ct[lane] = __ldg(camtab + (int64_t)cam * kCamTab + lane);
+            __syncwarp();
+            loaded = cam;
+        }
+        T acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = T(0);
+        for (int s0 = b0; s0 < b1; s0 += 32 * U) {
+            int pm[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = s0 + u * 32 + lane;
+                pm[u] = s < b1 ? __ldcs(P.cm2pm + s) : -1;
+            }
+            T2 sv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (pm[u] >= 0) sv[u] = ldcg(sbuf + pm[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (pm[u] >= 0) {
+                    T y[9];
+                    camera_y<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, y);
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) acc[a] += y[a];
+                }
+            }
+        }
+        T mine = T(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            T v = acc[a];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(full, v, d);
+            if (lane == a) mine = v;
+        }
+        if (lane < 9) cslot[(k - k0) * 9 + lane] = (double)mine;  // one conversion per lane
+        int nk = 0;
+        if (lane == 0) nk = atomicAdd(&next_chunk, 1);
+        k = __shfl_sync(full, nk, 0);
+    }
+    __syncthreads();
+    // finalise this CTA's cameras: chunk sums added in chunk order
+    double d1 = 0.0, d2 = 0.0;
+    for (int cam = cb + wid; cam < ce; cam += nwarp) {
+        const int a = lane < 9 ? lane : 0;
+        const int64_t vo = (int64_t)cam * kVec + a;
+        double cs = 0.0;
+        if (lane < 9)
+            for (int k = P.cfirst[cam]; k < P.cfirst[cam + 1]; ++k) cs += cslot[(k - k0) * 9 + a];
+        if (MODE == CAM_RHS) {
+            const double g = lane < 9 ? P.v[9 * (int64_t)cam + a] - cs : 0.0;
+            double z = 0.0;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) z += __ldg(P.Binv + 81 * (int64_t)cam + a * 9 + b) * lane9(g, b);
+            double rr = lane < 9 ? g * g : 0.0, rz = lane < 9 ? g * z : 0.0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                rr += __shfl_xor_sync(full, rr, d);
+                rz += __shfl_xor_sync(full, rz, d);
+            }
+            if (lane < 9) {
+                stcg(P.g + vo, g);
+                stcg(P.x + vo, 0.0);
+                stcg(P.r + vo, g);
+                stcg(P.z + vo, z);
+                if (sizeof(T) == 4) stcg((float *)P.zT + vo, (float)z);
+            }
+            d1 += rr;
+            d2 += rz;
+        } else {
+            double p;
+            if (MODE == CAM_MATVEC) p = P.p[vo];
+            else p = first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo));
+            double bp = 0.0;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) bp += __ldg(P.Bd + 81 * (int64_t)cam + a * 9 + b) * lane9(p, b);
+            const double q = bp - cs;
+            double pq = lane < 9 ? p * q : 0.0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) pq += __shfl_xor_sync(full, pq, d);
+            if (lane < 9) {
+                stcg(P.q + vo, q);
+                if (MODE == CAM_ITER) {
+                    stcg(p_cur + vo, p);
+                    if (pT_cur) stcg(pT_cur + vo, (T)p);
+                }
+            }
+            d1 += pq;
+        }
+    }
+    // CTA partials in a fixed order (warp w's cameras, then a tree over warps);
+    // d1, d2 are warp-uniform, so only lane 0 contributes
+    return block_sum2_all(lane == 0 ? d1 : 0.0, lane == 0 ? d2 : 0.0, sb);
+}
+
+// Search direction into shared memory (dense nc x 9, in T): p = z + beta p_prev
+// (p = z on the first iteration), or the given FP64 p (src_given).  The FP32
+// form builds it from float copies of z and p_prev with float4 loads; the FP64
+// form from the FP64 vectors, as the camera pass does.
+template <typename T>
+__device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_prev, double beta, bool first,
+                        const double *src_given) {
     const int total = P.nc * 9;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int cam = e / 9, a = e - cam * 9;
-        ps[e] = ldcg(pT + (int64_t)cam * kVec + a);
+    if (sizeof(T) == 4 && !src_given) {
+        const float4 *z4 = (const float4 *)P.zT, *p4 = (const float4 *)pT_prev;
+        const float fb = (float)beta;
+        const int nq = P.nc * (kVec / 4);  // float4 per camera row: 3 (9 values + padding)
+        for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+            const int cam = e / 3, part = e - cam * 3;
+            const float4 zv = __ldcg(z4 + e);
+            float4 v = zv;
+            if (!first) {
+                const float4 pv = __ldcg(p4 + e);
+                v = make_float4(fmaf(fb, pv.x, zv.x), fmaf(fb, pv.y, zv.y), fmaf(fb, pv.z, zv.z), fmaf(fb, pv.w, zv.w));
+            }
+            float *dst = (float *)ps + cam * 9 + part * 4;
+            dst[0] = v.x;
+            if (part < 2) {
+                dst[1] = v.y;
+                dst[2] = v.z;
+                dst[3] = v.w;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < total; e0 += blockDim.x * U) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = 0.0;
+            if (e < total) {
+                const int cam = e / 9, a = e - cam * 9;
+                const int64_t vo = (int64_t)cam * kVec + a;
+                if (src_given) v[u] = src_given[vo];
+                else v[u] = first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < total) ps[e] = (T)v[u];
+        }
     }
     __syncthreads();
 }
 
-// Sum of the per-CTA partials in a fixed order (every CTA gets the same value).
-__device__ __forceinline__ double sum_parts(const double *parts, int G, double *sb) {
-    __shared__ double s_out;
+// Sum of n partials in a fixed order (every CTA gets the same value).
+__device__ __forceinline__ double block_sum2_all_x(double x, double *sb);
+__device__ __forceinline__ double sum_parts(const double *parts, int n, double *sb) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) acc += ldcg(parts + i);
-    const double s = block_sum(acc, sb);
-    if (threadIdx.x == 0) s_out = s;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += ldcg(parts + i);
+    return block_sum2_all_x(acc, sb);
+}
+
+// Two block-wide sums in a fixed tree order (sb holds 64 doubles); every
+// thread gets the result.
+__device__ __forceinline__ double2 block_sum2_all(double x, double y, double *sb) {
+    __shared__ double2 s_out2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
-    return s_out;
+    if (lane == 0) {
+        sb[wid] = x;
+        sb[32 + wid] = y;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        double sx = in ? sb[lane] : 0.0, sy = in ? sb[32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) s_out2 = make_double2(sx, sy);
+    }
+    __syncthreads();
+    return s_out2;
+}
+
+__device__ __forceinline__ double block_sum2_all_x(double x, double *sb) { return block_sum2_all(x, 0.0, sb).x; }
+
+// Two sums of n partials each, in one pass; every CTA gets the same values.
+__device__ __forceinline__ double2 sum_parts2(const double *a, const double *b, int n, double *sb) {
+    double x = 0.0, y = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x += ldcg(a + i);
+        y += ldcg(b + i);
+    }
+    return block_sum2_all(x, y, sb);
 }
 
 // ---------------------------------------------------------------------------
-// persistent PCG kernel (cooperative launch, one CTA set for the whole solve)
+// persistent PCG kernel (cooperative launch, one CTA per SM for the whole solve)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kPcgBlock, sizeof(T) == 4 ? 4 : 2) pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin) {
+__global__ void __launch_bounds__(PcgBlock<T>::value, 1)
+    pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin) {
+    using T2 = typename V2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double sb[32];
+    __shared__ double sb[64];
     DevState *st = P.st;
     if (st->done) return;
     uint32_t epoch = 0;
     const int G = gridDim.x;
     const int nwarp = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t vec_n = (int64_t)P.nc * kVec;
     T *pT = (T *)P.pT;
-    T *cacc0 = (T *)P.cacc, *cacc1 = cacc0 + vec_n;
-    double *part_pq = P.red, *part_rho = P.red + G, *part_rr = P.red + 2 * G;
-    const int ncw = (P.nc + 2) / 3;  // warps of camera work (3 cameras x 9 rows per warp)
+    T2 *sbuf = (T2 *)P.sbuf;
+    double *part_rho = P.red, *part_rr = P.red + G, *part_pq = P.red + 2 * G;
+    const int ncw = (P.nc + 2) / 3;  // warps of camera-row work (3 cameras x 9 rows per warp)
     const int my_sub = lane / 9, row = lane % 9;
     const unsigned full = 0xffffffffu;
-
     T *ps = P.pcg_use_ps ? (T *)smem_raw : nullptr;
+    double *cslot = (double *)(smem_raw + P.pcg_ps_bytes);
     bool ok = true;
     auto barrier = [&]() -> bool { return grid_barrier(st, epoch, spin); };
+    // owner phase: p = z + beta p_prev written in FP64 and as T for the gathers
+    auto phase_p = [&](const double *p_prev, double *p_cur, double beta, bool first, const double *given) {
+        for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
+            const int cam = w * 3 + my_sub;
+            if (lane < 27 && cam < P.nc) {
+                const int64_t vo = (int64_t)cam * kVec + row;
+                const double pn = given ? given[vo]
+                                        : (first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo)));
+                if (!given) stcg(p_cur + vo, pn);
+                stcg(pT + vo, (T)pn);
+            }
+        }
+    };
 
     if (mode == PCG_MATVEC) {
         // p given in P.p (FP64): q = B~ p - E C~^-1 E^T p
-        for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-            const int cam = w * 3 + my_sub;
-            if (lane < 27 && cam < P.nc) stcg(pT + (int64_t)cam * kVec + row, (T)P.p[(int64_t)cam * kVec + row]);
+        if (ps) {
+            stage_p<T>(P, ps, nullptr, nullptr, 0.0, true, P.p);
+        } else {
+            phase_p(nullptr, nullptr, 0.0, true, P.p);
+            if (!(ok = barrier())) return;
         }
-        ok = barrier();
-        if (ok && ps) stage_p(P, pT, ps);
-        if (ok) point_pass<T, false>(P, ps, pT, cacc0);
-        if (ok) ok = barrier();
-        if (ok) {
-            for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-                const int cam = w * 3 + my_sub;
-                const bool act = lane < 27 && cam < P.nc;
-                const int64_t vo = (int64_t)(act ? cam : 0) * kVec;
-                const double pr = act ? P.p[vo + row] : 0.0;
-                double bp = 0.0;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    const double pc = __shfl_sync(full, pr, my_sub * 9 + c);
-                    if (act) bp += P.Bd[81 * (int64_t)cam + row * 9 + c] * pc;
-                }
-                if (act) P.q[vo + row] = bp - (double)ldcg(cacc0 + vo + row);
-            }
-        }
+        point_pass<T, false>(P, ps, pT, sbuf);
+        if (!barrier()) return;
+        camera_pass<T, CAM_MATVEC>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         return;
     }
 
-    // ---- right-hand side g = v - E C~^-1 w (Eq. 3) into cacc1 ----
-    point_pass<T, true>(P, nullptr, pT, cacc1);
+    // ---- right-hand side g = v - E C~^-1 w (Eq. 3), x = 0, r = g, z = B~^-1 g ----
+    point_pass<T, true>(P, nullptr, nullptr, sbuf);
     ok = barrier();
     if (ok) {
-        double rr = 0.0, rz = 0.0;
-        for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-            const int cam = w * 3 + my_sub;
-            const bool act = lane < 27 && cam < P.nc;
-            const int64_t vo = (int64_t)(act ? cam : 0) * kVec;
-            double g = 0.0;
-            if (act) {
-                g = P.v[9 * (int64_t)cam + row] - (double)ldcg(cacc1 + vo + row);
-                P.g[vo + row] = g;
-                P.x[vo + row] = 0.0;
-                P.r[vo + row] = g;
-            }
-            double z = 0.0;
-#pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                const double gc = __shfl_sync(full, g, my_sub * 9 + c);
-                if (act) z += P.Binv[81 * (int64_t)cam + row * 9 + c] * gc;
-            }
-            if (act) {
-                P.z[vo + row] = z;
-                rr += g * g;
-                rz += g * z;
-            }
-        }
+        const double2 d = camera_pass<T, CAM_RHS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         if (mode == PCG_RHS_ONLY) return;
-        const double s_rr = block_sum(rr, sb);
-        const double s_rz = block_sum(rz, sb);
         if (threadIdx.x == 0) {
-            stcg(part_rr + blockIdx.x, s_rr);
-            stcg(part_rho + blockIdx.x, s_rz);
+            stcg(part_rr + blockIdx.x, d.x);
+            stcg(part_rho + blockIdx.x, d.y);
         }
         ok = barrier();
     }
 
     int n = 0;
-    double r0 = 0.0, rho_prev = 0.0, rn = 0.0;
+    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;
     if (ok) {
-        r0 = sqrt(sum_parts(part_rr, G, sb));
+        const double2 s0 = sum_parts2(part_rr, part_rho, G, sb);
+        r0 = sqrt(s0.x);
+        rho = s0.y;
         rn = r0;
     }
     if (ok && r0 > 0.0) {
         for (;;) {
-            const double rho = sum_parts(part_rho, G, sb);
             if (!isfinite(rho)) break;
             const double beta = n == 0 ? 0.0 : rho / rho_prev;
-            // phase P: p = z + beta p
-            for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-                const int cam = w * 3 + my_sub;
-                if (lane < 27 && cam < P.nc) {
-                    const int64_t vo = (int64_t)cam * kVec + row;
-                    const double pn = n == 0 ? P.z[vo] : fma(beta, P.p[vo], P.z[vo]);
-                    P.p[vo] = pn;
-                    stcg(pT + vo, (T)pn);
-                }
+            double *p_cur = (n & 1) ? P.p2 : P.p;
+            const double *p_prev = (n & 1) ? P.p : P.p2;
+            T *pT_cur = (n & 1) ? (T *)P.pT2 : pT;
+            const T *pT_prev = (n & 1) ? pT : (T *)P.pT2;
+            if (ps) {
+                stage_p<T>(P, ps, p_prev, pT_prev, beta, n == 0, nullptr);
+            } else {
+                phase_p(p_prev, p_cur, beta, n == 0, nullptr);
+                if (!(ok = barrier())) break;
             }
+            point_pass<T, false>(P, ps, pT, sbuf);
             if (!(ok = barrier())) break;
-            // phase A: E C~^-1 E^T p
-            T *acc = (n & 1) ? cacc1 : cacc0;
-            T *acc_next = (n & 1) ? cacc0 : cacc1;
-            if (ps) stage_p(P, pT, ps);
-            point_pass<T, false>(P, ps, pT, acc);
-            if (!(ok = barrier())) break;
-            // phase Q: q = B~ p - acc; p.q
             {
-                double pq = 0.0;
-                for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-                    const int cam = w * 3 + my_sub;
-                    const bool act = lane < 27 && cam < P.nc;
-                    const int64_t vo = (int64_t)(act ? cam : 0) * kVec + row;
-                    const double pr = act ? P.p[vo] : 0.0;
-                    double bp = 0.0;
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        const double pc = __shfl_sync(full, pr, my_sub * 9 + c);
-                        if (act) bp += P.Bd[81 * (int64_t)cam + row * 9 + c] * pc;
-                    }
-                    if (act) {
-                        const double qv = bp - (double)ldcg(acc + vo);
-                        P.q[vo] = qv;
-                        pq += pr * qv;
-                        stcg(acc_next + vo, T(0));
-                    }
-                }
-                const double s = block_sum(pq, sb);
-                if (threadIdx.x == 0) stcg(part_pq + blockIdx.x, s);
+                const double2 d = camera_pass<T, CAM_ITER>(P, sbuf, p_prev, p_cur, sizeof(T) == 4 ? pT_cur : nullptr,
+                                                           beta, n == 0, cslot, sb);
+                if (threadIdx.x == 0) stcg(part_pq + blockIdx.x, d.x);
             }
             if (!(ok = barrier())) break;
             const double pq = sum_parts(part_pq, G, sb);
             if (!(pq > 0.0) || !isfinite(pq)) break;
             const double alpha = rho / pq;
-            // phase X: x += alpha p; r -= alpha q; z = B~^-1 r
+            // x += alpha p; r -= alpha q; z = B~^-1 r; partial r.r and r.z
             {
                 double rr = 0.0, rz = 0.0;
                 for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
@@ -496,18 +734,19 @@ __global__ void __launch_bounds__(kPcgBlock, sizeof(T) == 4 ? 4 : 2) pcg_kernel(
                     const int64_t vo = (int64_t)(act ? cam : 0) * kVec + row;
                     double rv = 0.0;
                     if (act) {
-                        P.x[vo] = fma(alpha, P.p[vo], P.x[vo]);
-                        rv = fma(-alpha, P.q[vo], P.r[vo]);
-                        P.r[vo] = rv;
+                        stcg(P.x + vo, fma(alpha, ldcg(p_cur + vo), ldcg(P.x + vo)));
+                        rv = fma(-alpha, ldcg(P.q + vo), ldcg(P.r + vo));
+                        stcg(P.r + vo, rv);
                     }
                     double z = 0.0;
 #pragma unroll
                     for (int c = 0; c < 9; ++c) {
                         const double rc = __shfl_sync(full, rv, my_sub * 9 + c);
-                        if (act) z += P.Binv[81 * (int64_t)cam + row * 9 + c] * rc;
+                        if (act) z += __ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c) * rc;
                     }
                     if (act) {
-                        P.z[vo] = z;
+                        stcg(P.z + vo, z);
+                        if (sizeof(T) == 4) stcg((float *)P.zT + vo, (float)z);
                         rr += rv * rv;
                         rz += rv * z;
                     }
@@ -522,7 +761,9 @@ __global__ void __launch_bounds__(kPcgBlock, sizeof(T) == 4 ? 4 : 2) pcg_kernel(
             if (!(ok = barrier())) break;
             ++n;
             rho_prev = rho;
-            rn = sqrt(sum_parts(part_rr, G, sb));
+            double2 sums = sum_parts2(part_rho, part_rr, G, sb);
+            rho = sums.x;
+            rn = sqrt(sums.y);
             if (rn <= tol * r0 || n >= max_iter) break;
         }
     }
@@ -651,15 +892,23 @@ cudaError_t launch_damp(const Prob &P, int damping, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Shared-memory plan: the search direction is copied into shared memory once
-// per pass when it fits in a third of an SM (so three CTAs stay resident).
+// Shared-memory plan: the camera-pass chunk slots of the busiest CTA, plus the
+// search direction (nc x 9) when it also fits; otherwise the point pass
+// gathers p from global memory and an extra barrier is needed.
 void plan_pcg_smem(Prob &P) {
     const int w = P.fp32 ? 4 : 8;
-    const int64_t psb = (int64_t)P.nc * 9 * w;
-    P.pcg_use_ps = psb <= 72 * 1024 ? 1 : 0;
-    P.pcg_smem = P.pcg_use_ps ? (int)psb : 0;
+    const int64_t budget = 227 * 1024 - 12 * 1024;
+    const int64_t slots = (int64_t)P.pcg_max_cta_chunks * 9 * 8;
+    const int64_t psb = (((int64_t)P.nc * 9 * w) + 127) & ~(int64_t)127;
+    P.pcg_use_ps = (psb + slots <= budget) ? 1 : 0;
+    P.pcg_ps_bytes = P.pcg_use_ps ? (int)psb : 0;
+    P.pcg_smem = (int)(P.pcg_ps_bytes + slots);
 }
 
+int pcg_block(const Prob &P) { return P.fp32 ? PcgBlock<float>::value : PcgBlock<double>::value; }
+
+// One CTA per SM (the camera partition is built for exactly that many);
+// returns 0 if the kernel cannot be resident with its shared memory.
 int pcg_grid_size(const Prob &P) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -668,13 +917,12 @@ int pcg_grid_size(const Prob &P) {
     int blocks = 0;
     if (P.fp32) {
         cudaFuncSetAttribute(pcg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<float>, kPcgBlock, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<float>, pcg_block(P), smem);
     } else {
         cudaFuncSetAttribute(pcg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<double>, kPcgBlock, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<double>, pcg_block(P), smem);
     }
-    if (blocks < 1) blocks = 1;
-    return sms * blocks;
+    return blocks >= 1 ? sms : 0;
 }
 
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
@@ -686,8 +934,9 @@ cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long l
     Prob Pc = P;
     void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit};
     if (P.fp32)
-        return cudaLaunchCooperativeKernel((const void *)pcg_kernel<float>, dim3(grid), dim3(kPcgBlock), args, smem, s);
-    return cudaLaunchCooperativeKernel((const void *)pcg_kernel<double>, dim3(grid), dim3(kPcgBlock), args, smem, s);
+        return cudaLaunchCooperativeKernel((const void *)pcg_kernel<float>, dim3(grid), dim3(pcg_block(P)), args, smem,
+                                           s);
+    return cudaLaunchCooperativeKernel((const void *)pcg_kernel<double>, dim3(grid), dim3(pcg_block(P)), args, smem, s);
 }
 
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s) {

@@ -332,6 +332,24 @@ cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, cons
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void invert_perm_kernel(const int32_t *perm, int64_t n, int32_t *inv) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[o]] = (int32_t)o;
+}
+__global__ void cm_map_kernel(const int32_t *cm_orig, const int32_t *inv, int64_t n, int32_t *cm2pm) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        cm2pm[s] = inv[cm_orig[s]];
+}
+}  // namespace
+
+// cm2pm[s] = point-major position of the observation at camera-major position s
+cudaError_t build_cm_map(Prob &P, int32_t *tmp_n, cudaStream_t s) {
+    invert_perm_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_orig, P.n, tmp_n);
+    cm_map_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_orig, tmp_n, P.n, P.cm2pm);
+    return cudaGetLastError();
+}
+
 cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s) {
     point_chunk_kernel<<<grid_for((int64_t)P.n_pchunks + 1), kBlock, 0, s>>>(P.pt_ptr, P.np, P.n, stride,
                                                                            P.n_pchunks, P.pchunk);
