@@ -180,6 +180,32 @@ mba_status mba_schur_matvec(mba_problem *problem, double mu, int32_t damping, co
 mba_status mba_step(mba_problem *problem, double mu, const mba_solver_options *opt, double *dc, double *dp,
                     int32_t *pcg_iters, double *model_decrease);
 
+/*
+ * Cost without any device allocation, for callers that cannot allocate
+ * device memory (a framework that owns every allocation through its own pool,
+ * a real-time loop where allocating is not allowed, code that must not fail
+ * for lack of memory after start-up).  The paper has no counterpart: it is a
+ * convenience entry point of this library.
+ *
+ * All array pointers are DEVICE pointers owned by the caller, in the layouts
+ * of mba_problem_create (cameras nc x 9, points np x 3, observations n x 2,
+ * cam_idx[n], pt_idx[n]); *d_cost (one double, device memory) receives
+ * F = 1/2 sum_k rho(|e_k|^2) in FP64.  Work is enqueued on cuda_stream (NULL =
+ * legacy default stream) and the call returns without waiting; the cost is in
+ * d_cost when the stream reaches it.  An index out of range yields a NaN cost.
+ *
+ * Scratch lives in one fixed device array of about 1.8 MB inside the library
+ * (every GPU that loads the library holds it until the process exits), so nc
+ * may be at most 8192; larger nc returns MBA_ERR_INVALID_ARG, as do NULL
+ * pointers, sizes < 1 and a bad loss.  The first call on a device looks up the
+ * array's device address (no allocation); make that first call before any
+ * stream capture.  Calls share the array: calls whose work overlaps on the GPU
+ * race and may return wrong costs, so order them (same stream or events).
+ */
+mba_status mba_cost_noalloc(const double *d_cameras, int32_t nc, const double *d_points, int32_t np,
+                            const double *d_observations, const int32_t *d_cam_idx, const int32_t *d_pt_idx,
+                            int64_t n, int32_t loss, double huber_delta, double *d_cost, void *cuda_stream);
+
 const char *mba_status_string(mba_status status);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mba_last_error(void);

@@ -91,6 +91,7 @@ def load():
             "mba_linear_system": (C.c_int, [P, dbl, i32, P, P, P, P, P]),
             "mba_schur_matvec": (C.c_int, [P, dbl, i32, P, P]),
             "mba_step": (C.c_int, [P, dbl, P, P, P, P, P]),
+            "mba_cost_noalloc": (C.c_int, [P, i32, P, i32, P, P, P, i64, i32, dbl, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
         }
@@ -282,6 +283,18 @@ def mba_step(h, mu, **opts):
     _check(load().mba_step(h, float(mu), C.byref(o), dc.ctypes.data_as(C.c_void_p), dp.ctypes.data_as(C.c_void_p),
                            C.byref(it), C.byref(md)))
     return dict(dc=dc, dp=dp, pcg_iters=it.value, model_dec=md.value)
+
+
+def mba_cost_noalloc(d_cameras, nc, d_points, np_, d_observations, d_cam_idx, d_pt_idx, n, loss="none",
+                     huber_delta=0.0, d_cost=None, stream=None):
+    """Cost from caller-owned device arrays (integer device addresses); no allocation.
+
+    Enqueues the work on ``stream`` and returns; the cost lands in ``d_cost``.
+    """
+    lb = LOSS[loss] if isinstance(loss, str) else int(loss)
+    _check(load().mba_cost_noalloc(C.c_void_p(d_cameras), int(nc), C.c_void_p(d_points), int(np_),
+                                   C.c_void_p(d_observations), C.c_void_p(d_cam_idx), C.c_void_p(d_pt_idx), int(n),
+                                   lb, float(huber_delta), C.c_void_p(d_cost), _stream_handle(stream)))
 
 
 class Problem:
