@@ -339,6 +339,8 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
 // camera-major Jacobian.
 template <typename T>
 __device__ __forceinline__ void camera_y(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *y);
+template <typename T>
+__device__ __forceinline__ void camera_acc(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *acc);
 template <>
 __device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
                                                 float *y) {
@@ -381,18 +383,26 @@ __device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, 
     y[8] = f * r2 * r2 * pss;
 }
 template <>
-__device__ __forceinline__ void camera_y<double>(const Prob &P, const double *ct, int64_t s, double s0, double s1,
-                                                 double *y) {
+__device__ __forceinline__ void camera_acc<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
+                                                  float *acc) {
+    float y[9];
+    camera_y<float>(P, ct, s, s0, s1, y);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) y[a] = __ldcs(P.Jcm + a * P.npad + s) * s0 + __ldcs(P.Jcm + (9 + a) * P.npad + s) * s1;
+    for (int a = 0; a < 9; ++a) acc[a] += y[a];
+}
+// FP64: acc += Jc~^T s as 18 fused multiply-adds on the stored camera-major Jc~
+template <>
+__device__ __forceinline__ void camera_acc<double>(const Prob &P, const double *ct, int64_t s, double s0, double s1,
+                                                   double *acc) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+        acc[a] = fma(__ldcs(P.Jcm + a * P.npad + s), s0, fma(__ldcs(P.Jcm + (9 + a) * P.npad + s), s1, acc[a]));
 }
 
 enum CamMode { CAM_RHS = 0, CAM_ITER = 1, CAM_MATVEC = 2 };
 
-__device__ __forceinline__ double2 block_sum2_all(double x, double y, double *sb);
+__device__ __forceinline__ double2 cta_sum2(double x, double y, bool warp_data, double *sb);
 
-// 9-vector held by lanes 0..8 of a warp: element b
-__device__ __forceinline__ double lane9(double v, int b) { return __shfl_sync(0xffffffffu, v, b); }
 
 // Camera pass.  Each CTA owns a contiguous run of whole cameras
 // [cta_cam[b], cta_cam[b+1]), balanced by observation count at creation; its
@@ -446,12 +456,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 if (pm[u] >= 0) sv[u] = ldcg(sbuf + pm[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (pm[u] >= 0) {
-                    T y[9];
-                    camera_y<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, y);
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) acc[a] += y[a];
-                }
+                if (pm[u] >= 0) camera_acc<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, acc);
             }
         }
         T mine = T(0);
@@ -468,58 +473,70 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         k = __shfl_sync(full, nk, 0);
     }
     __syncthreads();
-    // finalise this CTA's cameras: chunk sums added in chunk order
+    // finalise this CTA's cameras, three per warp (lanes 9s..9s+8 hold rows of
+    // camera s): chunk sums added in chunk order
     double d1 = 0.0, d2 = 0.0;
-    for (int cam = cb + wid; cam < ce; cam += nwarp) {
-        const int a = lane < 9 ? lane : 0;
-        const int64_t vo = (int64_t)cam * kVec + a;
+    const int sub = lane / 9, row = lane - 9 * sub;
+    for (int c0 = cb + 3 * wid; c0 < ce; c0 += 3 * nwarp) {
+        const int cam = c0 + sub;
+        const bool act = lane < 27 && cam < ce;
+        const int a = act ? row : 0;
+        const int cm = act ? cam : c0;
+        const int64_t vo = (int64_t)cm * kVec + a;
         double cs = 0.0;
-        if (lane < 9)
-            for (int k = P.cfirst[cam]; k < P.cfirst[cam + 1]; ++k) cs += cslot[(k - k0) * 9 + a];
+        if (act)
+            for (int k = P.cfirst[cm]; k < P.cfirst[cm + 1]; ++k) cs += cslot[(k - k0) * 9 + a];
+        double v1 = 0.0, v2 = 0.0;
         if (MODE == CAM_RHS) {
-            const double g = lane < 9 ? P.v[9 * (int64_t)cam + a] - cs : 0.0;
+            const double g = act ? P.v[9 * (int64_t)cm + a] - cs : 0.0;
             double z = 0.0;
 #pragma unroll
-            for (int b = 0; b < 9; ++b) z += __ldg(P.Binv + 81 * (int64_t)cam + a * 9 + b) * lane9(g, b);
-            double rr = lane < 9 ? g * g : 0.0, rz = lane < 9 ? g * z : 0.0;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                rr += __shfl_xor_sync(full, rr, d);
-                rz += __shfl_xor_sync(full, rz, d);
+            for (int b = 0; b < 9; ++b) {
+                const double gb = __shfl_sync(full, g, 9 * sub + b);
+                if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cm + a * 9 + b), gb, z);
             }
-            if (lane < 9) {
+            if (act) {
                 stcg(P.g + vo, g);
                 stcg(P.x + vo, 0.0);
                 stcg(P.r + vo, g);
                 stcg(P.z + vo, z);
                 if (sizeof(T) == 4) stcg((float *)P.zT + vo, (float)z);
+                v1 = g * g;
+                v2 = g * z;
             }
-            d1 += rr;
-            d2 += rz;
         } else {
-            double p;
-            if (MODE == CAM_MATVEC) p = P.p[vo];
-            else p = first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo));
+            double p = 0.0;
+            if (act) {
+                if (MODE == CAM_MATVEC) p = P.p[vo];
+                else p = first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo));
+            }
             double bp = 0.0;
 #pragma unroll
-            for (int b = 0; b < 9; ++b) bp += __ldg(P.Bd + 81 * (int64_t)cam + a * 9 + b) * lane9(p, b);
-            const double q = bp - cs;
-            double pq = lane < 9 ? p * q : 0.0;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) pq += __shfl_xor_sync(full, pq, d);
-            if (lane < 9) {
+            for (int b = 0; b < 9; ++b) {
+                const double pb = __shfl_sync(full, p, 9 * sub + b);
+                if (act) bp = fma(__ldg(P.Bd + 81 * (int64_t)cm + a * 9 + b), pb, bp);
+            }
+            if (act) {
+                const double q = bp - cs;
                 stcg(P.q + vo, q);
                 if (MODE == CAM_ITER) {
                     stcg(p_cur + vo, p);
                     if (pT_cur) stcg(pT_cur + vo, (T)p);
                 }
+                v1 = p * q;
             }
-            d1 += pq;
         }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            v1 += __shfl_xor_sync(full, v1, d);
+            v2 += __shfl_xor_sync(full, v2, d);
+        }
+        d1 += v1;
+        d2 += v2;
     }
     // CTA partials in a fixed order (warp w's cameras, then a tree over warps);
-    // d1, d2 are warp-uniform, so only lane 0 contributes
-    return block_sum2_all(lane == 0 ? d1 : 0.0, lane == 0 ? d2 : 0.0, sb);
+    // d1, d2 are already warp-uniform, so no per-warp shuffle tree is needed
+    return cta_sum2(lane == 0 ? d1 : 0.0, lane == 0 ? d2 : 0.0, false, sb);
 }
 
 // Search direction into shared memory (dense nc x 9, in T): p = z + beta p_prev
@@ -576,27 +593,24 @@ __device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_
     __syncthreads();
 }
 
-// Sum of n partials in a fixed order (every CTA gets the same value).
-__device__ __forceinline__ double block_sum2_all_x(double x, double *sb);
-__device__ __forceinline__ double sum_parts(const double *parts, int n, double *sb) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += ldcg(parts + i);
-    return block_sum2_all_x(acc, sb);
-}
-
-// Two block-wide sums in a fixed tree order (sb holds 64 doubles); every
-// thread gets the result.
-__device__ __forceinline__ double2 block_sum2_all(double x, double y, double *sb) {
+// CTA-wide sums of two doubles in a fixed tree order; every thread gets the
+// result.  With warp_data (warp-uniform) the warp first reduces its lanes by a
+// shuffle tree; without it lane 0's value is taken as the warp's sum, so warps
+// with nothing (or a single value) skip the tree: GB300's FP64 pipe takes 16
+// cycles per warp instruction.  Warp 0 then adds the per-warp sums.
+__device__ __forceinline__ double2 cta_sum2(double x, double y, bool warp_data, double *sb) {
     __shared__ double2 s_out2;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        y += __shfl_down_sync(0xffffffffu, y, o);
-    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (warp_data) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+    }
     __syncthreads();
     if (lane == 0) {
-        sb[wid] = x;
+        sb[wid] = x;  // lane 0 holds the warp's sum (or its only value)
         sb[32 + wid] = y;
     }
     __syncthreads();
@@ -614,16 +628,21 @@ __device__ __forceinline__ double2 block_sum2_all(double x, double y, double *sb
     return s_out2;
 }
 
-__device__ __forceinline__ double block_sum2_all_x(double x, double *sb) { return block_sum2_all(x, 0.0, sb).x; }
 
-// Two sums of n partials each, in one pass; every CTA gets the same values.
+// Two sums of n per-CTA partials (n <= blockDim.x: one load per thread, then
+// shuffle trees only in the warps that hold partials); every thread of every
+// CTA gets the same values.
 __device__ __forceinline__ double2 sum_parts2(const double *a, const double *b, int n, double *sb) {
     double x = 0.0, y = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         x += ldcg(a + i);
-        y += ldcg(b + i);
+        y += b ? ldcg(b + i) : 0.0;
     }
-    return block_sum2_all(x, y, sb);
+    return cta_sum2(x, y, (int)(threadIdx.x & ~31u) < n, sb);
+}
+
+__device__ __forceinline__ double sum_parts(const double *parts, int n, double *sb) {
+    return sum_parts2(parts, nullptr, n, sb).x;
 }
 
 // ---------------------------------------------------------------------------
@@ -725,13 +744,15 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             const double pq = sum_parts(part_pq, G, sb);
             if (!(pq > 0.0) || !isfinite(pq)) break;
             const double alpha = rho / pq;
-            // x += alpha p; r -= alpha q; z = B~^-1 r; partial r.r and r.z
+            // x += alpha p; r -= alpha q; z = B~^-1 r; partial r.r and r.z, over this
+            // CTA's own cameras (three per warp)
             {
                 double rr = 0.0, rz = 0.0;
-                for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
-                    const int cam = w * 3 + my_sub;
-                    const bool act = lane < 27 && cam < P.nc;
-                    const int64_t vo = (int64_t)(act ? cam : 0) * kVec + row;
+                const int cb = P.cta_cam[blockIdx.x], ce = P.cta_cam[blockIdx.x + 1];
+                for (int c0 = cb + 3 * wid; c0 < ce; c0 += 3 * nwarp) {
+                    const int cam = c0 + my_sub;
+                    const bool act = lane < 27 && cam < ce;
+                    const int64_t vo = (int64_t)(act ? cam : c0) * kVec + row;
                     double rv = 0.0;
                     if (act) {
                         stcg(P.x + vo, fma(alpha, ldcg(p_cur + vo), ldcg(P.x + vo)));
@@ -742,7 +763,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
 #pragma unroll
                     for (int c = 0; c < 9; ++c) {
                         const double rc = __shfl_sync(full, rv, my_sub * 9 + c);
-                        if (act) z += __ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c) * rc;
+                        if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c), rc, z);
                     }
                     if (act) {
                         stcg(P.z + vo, z);
@@ -751,11 +772,11 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                         rz += rv * z;
                     }
                 }
-                const double s_rr = block_sum(rr, sb);
-                const double s_rz = block_sum(rz, sb);
+                const bool has = cb + 3 * wid < ce;
+                const double2 sr = cta_sum2(rr, rz, has, sb);
                 if (threadIdx.x == 0) {
-                    stcg(part_rr + blockIdx.x, s_rr);
-                    stcg(part_rho + blockIdx.x, s_rz);
+                    stcg(part_rr + blockIdx.x, sr.x);
+                    stcg(part_rho + blockIdx.x, sr.y);
                 }
             }
             if (!(ok = barrier())) break;
