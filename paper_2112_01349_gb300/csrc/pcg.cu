@@ -341,6 +341,7 @@ template <typename T>
 __device__ __forceinline__ void camera_y(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *y);
 template <typename T>
 __device__ __forceinline__ void camera_acc(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *acc);
+__device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, float s1, float *y);
 template <>
 __device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
                                                 float *y) {
@@ -350,6 +351,9 @@ __device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, 
         s0 *= sw;
         s1 *= sw;
     }
+    camera_y_x(ct, X, s0, s1, y);
+}
+__device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, float s1, float *y) {
     const float P0 = ct[0] * X.x + ct[1] * X.y + ct[2] * X.z + ct[18];
     const float P1 = ct[3] * X.x + ct[4] * X.y + ct[5] * X.z + ct[19];
     const float P2 = ct[6] * X.x + ct[7] * X.y + ct[8] * X.z + ct[20];
@@ -444,11 +448,19 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
         for (int s0 = b0; s0 < b1; s0 += 32 * U) {
+            // all streamed loads of the batch first, then the dependent s gathers
             int pm[U];
+            float4 X[U];
+            float sw[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int s = s0 + u * 32 + lane;
-                pm[u] = s < b1 ? __ldcs(P.cm2pm + s) : -1;
+                const bool in = s < b1;
+                pm[u] = in ? __ldcs(P.cm2pm + s) : -1;
+                if (sizeof(T) == 4) {
+                    X[u] = in ? __ldcs((const float4 *)P.Xcm + s) : make_float4(0.f, 0.f, -1.f, 0.f);
+                    sw[u] = (in && P.loss != MBA_LOSS_NONE) ? __ldcs((const float *)P.swc + s) : 1.f;
+                }
             }
             T2 sv[U];
 #pragma unroll
@@ -456,7 +468,16 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 if (pm[u] >= 0) sv[u] = ldcg(sbuf + pm[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (pm[u] >= 0) camera_acc<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, acc);
+                if (pm[u] >= 0) {
+                    if (sizeof(T) == 4) {
+                        float y[9];
+                        camera_y_x((const float *)ct, X[u], (float)sv[u].x * sw[u], (float)sv[u].y * sw[u], y);
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) acc[a] += (T)y[a];
+                    } else {
+                        camera_acc<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, acc);
+                    }
+                }
             }
         }
         T mine = T(0);
