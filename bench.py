@@ -175,6 +175,25 @@ def run_reference(args, rank, world):
     return 0
 
 
+def profile_case(precision: str, scale: float) -> int:
+    """A small solve for ncu captures: the workload scaled by `scale` (0.3 gives
+    1.5M observations, a Jacobian stream larger than L2), 2 LM iterations with
+    PCG <= 30, so one capture holds a bounded number of PCG launches."""
+    import torch
+
+    from paper_2112_01349_gb300 import _build, mba
+    from scenes import config_scene
+
+    torch.cuda.set_device(0)
+    _build.build()
+    sc = config_scene(CONFIG, scale=scale)
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision) as pr:
+        s = pr.solve(max_iter=2, pcg_max_iter=30, collect_timing=1)
+    print(json.dumps({"profile_case": precision, "scale": scale, "nc": sc.nc, "np": sc.np_, "n": sc.n,
+                      "pcg_iters_total": s["pcg_iters_total"], "final_cost": s["final_cost"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,7 +201,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["fp32", "fp64"], default=None,
+                    help="profiling aid: run one small solve of the workload (see --scale) and exit; "
+                         "prints no bench line")
+    ap.add_argument("--scale", type=float, default=0.3, help="camera/point scale of --profile-case")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case, args.scale)
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local, dist = dist_setup(args.gpus)
