@@ -66,6 +66,8 @@ def _load():
             lib.orc_schur.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, P, P, P, P]
             lib.orc_lm_solve.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, C.c_int, C.c_int, dbl,
                                          C.c_int, dbl, dbl, dbl, C.c_int, P, P, P, P]
+            lib.orc_adjoint.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, C.c_int, dbl, P, P,
+                                        P, P, P, P]
             lib.orc_num_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -198,3 +200,18 @@ def lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=10, pcg_max=50, pcg_tol=1
         raise RuntimeError(f"orc_lm_solve failed: {rc}")
     trace = [{f: getattr(tr[i], f) for f, _ in Trace._fields_} for i in range(it.value)]
     return dict(cameras=cams, points=pts, trace=trace, iterations=it.value, final_cost=fc.value, radius=rad.value)
+
+
+def adjoint(cams, pts, obs, cam_idx, pt_idx, mu, gbar_c, gbar_p, loss="none", delta=0.0, damping="diag",
+            pcg_max=500, pcg_tol=1e-14):
+    """dict(grad_obs (n,2), grad_c0 (nc,9), grad_p0 (np,3), pcg_iters) for upstream gradient (gbar_c, gbar_p)."""
+    cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
+    gc, gp = _f64(gbar_c, (nc, 9)), _f64(gbar_p, (np_, 3))
+    go, gc0, gp0 = np.zeros((n, 2)), np.zeros((nc, 9)), np.zeros((np_, 3))
+    it = C.c_int()
+    rc = _load().orc_adjoint(nc, np_, n, _p(cams), _p(pts), _p(obs), _p(ci), _p(pi), LOSS[loss], float(delta),
+                             float(mu), DAMPING[damping], int(pcg_max), float(pcg_tol), _p(gc), _p(gp), _p(go),
+                             _p(gc0), _p(gp0), C.byref(it))
+    if rc:
+        raise RuntimeError(f"orc_adjoint failed: {rc}")
+    return dict(grad_obs=go, grad_c0=gc0, grad_p0=gp0, pcg_iters=it.value)

@@ -752,6 +752,55 @@ int orc_schur(int32_t nc, int32_t np, int64_t n, const double *cams, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adjoint of the solved state (differentiable BA layer; the paper has no     */
+/* counterpart).  At x* with M = H(x*) + mu D (the damped Gauss-Newton matrix */
+/* of the last step), solve M v = gbar by the same Schur elimination and PCG  */
+/* (gbar = dL/dx*, cameras then points).  By the implicit function theorem on */
+/* the optimality condition J^T W e = 0 with e = pi(x) - u, d(x*) by du_k is  */
+/* M^-1 J_k^T W_k, so dL/du_k = W_k J_k v (2 values per observation).  The    */
+/* initial estimate enters through the damping of the last step (proximal     */
+/* reading): dL/dx0 = mu D v.                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
+                const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
+                int pcg_max, double pcg_tol, const double *gbar_c, const double *gbar_p, double *grad_obs,
+                double *grad_c0, double *grad_p0, int *pcg_iters) {
+    lin_t L;
+    int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
+    if (rc) return rc;
+    linearise(&L, cams, pts, obs, loss, delta);
+    /* diagonal damping terms D before the right-hand side is replaced */
+    double *Dc = malloc(sizeof(double) * 9 * (size_t)nc), *Dp = malloc(sizeof(double) * 3 * (size_t)np);
+    double *vc = malloc(sizeof(double) * 9 * (size_t)nc), *vp = malloc(sizeof(double) * 3 * (size_t)np);
+    for (int32_t i = 0; i < nc; ++i)
+        for (int a = 0; a < 9; ++a) Dc[9 * (int64_t)i + a] = damp_term(damping, L.Hpp[81 * (int64_t)i + a * 9 + a]);
+    for (int32_t j = 0; j < np; ++j)
+        for (int a = 0; a < 3; ++a) Dp[3 * (int64_t)j + a] = damp_term(damping, L.Hll[9 * (int64_t)j + a * 3 + a]);
+    memcpy(L.v, gbar_c, sizeof(double) * 9 * (size_t)nc);
+    memcpy(L.w, gbar_p, sizeof(double) * 3 * (size_t)np);
+    int it = 0;
+    rc = damped_step(&L, mu, damping, 0, pcg_max, pcg_tol, vc, vp, &it, NULL);
+    if (!rc) {
+        for (int64_t k = 0; k < n; ++k) {
+            const double *Jc = L.Jc + 18 * k, *Jp = L.Jp + 6 * k;
+            const double *xc = vc + 9 * (int64_t)cam_idx[k], *xp = vp + 3 * (int64_t)pt_idx[k];
+            for (int r = 0; r < 2; ++r) {
+                double s = 0.0;
+                for (int a = 0; a < 9; ++a) s += Jc[r * 9 + a] * xc[a];
+                for (int a = 0; a < 3; ++a) s += Jp[r * 3 + a] * xp[a];
+                grad_obs[2 * k + r] = L.W[k] * s;
+            }
+        }
+        for (int64_t t = 0; t < 9 * (int64_t)nc; ++t) grad_c0[t] = mu * Dc[t] * vc[t];
+        for (int64_t t = 0; t < 3 * (int64_t)np; ++t) grad_p0[t] = mu * Dp[t] * vp[t];
+        if (pcg_iters) *pcg_iters = it;
+    }
+    free(Dc); free(Dp); free(vc); free(vp);
+    lin_free(&L);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Levenberg-Marquardt driver (Alg. 1 outer loop; Ceres-style trust region). */
 /* Readings: radius starts at initial_radius, mu = 1/radius; step accepted    */
 /* iff the model decrease is positive, the new cost is finite and the gain    */

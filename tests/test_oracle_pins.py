@@ -273,3 +273,23 @@ def test_accepted_cost_is_monotone_and_reaches_noise_floor():
     dof = 9 * sc.nc + 3 * sc.np_
     expected = 0.5 * 0.25 * (2 * sc.n - dof)
     assert r["final_cost"] == pytest.approx(expected, rel=0.05)
+
+
+@pytest.mark.parametrize("loss", ["none", "huber"])
+def test_adjoint_matches_dense_implicit_function_gradient(loss):
+    """dL/du_k = W_k J_k M^-1 gbar and dL/dx0 = mu D M^-1 gbar with a dense solve."""
+    sc = make_scene(4, 25, sigma=2.0, seed=15, outlier_frac=0.1)
+    mu = 1e-2
+    rng = np.random.default_rng(2)
+    gc, gp = rng.normal(size=(sc.nc, 9)), rng.normal(size=(sc.np_, 3))
+    r = oracle.adjoint(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, gc, gp, loss=loss,
+                       delta=2.0)
+    J, Wr, e, _ = _dense_system(sc, loss, 2.0)
+    H = J.T @ (Wr[:, None] * J)
+    d = np.clip(np.diag(H), 1e-6, 1e32)
+    v = np.linalg.solve(H + mu * np.diag(d), np.concatenate([gc.reshape(-1), gp.reshape(-1)]))
+    g_obs = (Wr * (J @ v)).reshape(-1, 2)
+    np.testing.assert_allclose(r["grad_obs"], g_obs, atol=1e-8 * np.abs(g_obs).max())
+    g0 = mu * d * v
+    np.testing.assert_allclose(np.concatenate([r["grad_c0"].reshape(-1), r["grad_p0"].reshape(-1)]), g0,
+                               atol=1e-8 * np.abs(g0).max())
