@@ -304,6 +304,32 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = LM_ITERS * args.steps * world / e2e_s
 
+    # differentiable-layer workload (200 cameras, 50k points, ~250k observations,
+    # FP32-mixed): forward LM to convergence, then the adjoint of the solution
+    layer = None
+    if rank == 0:
+        sc4 = config_scene(4)
+        rng = np.random.default_rng(0)
+        gc4, gp4 = rng.normal(size=(sc4.nc, 9)), rng.normal(size=(sc4.np_, 3))
+        with mba.Problem(sc4.cameras, sc4.points, sc4.observations, sc4.cam_idx, sc4.pt_idx, precision="fp32",
+                         stream=stream) as pr4:
+            fwd, adj = [], []
+            for rep in range(3):
+                pr4.reset()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                s4 = pr4.solve(max_iter=100, pcg_max_iter=100, pcg_rel_tol=1e-10, function_tol=1e-12)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                a4 = pr4.adjoint(gc4, gp4, mu=-1.0, pcg_max_iter=500, pcg_rel_tol=1e-10)
+                torch.cuda.synchronize()
+                fwd.append(t1 - t)
+                adj.append(time.perf_counter() - t1)
+        layer = {"workload": f"differentiable layer: {sc4.nc} cameras, {sc4.np_} points, {sc4.n} observations, "
+                             "FP32-mixed, LM to |dF|/F < 1e-12 (<= 100 iterations), then the adjoint",
+                 "forward_ms": 1e3 * min(fwd), "adjoint_ms": 1e3 * min(adj), "lm_iterations": s4["iterations"],
+                 "adjoint_pcg_iters": a4["pcg_iters"]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -340,6 +366,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": s32 and sum(s["kernel_launches"] for s in s32),
+        "layer": layer,
         "clocks": clk32,
     }
     print(json.dumps(line), flush=True)

@@ -181,6 +181,27 @@ mba_status mba_step(mba_problem *problem, double mu, const mba_solver_options *o
                     int32_t *pcg_iters, double *model_decrease);
 
 /*
+ * Gradient of the solved state for a differentiable BA layer (the paper has
+ * no counterpart; it reuses the Schur elimination and PCG of Alg. 2/3).  At
+ * the current parameters x* (normally the result of mba_solve), with
+ * M = H(x*) + mu D the damped Gauss-Newton matrix, v = M^-1 gbar is found by
+ * Schur elimination, PCG (opt->pcg_max_iter, opt->pcg_rel_tol, opt->damping)
+ * and back-substitution, gbar = (grad_cameras nc x 9, grad_points np x 3) being
+ * dL/dx*.  By the implicit function theorem on J^T W e = 0:
+ *   grad_obs (n x 2, caller's order)  dL/du_k = W_k J_k v
+ *   grad_init_cam (nc x 9), grad_init_pt (np x 3)  dL/dx0 = mu D v, the initial
+ *     estimate entering through the damping of the last (proximal) LM step.
+ * mu < 0 takes the damping of the last accepted step of the last mba_solve
+ * (the proximal step that produced x*); the exact implicit-function gradient
+ * of the observations is the limit mu -> 0, so a small explicit mu gives it
+ * more closely (the 7-DoF gauge keeps H singular at mu = 0).  Outputs may be NULL.
+ * The parameters are not changed.
+ */
+mba_status mba_adjoint(mba_problem *problem, const mba_solver_options *opt, double mu, const double *grad_cameras,
+                       const double *grad_points, double *grad_obs, double *grad_init_cam, double *grad_init_pt,
+                       int32_t *pcg_iters);
+
+/*
  * Cost without any device allocation, for callers that cannot allocate
  * device memory (a framework that owns every allocation through its own pool,
  * a real-time loop where allocating is not allowed, code that must not fail

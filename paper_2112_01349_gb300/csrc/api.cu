@@ -59,6 +59,7 @@ struct mba_problem {
     int nb_chunk = 0, nb_cost = 0;
     int pcg_grid = 0;
     mba_iteration *trace_dev = nullptr;
+    double last_mu = -1.0;  // damping of the last accepted step of the last solve
 };
 
 extern "C" {
@@ -671,7 +672,53 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         }
     }
     for (int i = 0; i < ne; ++i) cudaEventDestroy(ev[i]);
+    if (hs.accepted_total > 0) pr->last_mu = hs.mu_accepted;
     return st;
+}
+
+mba_status mba_adjoint(mba_problem *pr, const mba_solver_options *opt, double mu, const double *grad_cameras,
+                       const double *grad_points, double *grad_obs, double *grad_init_cam, double *grad_init_pt,
+                       int32_t *pcg_iters) {
+    g_err.clear();
+    if (!pr || !grad_cameras || !grad_points) return fail(MBA_ERR_INVALID_ARG, "NULL argument");
+    mba_solver_options o;
+    mba_solver_options_default(&o);
+    if (opt) o = *opt;
+    if (!valid_solver_opts(o)) return fail(MBA_ERR_INVALID_ARG, "bad solver options");
+    if (mu < 0.0) mu = pr->last_mu;
+    if (!(mu >= 0.0)) return fail(MBA_ERR_INVALID_ARG, "mu < 0 and no accepted step of a previous solve");
+    Prob &P = pr->P;
+    cudaStream_t s = pr->stream;
+    mba_status st = prepare_step(pr, mu, o.damping);
+    if (st) return st;
+    // right-hand side gbar in place of the gradient (v for cameras, w for points)
+    CK(cudaMemcpyAsync(P.v, grad_cameras, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.w, grad_points, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyHostToDevice, s));
+    const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
+    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+    CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));  // dp = v_p
+    DevState hs;
+    st = check_device_state(pr, &hs);
+    if (st) return st;
+    if (grad_obs) {
+        const int64_t slice = P.n < kEvalSlice ? P.n : kEvalSlice;
+        for (int64_t k0 = 0; k0 < P.n; k0 += slice) {
+            const int64_t m = (P.n - k0) < slice ? (P.n - k0) : slice;
+            CK(launch_adjoint_obs(P, pr->orig_cam + k0, pr->orig_pt + k0, pr->orig_uv + k0, m, pr->eval_stage, s));
+            CK(cudaMemcpyAsync(grad_obs + 2 * k0, pr->eval_stage, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+    if (grad_init_cam || grad_init_pt) {
+        CK(launch_adjoint_init(P, o.damping, mu, s));
+        if (grad_init_cam)
+            CK(cudaMemcpyAsync(grad_init_cam, P.cams_new, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyDeviceToHost, s));
+        if (grad_init_pt)
+            CK(cudaMemcpyAsync(grad_init_pt, P.pts_new, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (pcg_iters) *pcg_iters = hs.pcg_iters;
+    return MBA_OK;
 }
 
 }  // extern "C"

@@ -62,6 +62,7 @@ __global__ void lm_update_kernel(DevState *st, mba_iteration *trace, int trace_c
         st->factor = 2.0;
         if (function_tol > 0.0 && fabs(F - Fn) < function_tol * F) st->done = 1;
         st->cost = Fn;
+        st->mu_accepted = st->mu;
         st->accepted_total += 1;
     } else {
         radius = radius / st->factor;

@@ -35,6 +35,7 @@ struct DevState {
     double cost_new, model_dec, gain;
     double pcg_rel_res;
     double mu_override;   // >= 0: use this mu instead of 1/radius
+    double mu_accepted;   // mu of the last accepted step (the step that produced the current x)
     int32_t relin;        // 1: the linearisation must be rebuilt before the next solve
     int32_t accepted;     // decision of the last iteration
     int32_t done;         // 1: stop issuing work (function_tol met or error)
@@ -375,6 +376,11 @@ cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long l
 int pcg_grid_size(const Prob &P);
 void plan_pcg_smem(Prob &P);
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s);
+
+// adjoint.cu
+cudaError_t launch_adjoint_obs(const Prob &P, const int32_t *ci, const int32_t *pi, const double2 *uv, int64_t m,
+                               double *out, cudaStream_t s);
+cudaError_t launch_adjoint_init(const Prob &P, int damping, double mu, cudaStream_t s);
 
 // lm.cu
 cudaError_t launch_state_init(const Prob &P, double radius, double mu_override, int keep_cost, cudaStream_t s);

@@ -92,6 +92,7 @@ def load():
             "mba_schur_matvec": (C.c_int, [P, dbl, i32, P, P]),
             "mba_step": (C.c_int, [P, dbl, P, P, P, P, P]),
             "mba_cost_noalloc": (C.c_int, [P, i32, P, i32, P, P, P, i64, i32, dbl, P, P]),
+            "mba_adjoint": (C.c_int, [P, P, dbl, P, P, P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
         }
@@ -285,6 +286,21 @@ def mba_step(h, mu, **opts):
     return dict(dc=dc, dp=dp, pcg_iters=it.value, model_dec=md.value)
 
 
+def mba_adjoint(h, grad_cameras, grad_points, mu=-1.0, **opts):
+    """dict(grad_obs (n,2), grad_init_cam (nc,9), grad_init_pt (np,3), pcg_iters) for dL/dx* = (grad_cameras,
+    grad_points); mu < 0 uses the damping of the last solve's last accepted step."""
+    info = mba_problem_info(h)
+    o = solver_options(**opts)
+    gc = np.ascontiguousarray(grad_cameras, dtype=np.float64).reshape(info["nc"], 9)
+    gp = np.ascontiguousarray(grad_points, dtype=np.float64).reshape(info["np"], 3)
+    go = np.zeros((info["n"], 2))
+    gc0, gp0 = np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
+    it = C.c_int32()
+    f = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(load().mba_adjoint(h, C.byref(o), float(mu), f(gc), f(gp), f(go), f(gc0), f(gp0), C.byref(it)))
+    return dict(grad_obs=go, grad_init_cam=gc0, grad_init_pt=gp0, pcg_iters=it.value)
+
+
 def mba_cost_noalloc(d_cameras, nc, d_points, np_, d_observations, d_cam_idx, d_pt_idx, n, loss="none",
                      huber_delta=0.0, d_cost=None, stream=None):
     """Cost from caller-owned device arrays (integer device addresses); no allocation.
@@ -349,3 +365,6 @@ class Problem:
 
     def step(self, mu, **opts):
         return mba_step(self.handle, mu, **opts)
+
+    def adjoint(self, grad_cameras, grad_points, mu=-1.0, **opts):
+        return mba_adjoint(self.handle, grad_cameras, grad_points, mu, **opts)

@@ -1,0 +1,125 @@
+"""Differentiable BA layer: the CUDA adjoint against the CPU oracle's adjoint,
+and against central finite differences of a solved problem."""
+import numpy as np
+import pytest
+
+import oracle
+from scenes import make_scene
+from tests.gpu_util import rel_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mba():
+    from paper_2112_01349_gb300 import _build, mba as m
+
+    _build.build()
+    m.load()
+    return m
+
+
+@pytest.mark.parametrize("kind,precision,tol", [("small", "fp64", 1e-7), ("ragged", "fp64", 1e-7),
+                                                ("huber", "fp64", 1e-7), ("ragged", "fp32", 2e-3)])
+def test_adjoint_matches_oracle(mba, kind, precision, tol):
+    sc = {"small": lambda: make_scene(6, 400, sigma=0.5, seed=21),
+          "ragged": lambda: make_scene(40, 9001, track=("geom", 0.25), sigma=1.0, seed=22),
+          "huber": lambda: make_scene(12, 3001, track=("geom", 0.25), sigma=1.0, outlier_frac=0.05, seed=23)}[kind]()
+    loss = "huber" if kind == "huber" else "none"
+    mu = 1e-2
+    rng = np.random.default_rng(7)
+    gc, gp = rng.normal(size=(sc.nc, 9)), rng.normal(size=(sc.np_, 3))
+    ref = oracle.adjoint(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, gc, gp, loss=loss,
+                         delta=2.0, pcg_max=1000, pcg_tol=1e-14)
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision, loss=loss,
+                     huber_delta=2.0) as pr:
+        r = pr.adjoint(gc, gp, mu=mu, pcg_max_iter=1000, pcg_rel_tol=1e-14)
+    rel_close(r["grad_obs"], ref["grad_obs"], tol, "grad_obs")
+    rel_close(r["grad_init_cam"], ref["grad_c0"], tol, "grad_init_cam")
+    rel_close(r["grad_init_pt"], ref["grad_p0"], tol, "grad_init_pt")
+
+
+def _pixels(cams, pts, sc):
+    _, e, *_ = oracle.evaluate(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx, jacobians=False)
+    return e + sc.observations
+
+
+def test_adjoint_matches_finite_differences(mba):
+    """L(x*(u)) = sum_k c_k . pi_k(x*) is invariant under the 7-DoF gauge, so the
+    finite difference of a converged solve is well defined; compare with the
+    adjoint's dL/du along random observation directions (step 1e-4 px).  The
+    adjoint uses the Gauss-Newton matrix, whose error against the true Hessian
+    scales with the residuals, hence a low-noise scene (0.01 px) and a small mu
+    (the exact implicit-function gradient is the limit mu -> 0)."""
+    sc = make_scene(8, 300, sigma=0.01, seed=41)
+    opts = dict(max_iter=100, pcg_max_iter=500, pcg_rel_tol=1e-14, function_tol=1e-15)
+    rng = np.random.default_rng(3)
+    c = rng.normal(size=(sc.n, 2))
+
+    def solve(obs):
+        with mba.Problem(sc.cameras, sc.points, obs, sc.cam_idx, sc.pt_idx) as pr:
+            pr.solve(**opts)
+            return pr.parameters()
+
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx) as pr:
+        pr.solve(**opts)
+        cams, pts = pr.parameters()
+        _, _, Jc, Jp, _ = oracle.evaluate(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx)
+        gc, gp = np.zeros((sc.nc, 9)), np.zeros((sc.np_, 3))
+        np.add.at(gc, sc.cam_idx, np.einsum("kr,kra->ka", c, Jc))
+        np.add.at(gp, sc.pt_idx, np.einsum("kr,kra->ka", c, Jp))
+        r = pr.adjoint(gc, gp, mu=1e-9, pcg_max_iter=1000, pcg_rel_tol=1e-14)
+    h = 1e-4
+    errs = []
+    for _ in range(8):
+        d = rng.normal(size=(sc.n, 2))
+        Lp = float(np.sum(c * _pixels(*solve(sc.observations + h * d), sc)))
+        Lm = float(np.sum(c * _pixels(*solve(sc.observations - h * d), sc)))
+        fd = (Lp - Lm) / (2 * h)
+        ad = float(np.sum(r["grad_obs"] * d))
+        errs.append(abs(fd - ad) / max(abs(fd), 1e-12))
+    assert max(errs) < 1e-3, errs
+
+
+def test_ba_layer_backward_is_the_adjoint(mba):
+    import torch
+
+    from paper_2112_01349_gb300.layer import ba_layer
+
+    sc = make_scene(6, 200, sigma=0.5, seed=43)
+    obs = torch.tensor(sc.observations, requires_grad=True)
+    c0 = torch.tensor(sc.cameras, requires_grad=True)
+    p0 = torch.tensor(sc.points, requires_grad=True)
+    cams, pts = ba_layer(obs, c0, p0, torch.tensor(sc.cam_idx), torch.tensor(sc.pt_idx), max_iter=30,
+                         pcg_max_iter=200, pcg_rel_tol=1e-12, function_tol=1e-14)
+    rng = np.random.default_rng(4)
+    wc, wp = torch.tensor(rng.normal(size=cams.shape)), torch.tensor(rng.normal(size=pts.shape))
+    (cams * wc).sum().add((pts * wp).sum()).backward()
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx) as pr:
+        s = pr.solve(max_iter=30, pcg_max_iter=200, pcg_rel_tol=1e-12, function_tol=1e-14)
+        r = pr.adjoint(wc.numpy(), wp.numpy(), mu=-1.0, pcg_max_iter=500, pcg_rel_tol=1e-12)
+    assert s["iterations"] <= 30
+    np.testing.assert_allclose(obs.grad.numpy(), r["grad_obs"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(c0.grad.numpy(), r["grad_init_cam"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(p0.grad.numpy(), r["grad_init_pt"], rtol=1e-9, atol=1e-12)
+
+
+def test_layer_workload_adjoint_fp32_mixed(mba):
+    """Differentiable-layer workload (200 cameras, 50k points, ~250k observations):
+    solve to convergence in FP32-mixed, then the adjoint against the oracle's
+    adjoint at the same state and damping."""
+    from scenes import config_scene
+
+    sc = config_scene(4)
+    rng = np.random.default_rng(9)
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision="fp32") as pr:
+        s = pr.solve(max_iter=100, pcg_max_iter=100, pcg_rel_tol=1e-10, function_tol=1e-12)
+        cams, pts = pr.parameters()
+        gc, gp = rng.normal(size=(sc.nc, 9)), rng.normal(size=(sc.np_, 3))
+        mu = 1e-4
+        r = pr.adjoint(gc, gp, mu=mu, pcg_max_iter=1000, pcg_rel_tol=1e-10)
+    assert s["accepted"] > 0
+    ref = oracle.adjoint(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx, mu, gc, gp, pcg_max=1000, pcg_tol=1e-12)
+    rel_close(r["grad_obs"], ref["grad_obs"], 5e-3, "grad_obs")
+    rel_close(r["grad_init_cam"], ref["grad_c0"], 5e-3, "grad_init_cam")
+    rel_close(r["grad_init_pt"], ref["grad_p0"], 5e-3, "grad_init_pt")
