@@ -227,6 +227,103 @@ mba_status mba_cost_noalloc(const double *d_cameras, int32_t nc, const double *d
                             const double *d_observations, const int32_t *d_cam_idx, const int32_t *d_pt_idx,
                             int64_t n, int32_t loss, double huber_delta, double *d_cost, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched local bundle adjustment: many small independent problems
+ * ("windows", e.g. the sliding windows of a visual SLAM back end) solved in
+ * ONE persistent kernel launch, captured once as a CUDA graph.  Each window
+ * runs its own Levenberg-Marquardt loop of Alg. 1 (same trust-region rule,
+ * Schur elimination of Sec. 3 Eq. 3, PCG of Alg. 2 with the implicit product
+ * of Alg. 3, back-substitution of Eq. 4 as mba_solve), with its own radius,
+ * accept/reject decisions and stopping test; windows never exchange data.
+ * The paper solves one problem at a time; batching is a form of this library.
+ *
+ * Windows are given concatenated: window w owns cameras
+ * [cam_offsets[w], cam_offsets[w+1]), points [pt_offsets[w], pt_offsets[w+1])
+ * and observations [obs_offsets[w], obs_offsets[w+1]) of the arrays below
+ * (offset arrays have n_windows + 1 entries, start at 0 and never decrease).
+ * cam_idx / pt_idx are LOCAL to the window (0 <= cam_idx < the window's
+ * camera count).  Limits: 1 <= cameras per window <= 64, every camera and
+ * point of a window observed at least once, at most 2^31 - 1 observations in
+ * total; otherwise MBA_ERR_INVALID_ARG.  Non-finite inputs give
+ * MBA_ERR_NONFINITE.  Precision and loss come from opt (as for
+ * mba_problem_create); the FP32-mixed form keeps the PCG dot products, the
+ * block inversions and the accept/reject cost in FP64.
+ * ------------------------------------------------------------------------ */
+typedef struct mba_batch mba_batch;
+
+typedef struct {
+    int32_t iterations;        /* LM iterations run, accepted or not */
+    int32_t accepted;          /* accepted steps */
+    int32_t pcg_iters_total;   /* PCG iterations of the forward solve */
+    int32_t status;            /* mba_status of this window */
+    double initial_cost;       /* F = 1/2 sum rho(|e|^2) before the first iteration (FP64) */
+    double final_cost;
+    double final_radius;
+    double mu_accepted;        /* mu of the last accepted step; -1 if none */
+    int32_t adjoint_pcg_iters; /* PCG iterations of the adjoint solve (0 if none) */
+    int32_t pad;
+} mba_window_summary;
+
+/* Launch schedule of the batched kernel.  threads_per_cta: 256 or 512;
+ * ctas_per_sm: resident windows per SM (1..8, capped by occupancy).  Zero
+ * fields choose automatically.  The schedule changes the order of the FP32 /
+ * FP64 partial sums inside a window (results agree to rounding), never the
+ * method; a given schedule gives the same bits on every run. */
+typedef struct {
+    int32_t threads_per_cta;
+    int32_t ctas_per_sm;
+} mba_batch_schedule;
+
+/* Upstream gradient for the adjoint of every window (same form as
+ * mba_adjoint): grad_cameras (total cameras x 9) and grad_points (total
+ * points x 3), host arrays in the concatenated order.  With mu < 0 the
+ * adjoint of a window uses mu of its last accepted step, and a window without
+ * an accepted step (it returned its input unchanged) gets an observation
+ * gradient of 0 and the upstream gradient itself as initial-estimate gradient.
+ * Windows hold at most 2^24 - 1 points. */
+typedef struct {
+    const double *grad_cameras;
+    const double *grad_points;
+    int32_t pcg_max_iter;      /* e.g. 500 */
+    int32_t pad;
+    double pcg_rel_tol;        /* e.g. 1e-12 */
+    double mu;                 /* >= 0: damping of the adjoint system of every window (as the mu
+                                  argument of mba_adjoint); < 0: each window's last accepted mu */
+} mba_batch_adjoint;
+
+mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const int64_t *pt_offsets,
+                            const int64_t *obs_offsets, const double *cameras, const double *points,
+                            const double *observations, const int32_t *cam_idx, const int32_t *pt_idx,
+                            const mba_problem_options *opt, mba_batch **out);
+void mba_batch_destroy(mba_batch *batch);
+/* Sizes: windows, total cameras / points / observations, largest window camera count. */
+mba_status mba_batch_info(const mba_batch *batch, int32_t *n_windows, int64_t *n_cameras, int64_t *n_points,
+                          int64_t *n_observations, int32_t *max_window_cameras);
+mba_status mba_batch_set_schedule(mba_batch *batch, const mba_batch_schedule *schedule);
+mba_status mba_batch_get_schedule(const mba_batch *batch, mba_batch_schedule *schedule);
+/* Times each admissible schedule on one solve of this batch (from the current
+ * parameters, which are restored afterwards) and keeps the fastest.  The
+ * solve options decide the work timed. *ms_best may be NULL. */
+mba_status mba_batch_autotune(mba_batch *batch, const mba_solver_options *opt, mba_batch_schedule *chosen,
+                              double *ms_best);
+/* Solves every window from its current parameters with opt->max_iter LM
+ * iterations (opt->function_tol may stop a window early), then, if adj is not
+ * NULL, runs each window's adjoint at its solution.  summaries (n_windows
+ * entries) and *ms (device time of the launch) may be NULL.  Returns MBA_OK
+ * if every window finished with MBA_OK, else the first failing window's
+ * status; summaries report every window. */
+mba_status mba_batch_solve(mba_batch *batch, const mba_solver_options *opt, const mba_batch_adjoint *adj,
+                           mba_window_summary *summaries, double *ms);
+mba_status mba_batch_get_parameters(const mba_batch *batch, double *cameras, double *points);
+/* NULL keeps the current values of that array. */
+mba_status mba_batch_set_parameters(mba_batch *batch, const double *cameras, const double *points);
+/* Restores the parameters given at creation. */
+mba_status mba_batch_reset(mba_batch *batch);
+/* Gradients of the last solve with an adjoint: grad_obs (total observations x 2,
+ * concatenated input order), grad_init_cam, grad_init_pt.  NULL outputs are skipped. */
+mba_status mba_batch_get_gradients(const mba_batch *batch, double *grad_obs, double *grad_init_cam,
+                                   double *grad_init_pt);
+
 const char *mba_status_string(mba_status status);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mba_last_error(void);

@@ -45,6 +45,13 @@ struct Carve {
 
 }  // namespace
 
+namespace mba {
+mba_status api_fail(mba_status st, const char *msg) {
+    g_err = msg ? msg : "";
+    return st;
+}
+}  // namespace mba
+
 struct mba_problem {
     Prob P;
     cudaStream_t stream = nullptr;

@@ -1,0 +1,1693 @@
+// batch.cu -- batched local bundle adjustment: many independent windows in one
+// persistent launch.  Each CTA claims whole windows (largest first, from a
+// global counter) and runs, for its window alone, the method of the single
+// problem solver:
+//   LM loop of Alg. 1 with the trust-region rule of lm.cu,
+//   residual / Jacobian / Hessian blocks (Alg. 1; Sec. 3 Eq. 2),
+//   Schur elimination (Sec. 3 Eq. 3) and the block-Jacobi PCG of Alg. 2 with
+//   the implicit product of Alg. 3, back-substitution (Sec. 3 Eq. 4), FP64
+//   cost for accept/reject,
+// and, optionally, the adjoint of its solution (as mba_adjoint).  Windows never
+// exchange data, so a CTA synchronises only with itself.
+//
+// Layout.  The camera side of a window (at most 64 cameras: parameters, camera
+// tables, B, v, the preconditioner, the PCG vectors, per-warp partial sums)
+// lives in shared memory.  Points and observations live in global memory,
+// indexed globally; a window's working set is a few hundred KB and stays in L2.
+//
+// Matrix-free Jacobian.  The point and camera passes recompute the projection
+// of each observation from the camera table and the point instead of storing
+// J (96 B per observation in FP32): a window is latency- and L2-bound, not
+// FP32-bound, so recomputing is the cheaper side of the trade.
+//   Jc p  = b_r . (m x X) + D_r . p_t + p_r (d p_f + f r^2 (p_k1 + r^2 p_k2))
+//           with m = M p_w per camera, b_r = row r of Jp = D R (of D in the
+//           first-order branch), D = d(pixel)/dP;
+//   Jc^T s = (M^T (X x g), D^T s, (d, f r^2, f r^4) (p . s)), g = R^T D^T s
+//           (D^T s in the first-order branch).
+// The IRLS weight W multiplies the products once (W Jp^T Jc p, W Jp b), which
+// equals the sqrt(W) scaling of both factors.
+//
+// Summation orders are fixed by the launch schedule (threads per CTA), so a
+// schedule gives the same bits on every run.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mba_internal.cuh"
+
+namespace mba {
+
+namespace {
+
+constexpr int kBMaxCams = 64;  // cameras per window
+constexpr int kTabS = 29;      // shared-memory stride of a T camera-table row (odd: conflict-free gathers)
+
+struct WinDesc {
+    int32_t cam0, nc;    // first camera (global index), count
+    int32_t pt0, np;     // first point, count
+    int32_t obs0, n;     // first observation of the point- and camera-major regions, count
+    int32_t wch0, nwch;  // warp chunks [wch0, wch0 + nwch) and their end entry wch0 + nwch
+};
+
+struct BatchOpts {
+    int32_t max_iter, pcg_max_iter, damping, adjoint, adj_pcg_max, pad;
+    double pcg_tol, initial_radius, min_rel_dec, function_tol, adj_pcg_tol, adj_mu;
+};
+
+struct BatchArgs {
+    int32_t nw, ncmax, loss, pad;
+    double delta;
+    const WinDesc *desc;
+    const int32_t *order;     // claim order (windows by decreasing observation count)
+    int32_t *counter;         // claim counter, zeroed before each launch
+    const BatchOpts *opts;
+    const int2 *wchunk;       // (first point, first observation) of each warp chunk
+    const int2 *pm_pc;        // point-major (point, camera), global indices
+    const double2 *pm_uv;     // point-major pixels
+    const int32_t *pm_orig;   // point-major -> input index
+    const int32_t *cm_pt;     // camera-major point
+    const int32_t *cm2pm;     // camera-major -> point-major position
+    const int32_t *cam_ptr;   // camera-major offsets per camera (global cameras + 1)
+    double *cams, *pts, *pts_new, *dp, *Hll, *wv;
+    const int32_t *pm2cm;     // point-major -> camera-major position
+    void *Cinv;               // [np][6] T: packed inverse of the damped C~
+    void *Wpm;                // [n] T: IRLS weight, point-major (NULL without a loss)
+    void *pmX;                // [n][4] T: the observation's point, point-major (per linearisation)
+    void *pmC;                // [n][8] T: C~^-1 of its point, W, (local point << 6 | local camera) (per solve)
+    void *cmX;                // [n][4] T: the observation's point, camera-major (per linearisation)
+    void *cms;                // [n] T2: s_k = W Jp b_j, camera-major (per PCG pass)
+    const double *gbar_c, *gbar_p;
+    double *grad_obs, *grad_c0, *grad_p0;
+    mba_window_summary *out;
+};
+
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+};
+template <>
+struct V2<double> {
+    using type = double2;
+};
+
+// Shared memory of one CTA, carved from the dynamic allocation.
+template <typename T>
+struct WinMem {
+    double *cams, *camn, *tab64, *Hpp, *v, *Binv, *x, *r, *z, *p, *q, *slot, *sb;
+    T *tabT, *pv;
+    int32_t *cptr, *wf, *wl, *wcam0;
+};
+
+template <typename T>
+__host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int nwarp, WinMem<T> &m) {
+    uintptr_t off = 0;
+    const uintptr_t b = (uintptr_t)base;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = (void *)(b + off);
+        off += (bytes + 15) & ~(size_t)15;
+        return p;
+    };
+    const size_t c9 = 9 * (size_t)ncmax;
+    m.cams = (double *)take(8 * c9);
+    m.camn = (double *)take(8 * c9);
+    m.tab64 = (double *)take(8 * (size_t)kCamTab * ncmax);
+    m.Hpp = (double *)take(8 * 45 * (size_t)ncmax);
+    m.v = (double *)take(8 * c9);
+    m.Binv = (double *)take(8 * 45 * (size_t)ncmax);
+    m.x = (double *)take(8 * c9);
+    m.r = (double *)take(8 * c9);
+    m.z = (double *)take(8 * c9);
+    m.p = (double *)take(8 * c9);
+    m.q = (double *)take(8 * c9);
+    m.slot = (double *)take(8 * 54 * (size_t)(nwarp + ncmax));
+    m.sb = (double *)take(8 * 2 * (size_t)nwarp);
+    m.tabT = (T *)take(sizeof(T) * kTabS * (size_t)ncmax);
+    m.pv = (T *)take(sizeof(T) * c9);
+    m.cptr = (int32_t *)take(4 * (size_t)(ncmax + 1));
+    m.wf = (int32_t *)take(4 * (size_t)ncmax);
+    m.wl = (int32_t *)take(4 * (size_t)ncmax);
+    m.wcam0 = (int32_t *)take(4 * (size_t)nwarp);
+    return (size_t)off;
+}
+
+// Per-window control state (shared, written by thread 0 between barriers).
+struct WinState {
+    double radius, factor, mu, F, F0, Fn, ldec, mu_acc;
+    int32_t win, relin, done, iter, acc_total, pcg_total, status, accept, adj_iters, pad;
+};
+
+__device__ __forceinline__ double damp_term_b(int damping, double d) {
+    if (damping == MBA_DAMP_IDENTITY) return 1.0;
+    return fmin(fmax(d, 1e-6), 1e32);
+}
+
+// Block-wide sums of two doubles; every thread gets the result.  Fixed order:
+// a butterfly in each warp, then the warp sums in warp order.
+template <int NT>
+__device__ __forceinline__ double2 cta_sum2(double a, double b, double *sb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sb[2 * wid] = a;
+        sb[2 * wid + 1] = b;
+    }
+    __syncthreads();
+    double x = 0.0, y = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        x += sb[2 * w];
+        y += sb[2 * w + 1];
+    }
+    __syncthreads();
+    return make_double2(x, y);
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_c(const T *Ci, int pt, T *c) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) c[q] = Ci[6 * (int64_t)pt + q];
+}
+
+template <typename T>
+__device__ __forceinline__ void sym3_mul(const T *c, T a0, T a1, T a2, T *b) {
+    b[0] = c[0] * a0 + c[1] * a1 + c[2] * a2;
+    b[1] = c[1] * a0 + c[3] * a1 + c[4] * a2;
+    b[2] = c[2] * a0 + c[4] * a1 + c[5] * a2;
+}
+
+// Projection of one observation with the pieces of its Jacobian that the
+// matrix-free passes need: the normalised point p, r^2, the distortion d,
+// D = d(pixel)/dP (2x3) and Jp = D R; e = pi - u if RES.  Same arithmetic as
+// project<T, true> for e, D and Jp.
+template <typename T>
+struct ObsJ {
+    T px, py, r2, d;
+    T D[6], Jp[6];
+    T e0, e1;
+};
+
+template <typename T, bool RES>
+__device__ __forceinline__ void obs_jac(const T *ct, T X0, T X1, T X2, T u0, T u1, ObsJ<T> &o) {
+    const T R0 = ct[0], R1 = ct[1], R2 = ct[2], R3 = ct[3], R4 = ct[4], R5 = ct[5], R6 = ct[6], R7 = ct[7],
+            R8 = ct[8];
+    const T P0 = R0 * X0 + R1 * X1 + R2 * X2 + ct[18];
+    const T P1 = R3 * X0 + R4 * X1 + R5 * X2 + ct[19];
+    const T P2 = R6 * X0 + R7 * X1 + R8 * X2 + ct[20];
+    const T iz = rcp_rn(P2);
+    const T px = -P0 * iz, py = -P1 * iz;
+    const T f = ct[21], k1 = ct[22], k2 = ct[23];
+    const T r2 = px * px + py * py;
+    const T d = T(1) + k1 * r2 + k2 * r2 * r2;
+    if (RES) {
+        o.e0 = f * d * px - u0;
+        o.e1 = f * d * py - u1;
+    }
+    const T dd = T(2) * k1 + T(4) * k2 * r2;
+    const T a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
+    o.D[0] = -a00 * iz;
+    o.D[1] = -a01 * iz;
+    o.D[2] = -(a00 * px + a01 * py) * iz;
+    o.D[3] = -a01 * iz;
+    o.D[4] = -a11 * iz;
+    o.D[5] = -(a01 * px + a11 * py) * iz;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o.Jp[r * 3 + 0] = o.D[r * 3] * R0 + o.D[r * 3 + 1] * R3 + o.D[r * 3 + 2] * R6;
+        o.Jp[r * 3 + 1] = o.D[r * 3] * R1 + o.D[r * 3 + 1] * R4 + o.D[r * 3 + 2] * R7;
+        o.Jp[r * 3 + 2] = o.D[r * 3] * R2 + o.D[r * 3 + 1] * R5 + o.D[r * 3 + 2] * R8;
+    }
+    o.px = px;
+    o.py = py;
+    o.r2 = r2;
+    o.d = d;
+}
+
+// t = Jc v for the camera vector v given as pv = (M v_w, v_t, v_f, v_k1, v_k2).
+template <typename T>
+__device__ __forceinline__ void jc_apply(const T *ct, const T *pv, const ObsJ<T> &o, T X0, T X1, T X2, T &t0,
+                                         T &t1) {
+    const T c0 = pv[1] * X2 - pv[2] * X1, c1 = pv[2] * X0 - pv[0] * X2, c2 = pv[0] * X1 - pv[1] * X0;
+    const bool small = ct[24] != T(0);
+    const T *b = small ? o.D : o.Jp;
+    const T kap = o.d * pv[6] + ct[21] * o.r2 * (pv[7] + o.r2 * pv[8]);
+    t0 = b[0] * c0 + b[1] * c1 + b[2] * c2 + o.D[0] * pv[3] + o.D[1] * pv[4] + o.D[2] * pv[5] + o.px * kap;
+    t1 = b[3] * c0 + b[4] * c1 + b[5] * c2 + o.D[3] * pv[3] + o.D[4] * pv[4] + o.D[5] * pv[5] + o.py * kap;
+}
+
+// y = Jc^T s by the transposed chain rule (no Jc formed).
+template <typename T>
+__device__ __forceinline__ void jct_apply(const T *ct, T X0, T X1, T X2, T s0, T s1, T *y) {
+    const T P0 = ct[0] * X0 + ct[1] * X1 + ct[2] * X2 + ct[18];
+    const T P1 = ct[3] * X0 + ct[4] * X1 + ct[5] * X2 + ct[19];
+    const T P2 = ct[6] * X0 + ct[7] * X1 + ct[8] * X2 + ct[20];
+    const T iz = rcp_rn(P2);
+    const T px = -P0 * iz, py = -P1 * iz;
+    const T f = ct[21], k1 = ct[22], k2 = ct[23];
+    const T r2 = px * px + py * py;
+    const T d = T(1) + k1 * r2 + k2 * r2 * r2;
+    const T dd = T(2) * k1 + T(4) * k2 * r2;
+    const T a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
+    const T g0 = -(a00 * s0 + a01 * s1) * iz, g1 = -(a01 * s0 + a11 * s1) * iz;
+    const T v0 = g0, v1 = g1, v2 = g0 * px + g1 * py;  // D^T s
+    y[3] = v0;
+    y[4] = v1;
+    y[5] = v2;
+    T w0 = v0, w1 = v1, w2 = v2;
+    if (ct[24] == T(0)) {
+        w0 = ct[0] * v0 + ct[3] * v1 + ct[6] * v2;
+        w1 = ct[1] * v0 + ct[4] * v1 + ct[7] * v2;
+        w2 = ct[2] * v0 + ct[5] * v1 + ct[8] * v2;
+    }
+    const T u0 = X1 * w2 - X2 * w1, u1 = X2 * w0 - X0 * w2, u2 = X0 * w1 - X1 * w0;
+    y[0] = ct[9] * u0 + ct[12] * u1 + ct[15] * u2;
+    y[1] = ct[10] * u0 + ct[13] * u1 + ct[16] * u2;
+    y[2] = ct[11] * u0 + ct[14] * u1 + ct[17] * u2;
+    const T pss = px * s0 + py * s1;
+    y[6] = d * pss;
+    y[7] = f * r2 * pss;
+    y[8] = f * r2 * r2 * pss;
+}
+
+// Inclusive segmented scan over the lanes of a warp; segments are runs of
+// equal keys (whole points, contiguous).
+template <typename T, int K>
+__device__ __forceinline__ void seg_scan(T *u, int key, int lane) {
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const int kp = __shfl_up_sync(0xffffffffu, key, dd);
+        T v[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] = __shfl_up_sync(0xffffffffu, u[q], dd);
+        if (lane >= dd && kp == key)
+#pragma unroll
+            for (int q = 0; q < K; ++q) u[q] += v[q];
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void warp_allsum(T *u) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < K; ++q) u[q] += __shfl_xor_sync(0xffffffffu, u[q], o);
+}
+
+// Per-observation records, rewritten once per linearisation (X) or per damped
+// solve (C~^-1, W, key) so that the PCG passes read them coalesced, one level
+// of indirection deep, instead of gathering per point.
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T &a, T &b, T &c, T &d);
+template <>
+__device__ __forceinline__ void ld4<float>(const float *p, float &a, float &b, float &c, float &d) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = v.x;
+    b = v.y;
+    c = v.z;
+    d = v.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double *p, double &a, double &b, double &c, double &d) {
+    const double2 u = reinterpret_cast<const double2 *>(p)[0], v = reinterpret_cast<const double2 *>(p)[1];
+    a = u.x;
+    b = u.y;
+    c = v.x;
+    d = v.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, T a, T b, T c, T d);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double *p, double a, double b, double c, double d) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
+// (local point << 6) | local camera, carried in the record's last T slot
+__device__ __forceinline__ float key_bits(float, int k) { return __int_as_float(k); }
+__device__ __forceinline__ double key_bits(double, int k) { return __longlong_as_double((long long)k); }
+__device__ __forceinline__ int key_of(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int key_of(double v) { return (int)__double_as_longlong(v); }
+
+template <typename T>
+struct PmRec {
+    T X0, X1, X2, W;
+    T c[6];
+    int key;  // (local point << 6) | local camera
+    int cm;   // camera-major position of the observation
+};
+
+template <typename T>
+__device__ __forceinline__ void load_rec(const BatchArgs &A, int o, PmRec<T> &r) {
+    const T *px = (const T *)A.pmX + 4 * (int64_t)o;
+    const T *pc = (const T *)A.pmC + 8 * (int64_t)o;
+    T unused, kb;
+    ld4<T>(px, r.X0, r.X1, r.X2, unused);
+    ld4<T>(pc, r.c[0], r.c[1], r.c[2], r.c[3]);
+    ld4<T>(pc + 4, r.c[4], r.c[5], r.W, kb);
+    r.key = key_of(kb);
+    r.cm = __ldg(A.pm2cm + o);
+}
+
+// Linearisation over the window's warp chunks: e, Jp and W per observation; per point
+// C = sum W Jp^T Jp and w = -sum W Jp^T e by a segmented scan (whole points per
+// chunk) or a warp sum (one long-track point); the point-major X record and W.
+template <typename T, int NT>
+__device__ void lin_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    T *pmX = (T *)A.pmX;
+    T *Wpm = (T *)A.Wpm;
+    const T delta = (T)A.delta;
+    for (int c = d.wch0 + wid; c < d.wch0 + d.nwch; c += NW) {
+        const int2 c0 = __ldg(A.wchunk + c), c1 = __ldg(A.wchunk + c + 1);
+        const int o0 = c0.y, m = c1.y - c0.y;
+        const bool longp = m > 32;
+        T h[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) h[q] = T(0);
+        int key = -1 - lane, pt = c0.x;
+        for (int base = 0; base < m; base += 32) {
+            const bool act = base + lane < m;
+            const int o = o0 + base + (act ? lane : 0);
+            const int2 pc = __ldg(A.pm_pc + o);
+            pt = pc.x;
+            if (act) key = pc.x;
+            const T X0 = (T)A.pts[3 * (int64_t)pt], X1 = (T)A.pts[3 * (int64_t)pt + 1],
+                    X2 = (T)A.pts[3 * (int64_t)pt + 2];
+            const double2 uv = __ldg(A.pm_uv + o);
+            T e[2], Jc[18], Jp[6];
+            project<T, true>(M.tabT + (pc.y - d.cam0) * kTabS, X0, X1, X2, (T)uv.x, (T)uv.y, e, Jc, Jp);
+            T rho, W;
+            loss_weight<T>(A.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+            if (act) {
+                T jw[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) jw[q] = W * Jp[q];
+                h[0] += jw[0] * Jp[0] + jw[3] * Jp[3];
+                h[1] += jw[0] * Jp[1] + jw[3] * Jp[4];
+                h[2] += jw[0] * Jp[2] + jw[3] * Jp[5];
+                h[3] += jw[1] * Jp[1] + jw[4] * Jp[4];
+                h[4] += jw[1] * Jp[2] + jw[4] * Jp[5];
+                h[5] += jw[2] * Jp[2] + jw[5] * Jp[5];
+                h[6] -= jw[0] * e[0] + jw[3] * e[1];
+                h[7] -= jw[1] * e[0] + jw[4] * e[1];
+                h[8] -= jw[2] * e[0] + jw[5] * e[1];
+                st4<T>(pmX + 4 * (int64_t)o, X0, X1, X2, T(0));
+                if (Wpm) Wpm[o] = W;
+            }
+        }
+        bool tail;
+        if (longp) {
+            warp_allsum<T, 9>(h);
+            tail = lane == 0;
+            pt = c0.x;
+        } else {
+            seg_scan<T, 9>(h, key, lane);
+            const int nxt = __shfl_down_sync(full, key, 1);
+            tail = lane < m && (lane == 31 || lane == m - 1 || nxt != key);
+        }
+        if (tail) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) A.Hll[6 * (int64_t)pt + q] = (double)h[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A.wv[3 * (int64_t)pt + q] = (double)h[6 + q];
+        }
+    }
+}
+
+// Right-hand side pass, per observation (no segments): the C~^-1 / W / key
+// record, then s_k = W Jp b_j with b_j = C~_j^-1 wvec_j into camera-major order.
+template <typename T, int NT>
+__device__ void rhs_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *wvec) {
+    using T2 = typename V2<T>::type;
+    const T *Ci = (const T *)A.Cinv;
+    const T *Wpm = (const T *)A.Wpm;
+    T *pmC = (T *)A.pmC;
+    T2 *cms = (T2 *)A.cms;
+    for (int k = threadIdx.x; k < d.n; k += NT) {
+        const int o = d.obs0 + k;
+        const int2 pc = __ldg(A.pm_pc + o);
+        const int pt = pc.x, lc = pc.y - d.cam0;
+        T ci[6];
+        ld_c<T>(Ci, pt, ci);
+        const T W = Wpm ? Wpm[o] : T(1);
+        T *rc = pmC + 8 * (int64_t)o;
+        st4<T>(rc, ci[0], ci[1], ci[2], ci[3]);
+        st4<T>(rc + 4, ci[4], ci[5], W, key_bits(T(0), ((pt - d.pt0) << 6) | lc));
+        T X0, X1, X2, unused;
+        ld4<T>((const T *)A.pmX + 4 * (int64_t)o, X0, X1, X2, unused);
+        ObsJ<T> J;
+        obs_jac<T, false>(M.tabT + lc * kTabS, X0, X1, X2, T(0), T(0), J);
+        T b[3];
+        sym3_mul<T>(ci, (T)wvec[3 * (int64_t)pt], (T)wvec[3 * (int64_t)pt + 1], (T)wvec[3 * (int64_t)pt + 2], b);
+        T2 sv;
+        sv.x = W * (J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2]);
+        sv.y = W * (J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2]);
+        cms[__ldg(A.pm2cm + o)] = sv;
+    }
+}
+
+// u_k = W Jp^T (Jc v) for one record (v given by its pv row)
+template <typename T>
+__device__ __forceinline__ void rec_u(const WinMem<T> &M, const PmRec<T> &r, ObsJ<T> &J, T &a0, T &a1, T *u) {
+    const int lc = r.key & 63;
+    const T *ct = M.tabT + lc * kTabS;
+    obs_jac<T, false>(ct, r.X0, r.X1, r.X2, T(0), T(0), J);
+    jc_apply<T>(ct, M.pv + lc * 9, J, r.X0, r.X1, r.X2, a0, a1);
+    const T tw0 = r.W * a0, tw1 = r.W * a1;
+    u[0] = J.Jp[0] * tw0 + J.Jp[3] * tw1;
+    u[1] = J.Jp[1] * tw0 + J.Jp[4] * tw1;
+    u[2] = J.Jp[2] * tw0 + J.Jp[5] * tw1;
+}
+
+// The E^T p, C~^-1, E pass of Alg. 3: s_k = W Jp b_j, b_j = C~_j^-1 sum_k u_k,
+// stored camera-major.  The records of the next chunk are loaded before the
+// current chunk is computed (software pipelining over the warp's chunks).
+template <typename T, int NT>
+__device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    using T2 = typename V2<T>::type;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    T2 *cms = (T2 *)A.cms;
+    const int cend = d.wch0 + d.nwch;
+    int c = d.wch0 + wid;
+    if (c >= cend) return;
+    int2 mc = __ldg(A.wchunk + c), mc1 = __ldg(A.wchunk + c + 1);
+    PmRec<T> cur;
+    load_rec<T>(A, mc.y + ((lane < mc1.y - mc.y) ? lane : 0), cur);
+    int2 mn = mc1, mn1 = mc1;
+    if (c + NW < cend) {
+        mn = __ldg(A.wchunk + c + NW);
+        mn1 = __ldg(A.wchunk + c + NW + 1);
+    }
+    for (;;) {
+        const bool more = c + NW < cend;
+        PmRec<T> nxt;
+        if (more) load_rec<T>(A, mn.y + ((lane < mn1.y - mn.y) ? lane : 0), nxt);
+        int2 mm = mn1, mm1 = mn1;
+        if (c + 2 * NW < cend) {
+            mm = __ldg(A.wchunk + c + 2 * NW);
+            mm1 = __ldg(A.wchunk + c + 2 * NW + 1);
+        }
+        const int o0 = mc.y, m = mc1.y - mc.y;
+        if (m <= 32) {
+            const bool act = lane < m;
+            const int key = act ? (cur.key >> 6) : -1 - lane;
+            ObsJ<T> J;
+            T a0, a1, u[3];
+            rec_u<T>(M, cur, J, a0, a1, u);
+            seg_scan<T, 3>(u, key, lane);
+            const int kn = __shfl_down_sync(full, key, 1);
+            const bool tail = act && (lane == 31 || lane == m - 1 || kn != key);
+            const unsigned tails = __ballot_sync(full, tail);
+            const unsigned mine = tails & (0xffffffffu << lane);
+            const int src = mine ? __ffs(mine) - 1 : lane;
+            T bt[3], b[3];
+            sym3_mul<T>(cur.c, u[0], u[1], u[2], bt);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) b[q] = __shfl_sync(full, bt[q], src);
+            if (act) {
+                T2 sv;
+                sv.x = cur.W * (J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2]);
+                sv.y = cur.W * (J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2]);
+                cms[cur.cm] = sv;
+            }
+        } else {
+            // one point with a long track: two sweeps over 32-observation slices
+            T a[3] = {T(0), T(0), T(0)};
+            T cc[6];
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    PmRec<T> r;
+                    load_rec<T>(A, o0 + base + lane, r);
+                    ObsJ<T> J;
+                    T a0, a1, u[3];
+                    rec_u<T>(M, r, J, a0, a1, u);
+                    a[0] += u[0];
+                    a[1] += u[1];
+                    a[2] += u[2];
+                }
+            }
+            warp_allsum<T, 3>(a);
+            PmRec<T> r0;
+            load_rec<T>(A, o0, r0);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) cc[q] = r0.c[q];
+            T b[3];
+            sym3_mul<T>(cc, a[0], a[1], a[2], b);
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    PmRec<T> r;
+                    load_rec<T>(A, o0 + base + lane, r);
+                    ObsJ<T> J;
+                    obs_jac<T, false>(M.tabT + (r.key & 63) * kTabS, r.X0, r.X1, r.X2, T(0), T(0), J);
+                    T2 sv;
+                    sv.x = r.W * (J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2]);
+                    sv.y = r.W * (J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2]);
+                    cms[r.cm] = sv;
+                }
+            }
+        }
+        if (!more) break;
+        c += NW;
+        mc = mn;
+        mc1 = mn1;
+        mn = mm;
+        mn1 = mm1;
+        cur = nxt;
+    }
+}
+
+// Back-substitution (Sec. 3 Eq. 4): dp_j = C~_j^-1 (wvec_j - sum_k W Jp^T Jc x),
+// d_k = Jc x + Jp dp_j.  Forward solve: candidate points and this thread's
+// share of the model decrease sum_k W (-e.d - |d|^2/2).  Adjoint: W d_k per
+// observation in input order.
+template <typename T, int NT>
+__device__ double back_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *wvec,
+                              bool adj) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    double ldec = 0.0;
+    for (int c = d.wch0 + wid; c < d.wch0 + d.nwch; c += NW) {
+        const int2 c0 = __ldg(A.wchunk + c), c1 = __ldg(A.wchunk + c + 1);
+        const int o0 = c0.y, m = c1.y - c0.y;
+        // first sweep: u sums (segmented for whole-point chunks, warp-wide for a long track)
+        T u[3] = {T(0), T(0), T(0)};
+        int key = -1 - lane;
+        PmRec<T> r;
+        T a0 = T(0), a1 = T(0);
+        ObsJ<T> J;
+        for (int base = 0; base < m; base += 32) {
+            const bool act = base + lane < m;
+            load_rec<T>(A, o0 + base + (act ? lane : 0), r);
+            T uu[3];
+            rec_u<T>(M, r, J, a0, a1, uu);
+            if (act) {
+                key = r.key >> 6;
+                u[0] += uu[0];
+                u[1] += uu[1];
+                u[2] += uu[2];
+            }
+        }
+        T b[3];
+        bool tail;
+        int ptl;
+        if (m > 32) {
+            warp_allsum<T, 3>(u);
+            tail = lane == 0;
+            ptl = c0.x - d.pt0;
+        } else {
+            seg_scan<T, 3>(u, key, lane);
+            const int kn = __shfl_down_sync(full, key, 1);
+            tail = lane < m && (lane == 31 || lane == m - 1 || kn != key);
+            ptl = key;
+        }
+        const unsigned tails = __ballot_sync(full, tail);
+        const unsigned mine = tails & (0xffffffffu << lane);
+        const int src = m > 32 ? 0 : (mine ? __ffs(mine) - 1 : lane);
+        {
+            T bt[3];
+            const int64_t pt = (int64_t)d.pt0 + (ptl >= 0 ? ptl : 0);
+            sym3_mul<T>(r.c, (T)wvec[3 * pt] - u[0], (T)wvec[3 * pt + 1] - u[1], (T)wvec[3 * pt + 2] - u[2], bt);
+            if (tail) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    A.dp[3 * pt + q] = (double)bt[q];
+                    if (!adj) A.pts_new[3 * pt + q] = A.pts[3 * pt + q] + (double)bt[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) b[q] = __shfl_sync(full, bt[q], src);
+        }
+        // second sweep: d_k (the records of a whole-point chunk are still in registers)
+        for (int base = 0; base < m; base += 32) {
+            const bool act = base + lane < m;
+            const int o = o0 + base + (act ? lane : 0);
+            if (m > 32) {
+                load_rec<T>(A, o, r);
+                T uu[3];
+                rec_u<T>(M, r, J, a0, a1, uu);
+            }
+            if (act) {
+                const T dd0 = a0 + J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2];
+                const T dd1 = a1 + J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2];
+                if (adj) {
+                    const int64_t k = __ldg(A.pm_orig + o);
+                    A.grad_obs[2 * k] = (double)r.W * (double)dd0;
+                    A.grad_obs[2 * k + 1] = (double)r.W * (double)dd1;
+                } else {
+                    const double2 uv = __ldg(A.pm_uv + o);
+                    ObsJ<T> Je;
+                    obs_jac<T, true>(M.tabT + (r.key & 63) * kTabS, r.X0, r.X1, r.X2, (T)uv.x, (T)uv.y, Je);
+                    const double e0 = (double)Je.e0, e1 = (double)Je.e1, x0 = (double)dd0, x1 = (double)dd1;
+                    ldec += (double)r.W * (-(e0 * x0 + e1 * x1) - 0.5 * (x0 * x0 + x1 * x1));
+                }
+            }
+        }
+    }
+    return ldec;
+}
+
+// Camera-major pass: warp w owns observations [lo(w), lo(w+1)) of the window
+// (lo(w) = w n / NW), split at camera boundaries into segments; each segment's
+// sum goes to slot (w + camera), a slot no other segment uses.  LIN: the 45
+// entries of B = sum W Jc^T Jc and v = -sum W Jc^T e (54 per slot);
+// otherwise sum Jc^T s (9 per slot).
+template <typename T, int NT, bool LIN>
+__device__ void camera_pass(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    using T2 = typename V2<T>::type;
+    constexpr int NW = NT / 32;
+    constexpr int K = LIN ? 54 : 9;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lo = (int)(((int64_t)wid * d.n) / NW), hi = (int)(((int64_t)(wid + 1) * d.n) / NW);
+    if (lo >= hi) return;
+    T *cmX = (T *)A.cmX;
+    const T2 *cms = (const T2 *)A.cms;
+    const T delta = (T)A.delta;
+    int cam = M.wcam0[wid];
+    int beg = lo;
+    for (;;) {
+        const int end = min(hi, M.cptr[cam + 1]);
+        const T *ct = M.tabT + cam * kTabS;
+        T acc[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[q] = T(0);
+#pragma unroll 2
+        for (int c = beg + lane; c < end; c += 32) {
+            const int gc = d.obs0 + c;
+            T X0, X1, X2;
+            if (LIN) {
+                const int pt = __ldg(A.cm_pt + gc), pm = __ldg(A.cm2pm + gc);
+                X0 = (T)A.pts[3 * (int64_t)pt];
+                X1 = (T)A.pts[3 * (int64_t)pt + 1];
+                X2 = (T)A.pts[3 * (int64_t)pt + 2];
+                st4<T>(cmX + 4 * (int64_t)gc, X0, X1, X2, T(0));
+                const double2 uv = __ldg(A.pm_uv + pm);
+                T e[2], Jc[18], Jp[6];
+                project<T, true>(ct, X0, X1, X2, (T)uv.x, (T)uv.y, e, Jc, Jp);
+                T rho, W;
+                loss_weight<T>(A.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+                int idx = 0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const T w0 = W * Jc[a], w1 = W * Jc[9 + a];
+#pragma unroll
+                    for (int b = a; b < 9; ++b) acc[idx++] += w0 * Jc[b] + w1 * Jc[9 + b];
+                    acc[45 + a] -= w0 * e[0] + w1 * e[1];
+                }
+            } else {
+                T unused;
+                ld4<T>(cmX + 4 * (int64_t)gc, X0, X1, X2, unused);
+                const T2 sv = cms[gc];
+                T y[9];
+                jct_apply<T>(ct, X0, X1, X2, sv.x, sv.y, y);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) acc[q] += y[q];
+            }
+        }
+        warp_allsum<T, K>(acc);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < K; ++q) M.slot[(wid + cam) * K + q] = (double)acc[q];
+        if (end >= hi) break;
+        beg = end;
+        ++cam;
+    }
+}
+
+// Sum of camera i's segment slots (stride K), in warp order.
+__device__ __forceinline__ double slot_sum(const double *slot, const int32_t *wf, const int32_t *wl, int i, int K,
+                                           int q) {
+    double s = 0.0;
+    for (int w = wf[i]; w <= wl[i]; ++w) s += slot[(w + i) * K + q];
+    return s;
+}
+
+// (M v_w, v_t, v_f, v_k1, v_k2) per camera in T, for jc_apply.
+template <typename T, int NT>
+__device__ __forceinline__ void make_pv(const WinMem<T> &M, const double *vec, int nc) {
+    for (int t = threadIdx.x; t < 9 * nc; t += NT) {
+        const int i = t / 9, a = t - 9 * (t / 9);
+        T val;
+        if (a < 3) {
+            const T *Mr = M.tabT + i * kTabS + 9 + 3 * a;
+            val = Mr[0] * (T)vec[9 * i] + Mr[1] * (T)vec[9 * i + 1] + Mr[2] * (T)vec[9 * i + 2];
+        } else {
+            val = (T)vec[t];
+        }
+        M.pv[t] = val;
+    }
+}
+
+// z = B~^-1 r per camera (packed symmetric inverse); returns (r.r, r.z) partials.
+template <typename T, int NT>
+__device__ __forceinline__ double2 precond(const WinMem<T> &M, int nc) {
+    double rr = 0.0, rz = 0.0;
+    for (int t = threadIdx.x; t < 9 * nc; t += NT) {
+        const int i = t / 9, a = t - 9 * (t / 9);
+        const double *Bi = M.Binv + 45 * i;
+        const double *ri = M.r + 9 * i;
+        double z = 0.0;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) z = fma(Bi[sym9(a, b)], ri[b], z);
+        M.z[t] = z;
+        rr = fma(M.r[t], M.r[t], rr);
+        rz = fma(M.r[t], z, rz);
+    }
+    return make_double2(rr, rz);
+}
+
+template <typename T, int NT>
+__device__ void linearize(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    for (int t = threadIdx.x; t < d.nc * kCamTab; t += NT) {
+        const int i = t / kCamTab, q = t - kCamTab * (t / kCamTab);
+        M.tabT[i * kTabS + q] = (T)M.tab64[t];
+    }
+    __syncthreads();
+    lin_points<T, NT>(A, M, d);
+    __syncthreads();
+    camera_pass<T, NT, true>(A, M, d);
+    __syncthreads();
+    for (int t = threadIdx.x; t < d.nc * 54; t += NT) {
+        const int i = t / 54, q = t - 54 * (t / 54);
+        const double s = slot_sum(M.slot, M.wf, M.wl, i, 54, q);
+        if (q < 45) M.Hpp[45 * i + q] = s;
+        else M.v[9 * i + (q - 45)] = s;
+    }
+    __syncthreads();
+}
+
+// B~ = B + mu D and its inverse (Cholesky, FP64, packed), C~^-1 per point (adjugate, FP64 -> T).
+template <typename T, int NT>
+__device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const WinDesc &d, double mu, int damping) {
+    for (int i = threadIdx.x; i < d.nc; i += NT) {
+        double L[81];
+        for (int a = 0; a < 9; ++a)
+            for (int b = 0; b < 9; ++b) L[a * 9 + b] = M.Hpp[45 * i + sym9(a, b)];
+        for (int a = 0; a < 9; ++a) L[a * 10] += mu * damp_term_b(damping, L[a * 10]);
+        bool ok = true;
+        for (int j = 0; j < 9 && ok; ++j) {
+            double s = L[j * 9 + j];
+            for (int k = 0; k < j; ++k) s -= L[j * 9 + k] * L[j * 9 + k];
+            if (!(s > 0.0) || !isfinite(s)) {
+                ok = false;
+                break;
+            }
+            const double l = sqrt(s);
+            L[j * 9 + j] = l;
+            for (int r = j + 1; r < 9; ++r) {
+                double t = L[r * 9 + j];
+                for (int k = 0; k < j; ++k) t -= L[r * 9 + k] * L[j * 9 + k];
+                L[r * 9 + j] = t / l;
+            }
+        }
+        if (!ok) {
+            S.status = MBA_ERR_NONFINITE;
+            continue;
+        }
+        for (int col = 0; col < 9; ++col) {
+            double y[9];
+            for (int r = 0; r < 9; ++r) {
+                double s = (r == col) ? 1.0 : 0.0;
+                for (int k = 0; k < r; ++k) s -= L[r * 9 + k] * y[k];
+                y[r] = s / L[r * 9 + r];
+            }
+            for (int r = 8; r >= 0; --r) {
+                double s = y[r];
+                for (int k = r + 1; k < 9; ++k) s -= L[k * 9 + r] * y[k];
+                y[r] = s / L[r * 9 + r];
+            }
+            for (int r = col; r < 9; ++r) M.Binv[45 * i + sym9(col, r)] = y[r];
+        }
+    }
+    T *Ci = (T *)A.Cinv;
+    for (int j = threadIdx.x; j < d.np; j += NT) {
+        const int64_t pt = d.pt0 + j;
+        const double *h = A.Hll + 6 * pt;
+        const double a00 = h[0] + mu * damp_term_b(damping, h[0]), a01 = h[1], a02 = h[2];
+        const double a11 = h[3] + mu * damp_term_b(damping, h[3]), a12 = h[4];
+        const double a22 = h[5] + mu * damp_term_b(damping, h[5]);
+        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const double det = a00 * c00 + a01 * c01 + a02 * c02;
+        if (!(det > 0.0) || !isfinite(det)) {
+            S.status = MBA_ERR_NONFINITE;
+            continue;
+        }
+        const double id = 1.0 / det;
+        Ci[6 * pt + 0] = (T)(c00 * id);
+        Ci[6 * pt + 1] = (T)(c01 * id);
+        Ci[6 * pt + 2] = (T)(c02 * id);
+        Ci[6 * pt + 3] = (T)((a00 * a22 - a02 * a02) * id);
+        Ci[6 * pt + 4] = (T)((a02 * a01 - a00 * a12) * id);
+        Ci[6 * pt + 5] = (T)((a00 * a11 - a01 * a01) * id);
+    }
+}
+
+// PCG of Alg. 2 on S x = g, g = vvec - E C~^-1 wvec (Sec. 3 Eq. 3), x0 = 0;
+// leaves x in M.x and returns the iteration count.
+template <typename T, int NT>
+__device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *vvec, const double *wvec,
+                   double mu, int damping, int max_iter, double tol) {
+    const int m9 = 9 * d.nc;
+    rhs_points<T, NT>(A, M, d, wvec);
+    __syncthreads();
+    camera_pass<T, NT, false>(A, M, d);
+    __syncthreads();
+    for (int t = threadIdx.x; t < m9; t += NT) {
+        const int i = t / 9, a = t - 9 * (t / 9);
+        M.r[t] = vvec[t] - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
+        M.x[t] = 0.0;
+    }
+    __syncthreads();
+    double2 s0 = precond<T, NT>(M, d.nc);
+    s0 = cta_sum2<NT>(s0.x, s0.y, M.sb);
+    const double r0 = sqrt(s0.x);
+    double rho = s0.y, rho_prev = 0.0, rn = r0;
+    int n = 0;
+    if (r0 > 0.0) {
+        for (;;) {
+            if (!isfinite(rho)) break;
+            const double beta = n == 0 ? 0.0 : rho / rho_prev;
+            for (int t = threadIdx.x; t < m9; t += NT) M.p[t] = n == 0 ? M.z[t] : fma(beta, M.p[t], M.z[t]);
+            __syncthreads();
+            make_pv<T, NT>(M, M.p, d.nc);
+            __syncthreads();
+            iter_points<T, NT>(A, M, d);
+            __syncthreads();
+            camera_pass<T, NT, false>(A, M, d);
+            __syncthreads();
+            double pq = 0.0;
+            for (int t = threadIdx.x; t < m9; t += NT) {
+                const int i = t / 9, a = t - 9 * (t / 9);
+                const double *Hi = M.Hpp + 45 * i;
+                const double *pi_ = M.p + 9 * i;
+                double bp = 0.0;
+#pragma unroll
+                for (int b = 0; b < 9; ++b) bp = fma(Hi[sym9(a, b)], pi_[b], bp);
+                bp = fma(mu * damp_term_b(damping, Hi[sym9(a, a)]), pi_[a], bp);
+                const double q = bp - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
+                M.q[t] = q;
+                pq = fma(M.p[t], q, pq);
+            }
+            pq = cta_sum2<NT>(pq, 0.0, M.sb).x;
+            if (!(pq > 0.0) || !isfinite(pq)) break;
+            const double alpha = rho / pq;
+            for (int t = threadIdx.x; t < m9; t += NT) {
+                M.x[t] = fma(alpha, M.p[t], M.x[t]);
+                M.r[t] = fma(-alpha, M.q[t], M.r[t]);
+            }
+            __syncthreads();
+            double2 s = precond<T, NT>(M, d.nc);
+            s = cta_sum2<NT>(s.x, s.y, M.sb);
+            ++n;
+            rho_prev = rho;
+            rho = s.y;
+            rn = sqrt(s.x);
+            if (rn <= tol * r0 || n >= max_iter) break;
+        }
+    }
+    return n;
+}
+
+// F = 1/2 sum rho(|e|^2) in FP64 with the FP64 camera table in M.tab64.
+template <typename T, int NT>
+__device__ double cost(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *pts) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < d.n; k += NT) {
+        const int o = d.obs0 + k;
+        const int2 pc = __ldg(A.pm_pc + o);
+        const double2 uv = __ldg(A.pm_uv + o);
+        double e[2];
+        project<double, false>(M.tab64 + kCamTab * (pc.y - d.cam0), pts[3 * (int64_t)pc.x],
+                               pts[3 * (int64_t)pc.x + 1], pts[3 * (int64_t)pc.x + 2], uv.x, uv.y, e, nullptr,
+                               nullptr);
+        double rho, W;
+        loss_weight<double>(A.loss, A.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+        acc += rho;
+    }
+    return 0.5 * cta_sum2<NT>(acc, 0.0, M.sb).x;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void tables64(const WinMem<T> &M, const double *cams, int nc) {
+    for (int i = threadIdx.x; i < nc; i += NT) camera_table_row(cams + 9 * i, M.tab64 + kCamTab * i);
+}
+
+// Warp ownership of the camera-major observations of a window.
+template <int NT>
+__device__ __forceinline__ int warp_lo(int w, int n) {
+    return (int)(((int64_t)w * n) / (NT / 32));
+}
+template <int NT>
+__device__ int owner_warp(int r, int n) {
+    constexpr int NW = NT / 32;
+    int w = (int)(((int64_t)r * NW) / n);
+    if (w > NW - 1) w = NW - 1;
+    while (w + 1 < NW && warp_lo<NT>(w + 1, n) <= r) ++w;
+    while (w > 0 && warp_lo<NT>(w, n) > r) --w;
+    return w;
+}
+
+template <typename T, int NT>
+__device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMem<T> &M, WinState &S, int wi) {
+    constexpr int NW = NT / 32;
+    const WinDesc d = A.desc[wi];
+    const int tid = threadIdx.x, m9 = 9 * d.nc;
+    for (int t = tid; t < m9; t += NT) M.cams[t] = A.cams[9 * (int64_t)d.cam0 + t];
+    for (int t = tid; t <= d.nc; t += NT) M.cptr[t] = __ldg(A.cam_ptr + d.cam0 + t) - d.obs0;
+    if (tid == 0) {
+        S.radius = O.initial_radius;
+        S.factor = 2.0;
+        S.mu = 1.0 / O.initial_radius;
+        S.mu_acc = -1.0;
+        S.relin = 1;
+        S.done = 0;
+        S.iter = 0;
+        S.acc_total = 0;
+        S.pcg_total = 0;
+        S.status = MBA_OK;
+        S.accept = 0;
+        S.adj_iters = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < d.nc; i += NT) {
+        M.wf[i] = owner_warp<NT>(M.cptr[i], d.n);
+        M.wl[i] = owner_warp<NT>(M.cptr[i + 1] - 1, d.n);
+    }
+    if (tid < NW) {
+        const int lo = warp_lo<NT>(tid, d.n);
+        int c = 0;
+        while (c + 1 < d.nc && M.cptr[c + 1] <= lo) ++c;
+        M.wcam0[tid] = c;
+    }
+    tables64<T, NT>(M, M.cams, d.nc);
+    __syncthreads();
+    {
+        const double F = cost<T, NT>(A, M, d, A.pts);
+        if (tid == 0) {
+            S.F = F;
+            S.F0 = F;
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < O.max_iter; ++it) {
+        if (S.done) break;
+        if (S.relin) {
+            linearize<T, NT>(A, M, d);
+            if (tid == 0) S.relin = 0;
+        }
+        const double mu = 1.0 / S.radius;
+        damp<T, NT>(A, M, S, d, mu, O.damping);
+        __syncthreads();
+        if (S.status != MBA_OK) break;
+        const int np_ = pcg<T, NT>(A, M, d, M.v, A.wv, mu, O.damping, O.pcg_max_iter, O.pcg_tol);
+        make_pv<T, NT>(M, M.x, d.nc);
+        __syncthreads();
+        double ld = back_points<T, NT>(A, M, d, A.wv, false);
+        ld = cta_sum2<NT>(ld, 0.0, M.sb).x;
+        for (int t = tid; t < m9; t += NT) M.camn[t] = M.cams[t] + M.x[t];
+        __syncthreads();
+        tables64<T, NT>(M, M.camn, d.nc);
+        __syncthreads();
+        const double Fn = cost<T, NT>(A, M, d, A.pts_new);
+        if (tid == 0) {
+            // trust-region rule of lm.cu
+            const double F = S.F, L = ld;
+            const double gain = (F - Fn) / L;
+            const int accept = (L > 0.0) && isfinite(Fn) && (gain > O.min_rel_dec);
+            double radius = S.radius;
+            if (accept) {
+                const double tt = 2.0 * gain - 1.0;
+                const double shrink = 1.0 - tt * tt * tt;
+                radius = radius / fmax(shrink, 1.0 / 3.0);
+                S.factor = 2.0;
+                if (O.function_tol > 0.0 && fabs(F - Fn) < O.function_tol * F) S.done = 1;
+                S.F = Fn;
+                S.mu_acc = mu;
+                S.acc_total += 1;
+                S.relin = 1;
+            } else {
+                radius = radius / S.factor;
+                S.factor *= 2.0;
+            }
+            S.radius = fmin(fmax(radius, 1e-32), 1e16);
+            S.mu = mu;
+            S.accept = accept;
+            S.pcg_total += np_;
+            S.iter = it + 1;
+        }
+        __syncthreads();
+        if (S.accept) {
+            for (int t = tid; t < m9; t += NT) M.cams[t] = M.camn[t];
+            for (int t = tid; t < 3 * d.np; t += NT)
+                A.pts[3 * (int64_t)d.pt0 + t] = A.pts_new[3 * (int64_t)d.pt0 + t];
+        }
+        __syncthreads();
+    }
+    // adjoint at the solution (mba_adjoint): v = M^-1 gbar, dL/du_k = W_k J_k v, dL/dx0 = mu D v
+    if (O.adjoint) {
+        if (S.status == MBA_OK && (O.adj_mu >= 0.0 || S.acc_total > 0)) {
+            tables64<T, NT>(M, M.cams, d.nc);
+            __syncthreads();
+            if (S.relin) {
+                linearize<T, NT>(A, M, d);
+                if (tid == 0) S.relin = 0;
+            }
+            const double mu = O.adj_mu >= 0.0 ? O.adj_mu : S.mu_acc;
+            damp<T, NT>(A, M, S, d, mu, O.damping);
+            __syncthreads();
+            if (S.status == MBA_OK) {
+                const int na = pcg<T, NT>(A, M, d, A.gbar_c + 9 * (int64_t)d.cam0, A.gbar_p, mu, O.damping,
+                                          O.adj_pcg_max, O.adj_pcg_tol);
+                make_pv<T, NT>(M, M.x, d.nc);
+                __syncthreads();
+                back_points<T, NT>(A, M, d, A.gbar_p, true);
+                __syncthreads();
+                for (int t = tid; t < m9; t += NT) {
+                    const int i = t / 9, a = t - 9 * (t / 9);
+                    A.grad_c0[9 * (int64_t)d.cam0 + t] =
+                        mu * damp_term_b(O.damping, M.Hpp[45 * i + sym9(a, a)]) * M.x[t];
+                }
+                for (int t = tid; t < 3 * d.np; t += NT) {
+                    const int64_t j = d.pt0 + t / 3;
+                    const int a = t - 3 * (t / 3);
+                    A.grad_p0[3 * j + a] =
+                        mu * damp_term_b(O.damping, A.Hll[6 * j + sym3(a, a)]) * A.dp[3 * j + a];
+                }
+                if (tid == 0) S.adj_iters = na;
+            }
+        } else if (S.status == MBA_OK) {
+            // no accepted step: x* = x0 for any nearby input
+            for (int k = tid; k < d.n; k += NT) {
+                const int64_t o = __ldg(A.pm_orig + d.obs0 + k);
+                A.grad_obs[2 * o] = 0.0;
+                A.grad_obs[2 * o + 1] = 0.0;
+            }
+            for (int t = tid; t < m9; t += NT) A.grad_c0[9 * (int64_t)d.cam0 + t] = A.gbar_c[9 * (int64_t)d.cam0 + t];
+            for (int t = tid; t < 3 * d.np; t += NT)
+                A.grad_p0[3 * (int64_t)d.pt0 + t] = A.gbar_p[3 * (int64_t)d.pt0 + t];
+        }
+        __syncthreads();
+        if (S.status != MBA_OK) {
+            for (int k = tid; k < d.n; k += NT) {
+                const int64_t o = __ldg(A.pm_orig + d.obs0 + k);
+                A.grad_obs[2 * o] = 0.0;
+                A.grad_obs[2 * o + 1] = 0.0;
+            }
+            for (int t = tid; t < m9; t += NT) A.grad_c0[9 * (int64_t)d.cam0 + t] = 0.0;
+            for (int t = tid; t < 3 * d.np; t += NT) A.grad_p0[3 * (int64_t)d.pt0 + t] = 0.0;
+        }
+    }
+    for (int t = tid; t < m9; t += NT) A.cams[9 * (int64_t)d.cam0 + t] = M.cams[t];
+    if (tid == 0) {
+        mba_window_summary o;
+        o.iterations = S.iter;
+        o.accepted = S.acc_total;
+        o.pcg_iters_total = S.pcg_total;
+        o.status = S.status;
+        o.initial_cost = S.F0;
+        o.final_cost = S.F;
+        o.final_radius = S.radius;
+        o.mu_accepted = S.mu_acc;
+        o.adjoint_pcg_iters = S.adj_iters;
+        o.pad = 0;
+        A.out[wi] = o;
+    }
+    __syncthreads();
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) batch_kernel(BatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WinState S;
+    WinMem<T> M;
+    win_carve<T>(smem_raw, A.ncmax, NT / 32, M);
+    const BatchOpts O = *A.opts;
+    for (;;) {
+        if (threadIdx.x == 0) S.win = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int k = S.win;
+        __syncthreads();
+        if (k >= A.nw) break;
+        solve_window<T, NT>(A, O, M, S, __ldg(A.order + k));
+    }
+}
+
+template <typename T, int NT>
+size_t smem_bytes(int ncmax) {
+    WinMem<T> m;
+    return win_carve<T>(nullptr, ncmax, NT / 32, m);
+}
+
+const void *kernel_ptr(bool fp32, int nt) {
+    if (fp32) return nt == 256 ? (const void *)batch_kernel<float, 256> : (const void *)batch_kernel<float, 512>;
+    return nt == 256 ? (const void *)batch_kernel<double, 256> : (const void *)batch_kernel<double, 512>;
+}
+
+size_t kernel_smem(bool fp32, int nt, int ncmax) {
+    if (fp32) return nt == 256 ? smem_bytes<float, 256>(ncmax) : smem_bytes<float, 512>(ncmax);
+    return nt == 256 ? smem_bytes<double, 256>(ncmax) : smem_bytes<double, 512>(ncmax);
+}
+
+size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+}  // namespace mba
+
+using namespace mba;
+
+struct mba_batch {
+    int32_t nw = 0, ncmax = 0;
+    int64_t nc = 0, np = 0, n = 0, nch = 0;
+    int fp32 = 0, loss = 0;
+    double delta = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *pool = nullptr;
+    BatchArgs A{};
+    WinDesc *desc = nullptr;
+    int32_t *order = nullptr, *counter = nullptr;
+    BatchOpts *opts = nullptr;
+    mba_window_summary *out = nullptr;
+    double *cams0 = nullptr, *pts0 = nullptr, *cams_bak = nullptr, *pts_bak = nullptr;
+    double *gbar_c = nullptr, *gbar_p = nullptr;
+    int sms = 0;
+    int nt = 0, cps = 0;            // schedule in use
+    cudaGraphExec_t gexec = nullptr;
+    int g_nt = 0, g_grid = 0;       // schedule the graph was captured with
+    bool has_grads = false;
+};
+
+namespace {
+
+#define BCK(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return api_fail(MBA_ERR_CUDA, (std::string(#call) + ": " + cudaGetErrorString(e_)).c_str()); \
+    } while (0)
+
+int max_ctas_per_sm(const mba_batch *b, int nt) {
+    const void *k = kernel_ptr(b->fp32, nt);
+    const size_t sm = kernel_smem(b->fp32, nt, b->ncmax);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, nt, sm) != cudaSuccess) return 0;
+    return blocks;
+}
+
+// Resolves a requested schedule to an admissible one (0 fields: automatic).
+mba_status resolve_schedule(const mba_batch *b, int want_nt, int want_cps, int *nt, int *cps) {
+    if (want_nt != 0 && want_nt != 256 && want_nt != 512)
+        return api_fail(MBA_ERR_INVALID_ARG, "threads_per_cta must be 0, 256 or 512");
+    if (want_cps < 0 || want_cps > 8) return api_fail(MBA_ERR_INVALID_ARG, "ctas_per_sm must be in 0..8");
+    const int t = want_nt ? want_nt : 256;
+    const int occ = max_ctas_per_sm(b, t);
+    if (occ < 1) return api_fail(MBA_ERR_INVALID_ARG, "the batched kernel cannot be resident with this schedule");
+    int c = want_cps ? want_cps : occ;
+    if (c > occ) c = occ;
+    *nt = t;
+    *cps = c;
+    return MBA_OK;
+}
+
+mba_status build_graph(mba_batch *b) {
+    const int grid_full = b->sms * b->cps;
+    const int grid = grid_full < b->nw ? grid_full : b->nw;
+    if (b->gexec && b->g_nt == b->nt && b->g_grid == grid) return MBA_OK;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    const void *k = kernel_ptr(b->fp32, b->nt);
+    const size_t sm = kernel_smem(b->fp32, b->nt, b->ncmax);
+    BCK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(int32_t), b->stream);
+    BatchArgs args = b->A;
+    void *kargs[] = {(void *)&args};
+    cudaError_t e2 = cudaLaunchKernel(k, dim3(grid), dim3(b->nt), kargs, sm, b->stream);
+    cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        const cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+        return api_fail(MBA_ERR_CUDA, (std::string("graph capture: ") + cudaGetErrorString(e)).c_str());
+    }
+    cudaError_t e4 = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) {
+        b->gexec = nullptr;
+        return api_fail(MBA_ERR_CUDA, (std::string("graph instantiate: ") + cudaGetErrorString(e4)).c_str());
+    }
+    b->g_nt = b->nt;
+    b->g_grid = grid;
+    return MBA_OK;
+}
+
+bool finite_all(const double *a, int64_t m) {
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const int64_t *pt_offsets,
+                            const int64_t *obs_offsets, const double *cameras, const double *points,
+                            const double *observations, const int32_t *cam_idx, const int32_t *pt_idx,
+                            const mba_problem_options *opt, mba_batch **out) {
+    if (!out) return api_fail(MBA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_windows < 1) return api_fail(MBA_ERR_INVALID_ARG, "n_windows must be >= 1");
+    if (!cam_offsets || !pt_offsets || !obs_offsets || !cameras || !points || !observations || !cam_idx || !pt_idx)
+        return api_fail(MBA_ERR_INVALID_ARG, "a required input pointer is NULL");
+    mba_problem_options o;
+    mba_problem_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != MBA_FP64 && o.precision != MBA_FP32_MIXED) return api_fail(MBA_ERR_INVALID_ARG, "bad precision");
+    if (o.loss != MBA_LOSS_NONE && o.loss != MBA_LOSS_HUBER) return api_fail(MBA_ERR_INVALID_ARG, "bad loss");
+    if (o.loss == MBA_LOSS_HUBER && !(o.huber_delta > 0.0))
+        return api_fail(MBA_ERR_INVALID_ARG, "huber_delta must be > 0");
+    const int nw = n_windows;
+    if (cam_offsets[0] != 0 || pt_offsets[0] != 0 || obs_offsets[0] != 0)
+        return api_fail(MBA_ERR_INVALID_ARG, "offset arrays must start at 0");
+    int ncmax = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int64_t nc = cam_offsets[w + 1] - cam_offsets[w], np = pt_offsets[w + 1] - pt_offsets[w],
+                      n = obs_offsets[w + 1] - obs_offsets[w];
+        if (nc < 1 || nc > kBMaxCams) return api_fail(MBA_ERR_INVALID_ARG, "a window needs 1..64 cameras");
+        if (np >= (int64_t(1) << 24)) return api_fail(MBA_ERR_INVALID_ARG, "a window may hold at most 2^24 - 1 points");
+        if (np < 1 || n < 1) return api_fail(MBA_ERR_INVALID_ARG, "a window needs >= 1 point and observation");
+        if (nc > ncmax) ncmax = (int)nc;
+    }
+    const int64_t NC = cam_offsets[nw], NP = pt_offsets[nw], N = obs_offsets[nw];
+    if (N >= (int64_t(1) << 31) - 64 || NP >= (int64_t(1) << 31) - 64 || NC >= (int64_t(1) << 31) - 64)
+        return api_fail(MBA_ERR_INVALID_ARG, "totals must be below 2^31 - 64");
+    if (!finite_all(cameras, 9 * NC) || !finite_all(points, 3 * NP) || !finite_all(observations, 2 * N))
+        return api_fail(MBA_ERR_NONFINITE, "non-finite camera, point or observation");
+
+    // ---- host layout: per window, stable point-major and camera-major orders ----
+    std::vector<int2> pm_pc((size_t)N);
+    std::vector<double2> pm_uv((size_t)N);
+    std::vector<int32_t> pm_orig((size_t)N), cm_pt((size_t)N), cm2pm((size_t)N), pm2cm((size_t)N),
+        cam_ptr((size_t)NC + 1);
+    std::vector<int2> wchunk;
+    std::vector<WinDesc> desc((size_t)nw);
+    wchunk.reserve((size_t)(N / 8 + 2 * nw + 16));
+    std::vector<int32_t> cntp, cntc, posp, posc, pmpos;
+    for (int w = 0; w < nw; ++w) {
+        const int32_t c0 = (int32_t)cam_offsets[w], p0 = (int32_t)pt_offsets[w], o0 = (int32_t)obs_offsets[w];
+        const int32_t nc = (int32_t)(cam_offsets[w + 1] - c0), np = (int32_t)(pt_offsets[w + 1] - p0),
+                      n = (int32_t)(obs_offsets[w + 1] - o0);
+        cntp.assign((size_t)np + 1, 0);
+        cntc.assign((size_t)nc + 1, 0);
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
+            if (ci < 0 || ci >= nc || pi < 0 || pi >= np)
+                return api_fail(MBA_ERR_INVALID_ARG, "observation index out of its window's range");
+            cntp[pi + 1]++;
+            cntc[ci + 1]++;
+        }
+        for (int32_t j = 0; j < np; ++j) {
+            if (cntp[j + 1] == 0) return api_fail(MBA_ERR_INVALID_ARG, "a point without observations");
+            cntp[j + 1] += cntp[j];
+        }
+        for (int32_t i = 0; i < nc; ++i) {
+            if (cntc[i + 1] == 0) return api_fail(MBA_ERR_INVALID_ARG, "a camera without observations");
+            cntc[i + 1] += cntc[i];
+        }
+        posp.assign(cntp.begin(), cntp.end() - 1);
+        posc.assign(cntc.begin(), cntc.end() - 1);
+        pmpos.resize((size_t)n);
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
+            const int32_t pp = o0 + posp[pi]++;
+            pm_pc[pp] = make_int2(p0 + pi, c0 + ci);
+            pm_uv[pp] = make_double2(observations[2 * (int64_t)(o0 + k)], observations[2 * (int64_t)(o0 + k) + 1]);
+            pm_orig[pp] = o0 + k;
+            pmpos[k] = pp;
+        }
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
+            const int32_t cp = o0 + posc[ci]++;
+            cm_pt[cp] = p0 + pi;
+            cm2pm[cp] = pmpos[k];
+            pm2cm[pmpos[k]] = cp;
+        }
+        for (int32_t i = 0; i < nc; ++i) cam_ptr[c0 + i] = o0 + cntc[i];
+        // warp chunks: greedy runs of whole points with <= 32 observations
+        WinDesc &d = desc[w];
+        d.cam0 = c0;
+        d.nc = nc;
+        d.pt0 = p0;
+        d.np = np;
+        d.obs0 = o0;
+        d.n = n;
+        d.wch0 = (int32_t)wchunk.size();
+        int32_t j = 0;
+        while (j < np) {
+            wchunk.push_back(make_int2(p0 + j, o0 + cntp[j]));
+            int32_t len = cntp[j + 1] - cntp[j];
+            ++j;
+            if (len <= 32)
+                while (j < np && len + (cntp[j + 1] - cntp[j]) <= 32) {
+                    len += cntp[j + 1] - cntp[j];
+                    ++j;
+                }
+        }
+        d.nwch = (int32_t)wchunk.size() - d.wch0;
+        wchunk.push_back(make_int2(p0 + np, o0 + n));
+        if ((int64_t)wchunk.size() >= (int64_t(1) << 31) - 64)
+            return api_fail(MBA_ERR_INVALID_ARG, "too many warp chunks");
+    }
+    cam_ptr[(size_t)NC] = (int32_t)N;
+    std::vector<int32_t> order((size_t)nw);
+    for (int w = 0; w < nw; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return desc[a].n > desc[b].n; });
+
+    mba_batch *b = new mba_batch();
+    b->nw = nw;
+    b->ncmax = ncmax;
+    b->nc = NC;
+    b->np = NP;
+    b->n = N;
+    b->nch = (int64_t)wchunk.size();
+    b->fp32 = o.precision == MBA_FP32_MIXED;
+    b->loss = o.loss;
+    b->delta = o.huber_delta;
+    auto fail_free = [&](mba_status st, const std::string &msg) {
+        mba_batch_destroy(b);
+        return api_fail(st, msg.c_str());
+    };
+    if (o.cuda_stream) {
+        b->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail_free(MBA_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+        b->own_stream = true;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->sms < 1) return fail_free(MBA_ERR_CUDA, "no CUDA device");
+    const size_t w = b->fp32 ? 4 : 8;
+    // one pool for everything
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o_ = off;
+        off += al256(bytes ? bytes : 1);
+        return o_;
+    };
+    const size_t o_desc = take(sizeof(WinDesc) * nw), o_order = take(4 * (size_t)nw), o_counter = take(256),
+                 o_opts = take(sizeof(BatchOpts)), o_out = take(sizeof(mba_window_summary) * nw),
+                 o_wch = take(sizeof(int2) * b->nch), o_pc = take(sizeof(int2) * N), o_uv = take(sizeof(double2) * N),
+                 o_orig = take(4 * (size_t)N), o_cmpt = take(4 * (size_t)N), o_cm2pm = take(4 * (size_t)N),
+                 o_cptr = take(4 * ((size_t)NC + 1)), o_cams = take(72 * (size_t)NC), o_cams0 = take(72 * (size_t)NC),
+                 o_camsb = take(72 * (size_t)NC), o_pts = take(24 * (size_t)NP), o_pts0 = take(24 * (size_t)NP),
+                 o_ptsb = take(24 * (size_t)NP), o_ptsn = take(24 * (size_t)NP), o_dp = take(24 * (size_t)NP),
+                 o_hll = take(48 * (size_t)NP), o_wv = take(24 * (size_t)NP), o_pm2cm = take(4 * (size_t)N),
+                 o_ci = take(6 * w * (size_t)NP), o_pmx = take(4 * w * (size_t)N), o_pmc = take(8 * w * (size_t)N),
+                 o_cmx = take(4 * w * (size_t)N), o_cms = take(2 * w * (size_t)N),
+                 o_W = o.loss != MBA_LOSS_NONE ? take(w * (size_t)N) : 0, o_gc = take(72 * (size_t)NC),
+                 o_gp = take(24 * (size_t)NP), o_go = take(16 * (size_t)N), o_g0c = take(72 * (size_t)NC),
+                 o_g0p = take(24 * (size_t)NP);
+    if (cudaMalloc(&b->pool, off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_free(MBA_ERR_OOM, "device allocation of the batch failed");
+    }
+    char *base = (char *)b->pool;
+    b->desc = (WinDesc *)(base + o_desc);
+    b->order = (int32_t *)(base + o_order);
+    b->counter = (int32_t *)(base + o_counter);
+    b->opts = (BatchOpts *)(base + o_opts);
+    b->out = (mba_window_summary *)(base + o_out);
+    b->cams0 = (double *)(base + o_cams0);
+    b->pts0 = (double *)(base + o_pts0);
+    b->cams_bak = (double *)(base + o_camsb);
+    b->pts_bak = (double *)(base + o_ptsb);
+    b->gbar_c = (double *)(base + o_gc);
+    b->gbar_p = (double *)(base + o_gp);
+    BatchArgs &A = b->A;
+    A.nw = nw;
+    A.ncmax = ncmax;
+    A.loss = o.loss;
+    A.delta = o.huber_delta;
+    A.desc = b->desc;
+    A.order = b->order;
+    A.counter = b->counter;
+    A.opts = b->opts;
+    A.wchunk = (const int2 *)(base + o_wch);
+    A.pm_pc = (const int2 *)(base + o_pc);
+    A.pm_uv = (const double2 *)(base + o_uv);
+    A.pm_orig = (const int32_t *)(base + o_orig);
+    A.cm_pt = (const int32_t *)(base + o_cmpt);
+    A.cm2pm = (const int32_t *)(base + o_cm2pm);
+    A.cam_ptr = (const int32_t *)(base + o_cptr);
+    A.cams = (double *)(base + o_cams);
+    A.pts = (double *)(base + o_pts);
+    A.pts_new = (double *)(base + o_ptsn);
+    A.dp = (double *)(base + o_dp);
+    A.Hll = (double *)(base + o_hll);
+    A.wv = (double *)(base + o_wv);
+    A.pm2cm = (const int32_t *)(base + o_pm2cm);
+    A.Cinv = base + o_ci;
+    A.pmX = base + o_pmx;
+    A.pmC = base + o_pmc;
+    A.cmX = base + o_cmx;
+    A.cms = base + o_cms;
+    A.Wpm = o.loss != MBA_LOSS_NONE ? (void *)(base + o_W) : nullptr;
+    A.gbar_c = b->gbar_c;
+    A.gbar_p = b->gbar_p;
+    A.grad_obs = (double *)(base + o_go);
+    A.grad_c0 = (double *)(base + o_g0c);
+    A.grad_p0 = (double *)(base + o_g0p);
+    A.out = b->out;
+    cudaStream_t s = b->stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) { return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s); };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = up(b->desc, desc.data(), sizeof(WinDesc) * nw);
+    if (e == cudaSuccess) e = up(b->order, order.data(), 4 * (size_t)nw);
+    if (e == cudaSuccess) e = up((void *)A.wchunk, wchunk.data(), sizeof(int2) * wchunk.size());
+    if (e == cudaSuccess) e = up((void *)A.pm_pc, pm_pc.data(), sizeof(int2) * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.pm_uv, pm_uv.data(), sizeof(double2) * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.pm_orig, pm_orig.data(), 4 * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.cm_pt, cm_pt.data(), 4 * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.cm2pm, cm2pm.data(), 4 * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.pm2cm, pm2cm.data(), 4 * (size_t)N);
+    if (e == cudaSuccess) e = up((void *)A.cam_ptr, cam_ptr.data(), 4 * ((size_t)NC + 1));
+    if (e == cudaSuccess) e = up(A.cams, cameras, 72 * (size_t)NC);
+    if (e == cudaSuccess) e = up(b->cams0, cameras, 72 * (size_t)NC);
+    if (e == cudaSuccess) e = up(A.pts, points, 24 * (size_t)NP);
+    if (e == cudaSuccess) e = up(b->pts0, points, 24 * (size_t)NP);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_obs, 0, 16 * (size_t)N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_c0, 0, 72 * (size_t)NC, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_p0, 0, 24 * (size_t)NP, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    mba_status st = resolve_schedule(b, 0, 0, &b->nt, &b->cps);
+    if (st != MBA_OK) {
+        std::string msg = mba_last_error();
+        mba_batch_destroy(b);
+        return api_fail(st, msg.c_str());
+    }
+    *out = b;
+    return MBA_OK;
+}
+
+void mba_batch_destroy(mba_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->pool) cudaFree(b->pool);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+mba_status mba_batch_info(const mba_batch *b, int32_t *n_windows, int64_t *n_cameras, int64_t *n_points,
+                          int64_t *n_observations, int32_t *max_window_cameras) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    if (n_windows) *n_windows = b->nw;
+    if (n_cameras) *n_cameras = b->nc;
+    if (n_points) *n_points = b->np;
+    if (n_observations) *n_observations = b->n;
+    if (max_window_cameras) *max_window_cameras = b->ncmax;
+    return MBA_OK;
+}
+
+mba_status mba_batch_set_schedule(mba_batch *b, const mba_batch_schedule *sc) {
+    if (!b || !sc) return api_fail(MBA_ERR_INVALID_ARG, "NULL argument");
+    int nt = 0, cps = 0;
+    mba_status st = resolve_schedule(b, sc->threads_per_cta, sc->ctas_per_sm, &nt, &cps);
+    if (st != MBA_OK) return st;
+    b->nt = nt;
+    b->cps = cps;
+    return MBA_OK;
+}
+
+mba_status mba_batch_get_schedule(const mba_batch *b, mba_batch_schedule *sc) {
+    if (!b || !sc) return api_fail(MBA_ERR_INVALID_ARG, "NULL argument");
+    sc->threads_per_cta = b->nt;
+    sc->ctas_per_sm = b->cps;
+    return MBA_OK;
+}
+
+mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mba_batch_adjoint *adj,
+                           mba_window_summary *summaries, double *ms) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    mba_solver_options o;
+    mba_solver_options_default(&o);
+    if (opt) o = *opt;
+    if (o.max_iter < 0 || o.pcg_max_iter < 0 || !(o.pcg_rel_tol >= 0.0) || !(o.initial_radius > 0.0) ||
+        (o.damping != MBA_DAMP_DIAG && o.damping != MBA_DAMP_IDENTITY))
+        return api_fail(MBA_ERR_INVALID_ARG, "bad solver options");
+    if (adj && (!adj->grad_cameras || !adj->grad_points || adj->pcg_max_iter < 0 || !(adj->pcg_rel_tol >= 0.0)))
+        return api_fail(MBA_ERR_INVALID_ARG, "bad adjoint arguments");
+    cudaStream_t s = b->stream;
+    BatchOpts bo{};
+    bo.max_iter = o.max_iter;
+    bo.pcg_max_iter = o.pcg_max_iter;
+    bo.damping = o.damping;
+    bo.adjoint = adj ? 1 : 0;
+    bo.adj_pcg_max = adj ? adj->pcg_max_iter : 0;
+    bo.pcg_tol = o.pcg_rel_tol;
+    bo.initial_radius = o.initial_radius;
+    bo.min_rel_dec = o.min_relative_decrease;
+    bo.function_tol = o.function_tol;
+    bo.adj_pcg_tol = adj ? adj->pcg_rel_tol : 0.0;
+    bo.adj_mu = adj ? adj->mu : -1.0;
+    BCK(cudaMemcpyAsync(b->opts, &bo, sizeof(bo), cudaMemcpyHostToDevice, s));
+    if (adj) {
+        BCK(cudaMemcpyAsync(b->gbar_c, adj->grad_cameras, 72 * (size_t)b->nc, cudaMemcpyHostToDevice, s));
+        BCK(cudaMemcpyAsync(b->gbar_p, adj->grad_points, 24 * (size_t)b->np, cudaMemcpyHostToDevice, s));
+    }
+    mba_status st = build_graph(b);
+    if (st != MBA_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        BCK(cudaEventCreate(&e0));
+        BCK(cudaEventCreate(&e1));
+        BCK(cudaEventRecord(e0, s));
+    }
+    BCK(cudaGraphLaunch(b->gexec, s));
+    if (ms) BCK(cudaEventRecord(e1, s));
+    std::vector<mba_window_summary> sum((size_t)b->nw);
+    BCK(cudaMemcpyAsync(sum.data(), b->out, sizeof(mba_window_summary) * b->nw, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    if (ms) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms = t;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (adj) b->has_grads = true;
+    if (summaries) std::memcpy(summaries, sum.data(), sizeof(mba_window_summary) * b->nw);
+    for (int w = 0; w < b->nw; ++w)
+        if (sum[w].status != MBA_OK) {
+            char buf[96];
+            std::snprintf(buf, sizeof(buf), "window %d: %s", w, mba_status_string((mba_status)sum[w].status));
+            return api_fail((mba_status)sum[w].status, buf);
+        }
+    return MBA_OK;
+}
+
+mba_status mba_batch_autotune(mba_batch *b, const mba_solver_options *opt, mba_batch_schedule *chosen,
+                              double *ms_best) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = b->stream;
+    BCK(cudaMemcpyAsync(b->cams_bak, b->A.cams, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, s));
+    BCK(cudaMemcpyAsync(b->pts_bak, b->A.pts, 24 * (size_t)b->np, cudaMemcpyDeviceToDevice, s));
+    const int nt0 = b->nt, cps0 = b->cps;
+    double best = -1.0;
+    int bnt = nt0, bcps = cps0;
+    const int nts[2] = {256, 512};
+    for (int a = 0; a < 2; ++a) {
+        const int occ = max_ctas_per_sm(b, nts[a]);
+        for (int c = 1; c <= occ && c <= 8; ++c) {
+            b->nt = nts[a];
+            b->cps = c;
+            double t = 0.0;
+            mba_status st = mba_batch_solve(b, opt, nullptr, nullptr, &t);
+            BCK(cudaMemcpyAsync(b->A.cams, b->cams_bak, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, s));
+            BCK(cudaMemcpyAsync(b->A.pts, b->pts_bak, 24 * (size_t)b->np, cudaMemcpyDeviceToDevice, s));
+            BCK(cudaStreamSynchronize(s));
+            if (st != MBA_OK && st != MBA_ERR_NONFINITE) {
+                b->nt = nt0;
+                b->cps = cps0;
+                return st;
+            }
+            if (best < 0.0 || t < best) {
+                best = t;
+                bnt = nts[a];
+                bcps = c;
+            }
+        }
+    }
+    b->nt = bnt;
+    b->cps = bcps;
+    if (chosen) {
+        chosen->threads_per_cta = bnt;
+        chosen->ctas_per_sm = bcps;
+    }
+    if (ms_best) *ms_best = best;
+    return MBA_OK;
+}
+
+mba_status mba_batch_get_parameters(const mba_batch *b, double *cameras, double *points) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    if (cameras) BCK(cudaMemcpyAsync(cameras, b->A.cams, 72 * (size_t)b->nc, cudaMemcpyDeviceToHost, b->stream));
+    if (points) BCK(cudaMemcpyAsync(points, b->A.pts, 24 * (size_t)b->np, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MBA_OK;
+}
+
+mba_status mba_batch_set_parameters(mba_batch *b, const double *cameras, const double *points) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    if ((cameras && !finite_all(cameras, 9 * b->nc)) || (points && !finite_all(points, 3 * b->np)))
+        return api_fail(MBA_ERR_NONFINITE, "non-finite parameters");
+    if (cameras) BCK(cudaMemcpyAsync(b->A.cams, cameras, 72 * (size_t)b->nc, cudaMemcpyHostToDevice, b->stream));
+    if (points) BCK(cudaMemcpyAsync(b->A.pts, points, 24 * (size_t)b->np, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MBA_OK;
+}
+
+mba_status mba_batch_reset(mba_batch *b) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    BCK(cudaMemcpyAsync(b->A.cams, b->cams0, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->A.pts, b->pts0, 24 * (size_t)b->np, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MBA_OK;
+}
+
+mba_status mba_batch_get_gradients(const mba_batch *b, double *grad_obs, double *grad_init_cam,
+                                   double *grad_init_pt) {
+    if (!b) return api_fail(MBA_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->has_grads) return api_fail(MBA_ERR_INVALID_ARG, "no solve with an adjoint has run");
+    if (grad_obs) BCK(cudaMemcpyAsync(grad_obs, b->A.grad_obs, 16 * (size_t)b->n, cudaMemcpyDeviceToHost, b->stream));
+    if (grad_init_cam)
+        BCK(cudaMemcpyAsync(grad_init_cam, b->A.grad_c0, 72 * (size_t)b->nc, cudaMemcpyDeviceToHost, b->stream));
+    if (grad_init_pt)
+        BCK(cudaMemcpyAsync(grad_init_pt, b->A.grad_p0, 24 * (size_t)b->np, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MBA_OK;
+}
+
+}  // extern "C"

@@ -382,6 +382,9 @@ cudaError_t launch_adjoint_obs(const Prob &P, const int32_t *ci, const int32_t *
                                double *out, cudaStream_t s);
 cudaError_t launch_adjoint_init(const Prob &P, int damping, double mu, cudaStream_t s);
 
+// api.cu: records msg as the calling thread's mba_last_error() text and returns st
+mba_status api_fail(mba_status st, const char *msg);
+
 // lm.cu
 cudaError_t launch_state_init(const Prob &P, double radius, double mu_override, int keep_cost, cudaStream_t s);
 cudaError_t launch_lm_update(const Prob &P, const mba_solver_options &o, cudaStream_t s);

@@ -58,6 +58,22 @@ class Summary(C.Structure):
                 ("trace", C.POINTER(Iteration)), ("trace_capacity", C.c_int32)]
 
 
+class WindowSummary(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("pcg_iters_total", C.c_int32),
+                ("status", C.c_int32), ("initial_cost", C.c_double), ("final_cost", C.c_double),
+                ("final_radius", C.c_double), ("mu_accepted", C.c_double), ("adjoint_pcg_iters", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class BatchSchedule(C.Structure):
+    _fields_ = [("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class BatchAdjoint(C.Structure):
+    _fields_ = [("grad_cameras", C.c_void_p), ("grad_points", C.c_void_p), ("pcg_max_iter", C.c_int32),
+                ("pad", C.c_int32), ("pcg_rel_tol", C.c_double), ("mu", C.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -93,6 +109,17 @@ def load():
             "mba_step": (C.c_int, [P, dbl, P, P, P, P, P]),
             "mba_cost_noalloc": (C.c_int, [P, i32, P, i32, P, P, P, i64, i32, dbl, P, P]),
             "mba_adjoint": (C.c_int, [P, P, dbl, P, P, P, P, P, P]),
+            "mba_batch_create": (C.c_int, [i32, P, P, P, P, P, P, P, P, P, P]),
+            "mba_batch_destroy": (None, [P]),
+            "mba_batch_info": (C.c_int, [P, P, P, P, P, P]),
+            "mba_batch_set_schedule": (C.c_int, [P, P]),
+            "mba_batch_get_schedule": (C.c_int, [P, P]),
+            "mba_batch_autotune": (C.c_int, [P, P, P, P]),
+            "mba_batch_solve": (C.c_int, [P, P, P, P, P]),
+            "mba_batch_get_parameters": (C.c_int, [P, P, P]),
+            "mba_batch_set_parameters": (C.c_int, [P, P, P]),
+            "mba_batch_reset": (C.c_int, [P]),
+            "mba_batch_get_gradients": (C.c_int, [P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
         }
@@ -368,3 +395,191 @@ class Problem:
 
     def adjoint(self, grad_cameras, grad_points, mu=-1.0, **opts):
         return mba_adjoint(self.handle, grad_cameras, grad_points, mu, **opts)
+
+
+# ---------------------------------------------------------------------------
+# batched windows
+# ---------------------------------------------------------------------------
+def _vp(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def mba_batch_create(cam_offsets, pt_offsets, obs_offsets, cameras, points, observations, cam_idx, pt_idx,
+                     precision="fp32", loss="none", huber_delta=0.0, stream=None) -> C.c_void_p:
+    """Concatenated windows (offset arrays of n_windows + 1 entries; cam_idx / pt_idx local to the window)."""
+    co = np.ascontiguousarray(cam_offsets, dtype=np.int64)
+    po = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+    oo = np.ascontiguousarray(obs_offsets, dtype=np.int64)
+    nw = len(co) - 1
+    if nw < 1 or len(po) != nw + 1 or len(oo) != nw + 1:
+        raise ValueError("offset arrays must have n_windows + 1 entries")
+    cams = np.ascontiguousarray(cameras, dtype=np.float64).reshape(-1, 9)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    obs = np.ascontiguousarray(observations, dtype=np.float64).reshape(-1, 2)
+    ci = np.ascontiguousarray(cam_idx, dtype=np.int32)
+    pi = np.ascontiguousarray(pt_idx, dtype=np.int32)
+    if len(cams) != co[-1] or len(pts) != po[-1] or len(obs) != oo[-1] or len(ci) != oo[-1] or len(pi) != oo[-1]:
+        raise ValueError("array lengths must match the last offsets")
+    o = mba_problem_options_default()
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
+    o.huber_delta = float(huber_delta)
+    o.cuda_stream = _stream_handle(stream)
+    h = C.c_void_p()
+    _check(load().mba_batch_create(nw, _vp(co), _vp(po), _vp(oo), _vp(cams), _vp(pts), _vp(obs), _vp(ci), _vp(pi),
+                                   C.byref(o), C.byref(h)))
+    return h
+
+
+def mba_batch_destroy(h):
+    if h:
+        load().mba_batch_destroy(h)
+
+
+def mba_batch_info(h):
+    nw, mc = C.c_int32(), C.c_int32()
+    nc, np_, n = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().mba_batch_info(h, C.byref(nw), C.byref(nc), C.byref(np_), C.byref(n), C.byref(mc)))
+    return dict(n_windows=nw.value, nc=nc.value, np=np_.value, n=n.value, max_window_cameras=mc.value)
+
+
+def mba_batch_set_schedule(h, threads_per_cta=0, ctas_per_sm=0):
+    sc = BatchSchedule(int(threads_per_cta), int(ctas_per_sm))
+    _check(load().mba_batch_set_schedule(h, C.byref(sc)))
+
+
+def mba_batch_get_schedule(h):
+    sc = BatchSchedule()
+    _check(load().mba_batch_get_schedule(h, C.byref(sc)))
+    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm)
+
+
+def mba_batch_autotune(h, **opts):
+    o = solver_options(**opts)
+    sc = BatchSchedule()
+    ms = C.c_double()
+    _check(load().mba_batch_autotune(h, C.byref(o), C.byref(sc), C.byref(ms)))
+    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm, ms=ms.value)
+
+
+def _summaries(arr):
+    names = [f[0] for f in WindowSummary._fields_ if f[0] != "pad"]
+    return [{k: getattr(s, k) for k in names} for s in arr]
+
+
+def mba_batch_solve(h, grad_cameras=None, grad_points=None, adjoint_pcg_max_iter=500, adjoint_pcg_rel_tol=1e-12,
+                    adjoint_mu=-1.0, check=True, **opts):
+    """Solves every window; with grad_cameras / grad_points also runs the adjoint.
+
+    Returns dict(summaries=[per-window dict], ms=device time of the launch, status)."""
+    info = mba_batch_info(h)
+    o = solver_options(**opts)
+    adj = None
+    keep = []
+    if grad_cameras is not None or grad_points is not None:
+        gc = np.ascontiguousarray(grad_cameras, dtype=np.float64).reshape(info["nc"], 9)
+        gp = np.ascontiguousarray(grad_points, dtype=np.float64).reshape(info["np"], 3)
+        keep = [gc, gp]
+        adj = BatchAdjoint(_vp(gc), _vp(gp), int(adjoint_pcg_max_iter), 0, float(adjoint_pcg_rel_tol),
+                           float(adjoint_mu))
+    arr = (WindowSummary * info["n_windows"])()
+    ms = C.c_double()
+    st = load().mba_batch_solve(h, C.byref(o), C.byref(adj) if adj is not None else None, arr, C.byref(ms))
+    del keep
+    if check:
+        _check(st)
+    return dict(summaries=_summaries(arr), ms=ms.value, status=st)
+
+
+def mba_batch_get_parameters(h):
+    info = mba_batch_info(h)
+    cams, pts = np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
+    _check(load().mba_batch_get_parameters(h, _vp(cams), _vp(pts)))
+    return cams, pts
+
+
+def mba_batch_set_parameters(h, cameras=None, points=None):
+    info = mba_batch_info(h)
+    c = None if cameras is None else np.ascontiguousarray(cameras, dtype=np.float64).reshape(info["nc"], 9)
+    p = None if points is None else np.ascontiguousarray(points, dtype=np.float64).reshape(info["np"], 3)
+    _check(load().mba_batch_set_parameters(h, None if c is None else _vp(c), None if p is None else _vp(p)))
+
+
+def mba_batch_reset(h):
+    _check(load().mba_batch_reset(h))
+
+
+def mba_batch_get_gradients(h):
+    info = mba_batch_info(h)
+    go, gc, gp = np.zeros((info["n"], 2)), np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
+    _check(load().mba_batch_get_gradients(h, _vp(go), _vp(gc), _vp(gp)))
+    return dict(grad_obs=go, grad_init_cam=gc, grad_init_pt=gp)
+
+
+def concat_windows(windows):
+    """Offsets and concatenated arrays of a list of (cameras, points, observations, cam_idx, pt_idx)."""
+    co, po, oo = [0], [0], [0]
+    for c, p, o, _, _ in windows:
+        co.append(co[-1] + len(c))
+        po.append(po[-1] + len(p))
+        oo.append(oo[-1] + len(o))
+    cat = lambda i, dt: np.concatenate([np.asarray(w[i], dtype=dt) for w in windows])  # noqa: E731
+    return (np.array(co, np.int64), np.array(po, np.int64), np.array(oo, np.int64), cat(0, np.float64).reshape(-1, 9),
+            cat(1, np.float64).reshape(-1, 3), cat(2, np.float64).reshape(-1, 2), cat(3, np.int32), cat(4, np.int32))
+
+
+class Batch:
+    """Owning wrapper over one mba_batch handle (windows given as a list of
+    (cameras, points, observations, cam_idx, pt_idx) with window-local indices)."""
+
+    def __init__(self, windows, precision="fp32", loss="none", huber_delta=0.0, stream=None):
+        self.offsets = concat_windows(windows)[:3]
+        self.handle = mba_batch_create(*concat_windows(windows), precision=precision, loss=loss,
+                                       huber_delta=huber_delta, stream=stream)
+        self.info = mba_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            mba_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, grad_cameras=None, grad_points=None, **opts):
+        return mba_batch_solve(self.handle, grad_cameras, grad_points, **opts)
+
+    def autotune(self, **opts):
+        return mba_batch_autotune(self.handle, **opts)
+
+    def set_schedule(self, threads_per_cta=0, ctas_per_sm=0):
+        mba_batch_set_schedule(self.handle, threads_per_cta, ctas_per_sm)
+
+    def schedule(self):
+        return mba_batch_get_schedule(self.handle)
+
+    def parameters(self):
+        return mba_batch_get_parameters(self.handle)
+
+    def window_parameters(self, w):
+        cams, pts = self.parameters()
+        co, po, _ = self.offsets
+        return cams[co[w]:co[w + 1]], pts[po[w]:po[w + 1]]
+
+    def set_parameters(self, cameras=None, points=None):
+        mba_batch_set_parameters(self.handle, cameras, points)
+
+    def reset(self):
+        mba_batch_reset(self.handle)
+
+    def gradients(self):
+        return mba_batch_get_gradients(self.handle)
