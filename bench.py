@@ -61,6 +61,19 @@ def pcg_bytes_per_iter(sc, w: int) -> float:
     return sc.n * (24 * w + 4) + sc.np_ * (6 * w + 4) + sc.nc * (2 * 81 * 8 + 6 * 9 * 8)
 
 
+# FP32 non-tensor peak derived from unit counts and clocks: 152 SMs x 128 FP32
+# lanes x 2 FLOP (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Batched windows: FP32 operations of one PCG iteration per observation in the
+# matrix-free passes (projection, D and Jp: 88; Jc p: 42; W Jp^T t: 14; scan
+# adds: 15; C~^-1: 18; s = W Jp b: 14; camera pass Jc^T s with its projection:
+# 115), and the bytes that pass must move per observation: (point, camera) 8,
+# camera-major position 4, s written 8 and read 8, camera-major X 16, plus per
+# point X 16 and C~^-1 24 (amortised over the track, mean 4.03).
+BATCH_FLOP_PER_OBS_ITER = 305
+BATCH_BYTES_PER_OBS_ITER = 8 + 4 + 8 + 8 + 16 + 40 / 4.03
+
+
 def pcg_flops_per_iter(sc) -> float:
     """48 FMA per observation (E^T p and E b), 9 per point (C~^-1), 2 x 81 per camera."""
     return 2.0 * (48 * sc.n + 9 * sc.np_ + 162 * sc.nc)
@@ -330,6 +343,83 @@ def main():
                  "forward_ms": 1e3 * min(fwd), "adjoint_ms": 1e3 * min(adj), "lm_iterations": s4["iterations"],
                  "adjoint_pcg_iters": a4["pcg_iters"]}
 
+    # batched local-BA windows (512 windows, cameras U[5,30], points U[200,3000],
+    # track 2 + Geom (mean 4), FP32-mixed): 8 LM iterations per window and the
+    # adjoint, one persistent launch replayed from a CUDA graph
+    batched = None
+    if rank == 0:
+        from scenes import make_windows
+
+        ws = make_windows(512)
+        tup = [(w.cameras, w.points, w.observations, w.cam_idx, w.pt_idx) for w in ws]
+        bopts = dict(max_iter=8, pcg_max_iter=PCG_MAX, pcg_rel_tol=1e-10)
+        rng = np.random.default_rng(5)
+        with mba.Batch(tup, precision="fp32", stream=stream) as bt:
+            gcb, gpb = rng.normal(size=(bt.info["nc"], 9)), rng.normal(size=(bt.info["np"], 3))
+            tune = bt.autotune(**bopts)
+            fwd_ms, full_ms = [], []
+            for rep in range(3):
+                bt.reset()
+                fwd_ms.append(bt.solve(**bopts)["ms"])
+                bt.reset()
+                rb = bt.solve(gcb, gpb, adjoint_pcg_max_iter=500, adjoint_pcg_rel_tol=1e-10, **bopts)
+                full_ms.append(rb["ms"])
+            sm_b = rb["summaries"]
+        nobs = sum(w.n for w in ws)
+        pcg_b = sum(x["pcg_iters_total"] for x in sm_b)
+        adj_b = sum(x["adjoint_pcg_iters"] for x in sm_b)
+        # obs-iterations of the PCG passes (forward right-hand sides + iterations, adjoint the same)
+        obs_it = sum(w.n * (x["pcg_iters_total"] + x["iterations"] + x["adjoint_pcg_iters"] + 1)
+                     for w, x in zip(ws, sm_b))
+        t_full = statistics.median(full_ms)
+        # end to end: pinned host buffers -> create (layout + H2D) -> solve + adjoint -> D2H of the
+        # parameters and gradients -> destroy
+        co, po, oo, cams_c, pts_c, obs_c, ci_c, pi_c = mba.concat_windows(tup)
+        hb = [pin(a) for a in (cams_c, pts_c, obs_c, ci_c, pi_c)]
+        hb_out = [torch.empty_like(hb[0]).pin_memory(), torch.empty_like(hb[1]).pin_memory(),
+                  torch.empty((nobs, 2), dtype=torch.float64).pin_memory()]
+        h2d_b = sum(t.numel() * t.element_size() for t in hb) + 8 * (len(co) + len(po) + len(oo))
+        d2h_b = sum(t.numel() * t.element_size() for t in hb_out)
+
+        def batch_e2e():
+            h = mba.mba_batch_create(co, po, oo, hb[0], hb[1], hb[2], hb[3], hb[4], precision="fp32", stream=stream)
+            mba.mba_batch_set_schedule(h, tune["threads_per_cta"], tune["ctas_per_sm"])
+            mba.mba_batch_solve(h, gcb, gpb, adjoint_pcg_max_iter=500, adjoint_pcg_rel_tol=1e-10, **bopts)
+            cv = mba.mba_batch_get_parameters(h)
+            g = mba.mba_batch_get_gradients(h)
+            hb_out[0].numpy()[:] = cv[0]
+            hb_out[1].numpy()[:] = cv[1]
+            hb_out[2].numpy()[:] = g["grad_obs"]
+            mba.mba_batch_destroy(h)
+
+        batch_e2e()
+        t0b = time.perf_counter()
+        for _ in range(2):
+            batch_e2e()
+        e2e_b = (time.perf_counter() - t0b) / 2
+        flops = obs_it * BATCH_FLOP_PER_OBS_ITER
+        batched = {
+            "workload": f"batched local BA: {len(ws)} windows (cameras U[5,30], points U[200,3000], track 2+Geom "
+                        f"mean 4, 1 px noise), {bt.info['nc']} cameras, {bt.info['np']} points, {nobs} observations "
+                        "in total, FP32-mixed, 8 LM iterations per window (PCG <= 100, rel tol 1e-10) + adjoint",
+            "ms_forward_plus_adjoint": t_full, "ms_forward": statistics.median(fwd_ms),
+            "windows_per_s": len(ws) / (t_full / 1e3),
+            "window_lm_iterations_per_s": sum(x["iterations"] for x in sm_b) / (t_full / 1e3),
+            "pcg_iters_forward": pcg_b, "pcg_iters_adjoint": adj_b,
+            "schedule": {"threads_per_cta": tune["threads_per_cta"], "ctas_per_sm": tune["ctas_per_sm"],
+                         "autotune_ms": tune["ms"]},
+            "launch": "one CUDA graph replay (claim-counter reset + one persistent kernel)",
+            "gpu_launches": 1,
+            "roofline": {"kernel": "batch_kernel (persistent, one window per CTA)", "bound": "alu",
+                         "achieved": flops / (t_full / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / (t_full / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
+                         "hbm_gbs": obs_it * BATCH_BYTES_PER_OBS_ITER / (t_full / 1e3) / 1e9,
+                         "note": "whole launch time; latency-bound (see profiles/)"},
+            "e2e": {"ms": 1e3 * e2e_b, "windows_per_s": len(ws) / e2e_b, "h2d_bytes_per_step": h2d_b,
+                    "d2h_bytes_per_step": d2h_b},
+        }
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -367,6 +457,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": s32 and sum(s["kernel_launches"] for s in s32),
         "layer": layer,
+        "batched": batched,
         "clocks": clk32,
     }
     print(json.dumps(line), flush=True)

@@ -265,13 +265,16 @@ typedef struct {
 } mba_window_summary;
 
 /* Launch schedule of the batched kernel.  threads_per_cta: 256 or 512;
- * ctas_per_sm: resident windows per SM (1..8, capped by occupancy).  Zero
- * fields choose automatically.  The schedule changes the order of the FP32 /
- * FP64 partial sums inside a window (results agree to rounding), never the
- * method; a given schedule gives the same bits on every run. */
+ * ctas_per_sm: resident windows per SM (1..4, capped by occupancy); schur: how
+ * the PCG forms S p (Alg. 3): 1 = implicit (two passes over the observations
+ * per iteration), 2 = explicit (S formed once per damped solve as 9x9 blocks,
+ * then a dense product per iteration).  Zero fields choose automatically.  The
+ * schedule changes the rounding inside a window (results agree to rounding),
+ * never the method; a given schedule gives the same bits on every run. */
 typedef struct {
     int32_t threads_per_cta;
     int32_t ctas_per_sm;
+    int32_t schur;
 } mba_batch_schedule;
 
 /* Upstream gradient for the adjoint of every window (same form as

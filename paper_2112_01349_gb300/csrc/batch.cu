@@ -51,10 +51,11 @@ struct WinDesc {
     int32_t pt0, np;     // first point, count
     int32_t obs0, n;     // first observation of the point- and camera-major regions, count
     int32_t wch0, nwch;  // warp chunks [wch0, wch0 + nwch) and their end entry wch0 + nwch
+    int32_t blk0, pad;   // first entry of the window's Schur-block pair offsets (nc (nc + 1) / 2 + 1 entries)
 };
 
 struct BatchOpts {
-    int32_t max_iter, pcg_max_iter, damping, adjoint, adj_pcg_max, pad;
+    int32_t max_iter, pcg_max_iter, damping, adjoint, adj_pcg_max, explicit_schur;
     double pcg_tol, initial_radius, min_rel_dec, function_tol, adj_pcg_tol, adj_mu;
 };
 
@@ -76,10 +77,15 @@ struct BatchArgs {
     const int32_t *pm2cm;     // point-major -> camera-major position
     void *Cinv;               // [np][6] T: packed inverse of the damped C~
     void *Wpm;                // [n] T: IRLS weight, point-major (NULL without a loss)
-    void *pmX;                // [n][4] T: the observation's point, point-major (per linearisation)
-    void *pmC;                // [n][8] T: C~^-1 of its point, W, (local point << 6 | local camera) (per solve)
+    void *Xw;                 // [np][4] T: the point (per linearisation)
     void *cmX;                // [n][4] T: the observation's point, camera-major (per linearisation)
     void *cms;                // [n] T2: s_k = W Jp b_j, camera-major (per PCG pass)
+    // explicit Schur complement (when selected)
+    void *Jcm;                // [n][24] T: sqrt(W)-scaled Jc (18) and Jp (6), camera-major (per linearisation)
+    const int32_t *blk_ptr;   // pair offsets of each upper 9x9 block (i <= k) of each window
+    const int2 *pairs;        // (camera-major position in camera i, in camera k) of one point, per block
+    void *S;                  // per CTA: packed upper blocks of S~ (smax values of T)
+    int64_t smax;
     const double *gbar_c, *gbar_p;
     double *grad_obs, *grad_c0, *grad_p0;
     mba_window_summary *out;
@@ -100,8 +106,16 @@ struct V2<double> {
 template <typename T>
 struct WinMem {
     double *cams, *camn, *tab64, *Hpp, *v, *Binv, *x, *r, *z, *p, *q, *slot, *sb;
-    T *tabT, *pv;
+    T *tabT, *pv, *stage;
     int32_t *cptr, *wf, *wl, *wcam0;
+};
+
+// Pairs staged per warp while a Schur block is formed, and the stride of one
+// staged pair (Jc~ of the first observation, F = G Jc~ of the second; padded).
+template <typename T>
+struct Stage {
+    static constexpr int pairs = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int stride = 37;
 };
 
 template <typename T>
@@ -133,6 +147,7 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
     m.wf = (int32_t *)take(4 * (size_t)ncmax);
     m.wl = (int32_t *)take(4 * (size_t)ncmax);
     m.wcam0 = (int32_t *)take(4 * (size_t)nwarp);
+    m.stage = (T *)take(sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp);
     return (size_t)off;
 }
 
@@ -174,8 +189,15 @@ __device__ __forceinline__ double2 cta_sum2(double a, double b, double *sb) {
 
 template <typename T>
 __device__ __forceinline__ void ld_c(const T *Ci, int pt, T *c) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) c[q] = Ci[6 * (int64_t)pt + q];
+    using T2 = typename V2<T>::type;
+    const T2 *p = reinterpret_cast<const T2 *>(Ci + 6 * (int64_t)pt);
+    const T2 a = p[0], b = p[1], e = p[2];
+    c[0] = a.x;
+    c[1] = a.y;
+    c[2] = b.x;
+    c[3] = b.y;
+    c[4] = e.x;
+    c[5] = e.y;
 }
 
 template <typename T>
@@ -334,12 +356,6 @@ __device__ __forceinline__ void st4<double>(double *p, double a, double b, doubl
     reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
     reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
 }
-// (local point << 6) | local camera, carried in the record's last T slot
-__device__ __forceinline__ float key_bits(float, int k) { return __int_as_float(k); }
-__device__ __forceinline__ double key_bits(double, int k) { return __longlong_as_double((long long)k); }
-__device__ __forceinline__ int key_of(float v) { return __float_as_int(v); }
-__device__ __forceinline__ int key_of(double v) { return (int)__double_as_longlong(v); }
-
 template <typename T>
 struct PmRec {
     T X0, X1, X2, W;
@@ -348,16 +364,34 @@ struct PmRec {
     int cm;   // camera-major position of the observation
 };
 
+// Per-observation words of a record (coalesced): (point, camera), the
+// camera-major position and the IRLS weight.
 template <typename T>
-__device__ __forceinline__ void load_rec(const BatchArgs &A, int o, PmRec<T> &r) {
-    const T *px = (const T *)A.pmX + 4 * (int64_t)o;
-    const T *pc = (const T *)A.pmC + 8 * (int64_t)o;
-    T unused, kb;
-    ld4<T>(px, r.X0, r.X1, r.X2, unused);
-    ld4<T>(pc, r.c[0], r.c[1], r.c[2], r.c[3]);
-    ld4<T>(pc + 4, r.c[4], r.c[5], r.W, kb);
-    r.key = key_of(kb);
-    r.cm = __ldg(A.pm2cm + o);
+__device__ __forceinline__ void load_idx(const BatchArgs &A, int o, int2 &pc, int &cm, T &W) {
+    pc = __ldg(A.pm_pc + o);
+    cm = __ldg(A.pm2cm + o);
+    W = A.Wpm ? ((const T *)A.Wpm)[o] : T(1);
+}
+
+// Per-point words of a record (gathered; lanes of one point share them):
+// the point in T and the packed C~^-1.
+template <typename T>
+__device__ __forceinline__ void load_pt(const BatchArgs &A, const WinDesc &d, int2 pc, int cm, T W, PmRec<T> &r) {
+    T unused;
+    ld4<T>((const T *)A.Xw + 4 * (int64_t)pc.x, r.X0, r.X1, r.X2, unused);
+    ld_c<T>((const T *)A.Cinv, pc.x, r.c);
+    r.W = W;
+    r.cm = cm;
+    r.key = ((pc.x - d.pt0) << 6) | (pc.y - d.cam0);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_rec(const BatchArgs &A, const WinDesc &d, int o, PmRec<T> &r) {
+    int2 pc;
+    int cm;
+    T W;
+    load_idx<T>(A, o, pc, cm, W);
+    load_pt<T>(A, d, pc, cm, W, r);
 }
 
 // Linearisation over the window's warp chunks: e, Jp and W per observation; per point
@@ -368,7 +402,7 @@ __device__ void lin_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
-    T *pmX = (T *)A.pmX;
+    T *Xw = (T *)A.Xw;
     T *Wpm = (T *)A.Wpm;
     const T delta = (T)A.delta;
     for (int c = d.wch0 + wid; c < d.wch0 + d.nwch; c += NW) {
@@ -405,7 +439,6 @@ __device__ void lin_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc
                 h[6] -= jw[0] * e[0] + jw[3] * e[1];
                 h[7] -= jw[1] * e[0] + jw[4] * e[1];
                 h[8] -= jw[2] * e[0] + jw[5] * e[1];
-                st4<T>(pmX + 4 * (int64_t)o, X0, X1, X2, T(0));
                 if (Wpm) Wpm[o] = W;
             }
         }
@@ -424,39 +457,30 @@ __device__ void lin_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc
             for (int q = 0; q < 6; ++q) A.Hll[6 * (int64_t)pt + q] = (double)h[q];
 #pragma unroll
             for (int q = 0; q < 3; ++q) A.wv[3 * (int64_t)pt + q] = (double)h[6 + q];
+            st4<T>(Xw + 4 * (int64_t)pt, (T)A.pts[3 * (int64_t)pt], (T)A.pts[3 * (int64_t)pt + 1],
+                   (T)A.pts[3 * (int64_t)pt + 2], T(0));
         }
     }
 }
 
-// Right-hand side pass, per observation (no segments): the C~^-1 / W / key
-// record, then s_k = W Jp b_j with b_j = C~_j^-1 wvec_j into camera-major order.
+// Right-hand side pass, per observation (no segments): s_k = W Jp b_j with
+// b_j = C~_j^-1 wvec_j, into camera-major order.
 template <typename T, int NT>
 __device__ void rhs_points(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *wvec) {
     using T2 = typename V2<T>::type;
-    const T *Ci = (const T *)A.Cinv;
-    const T *Wpm = (const T *)A.Wpm;
-    T *pmC = (T *)A.pmC;
     T2 *cms = (T2 *)A.cms;
     for (int k = threadIdx.x; k < d.n; k += NT) {
-        const int o = d.obs0 + k;
-        const int2 pc = __ldg(A.pm_pc + o);
-        const int pt = pc.x, lc = pc.y - d.cam0;
-        T ci[6];
-        ld_c<T>(Ci, pt, ci);
-        const T W = Wpm ? Wpm[o] : T(1);
-        T *rc = pmC + 8 * (int64_t)o;
-        st4<T>(rc, ci[0], ci[1], ci[2], ci[3]);
-        st4<T>(rc + 4, ci[4], ci[5], W, key_bits(T(0), ((pt - d.pt0) << 6) | lc));
-        T X0, X1, X2, unused;
-        ld4<T>((const T *)A.pmX + 4 * (int64_t)o, X0, X1, X2, unused);
+        PmRec<T> r;
+        load_rec<T>(A, d, d.obs0 + k, r);
+        const int pt = d.pt0 + (r.key >> 6);
         ObsJ<T> J;
-        obs_jac<T, false>(M.tabT + lc * kTabS, X0, X1, X2, T(0), T(0), J);
+        obs_jac<T, false>(M.tabT + (r.key & 63) * kTabS, r.X0, r.X1, r.X2, T(0), T(0), J);
         T b[3];
-        sym3_mul<T>(ci, (T)wvec[3 * (int64_t)pt], (T)wvec[3 * (int64_t)pt + 1], (T)wvec[3 * (int64_t)pt + 2], b);
+        sym3_mul<T>(r.c, (T)wvec[3 * (int64_t)pt], (T)wvec[3 * (int64_t)pt + 1], (T)wvec[3 * (int64_t)pt + 2], b);
         T2 sv;
-        sv.x = W * (J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2]);
-        sv.y = W * (J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2]);
-        cms[__ldg(A.pm2cm + o)] = sv;
+        sv.x = r.W * (J.Jp[0] * b[0] + J.Jp[1] * b[1] + J.Jp[2] * b[2]);
+        sv.y = r.W * (J.Jp[3] * b[0] + J.Jp[4] * b[1] + J.Jp[5] * b[2]);
+        cms[r.cm] = sv;
     }
 }
 
@@ -486,22 +510,38 @@ __device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDes
     const int cend = d.wch0 + d.nwch;
     int c = d.wch0 + wid;
     if (c >= cend) return;
+    // three-deep pipeline over the warp's chunks: chunk c computed, chunk c+NW's
+    // per-point gathers and chunk c+2NW's per-observation words in flight,
+    // chunk c+3NW's bounds read
+    auto lane_obs = [&](int2 a0, int2 a1) { return a0.y + ((lane < a1.y - a0.y) ? lane : 0); };
     int2 mc = __ldg(A.wchunk + c), mc1 = __ldg(A.wchunk + c + 1);
     PmRec<T> cur;
-    load_rec<T>(A, mc.y + ((lane < mc1.y - mc.y) ? lane : 0), cur);
-    int2 mn = mc1, mn1 = mc1;
-    if (c + NW < cend) {
+    load_rec<T>(A, d, lane_obs(mc, mc1), cur);
+    bool hn = c + NW < cend, hm = c + 2 * NW < cend;
+    int2 mn = mc1, mn1 = mc1, mm = mc1, mm1 = mc1, pcn = make_int2(0, 0);
+    int cmn = 0;
+    T Wn = T(1);
+    if (hn) {
         mn = __ldg(A.wchunk + c + NW);
         mn1 = __ldg(A.wchunk + c + NW + 1);
+        load_idx<T>(A, lane_obs(mn, mn1), pcn, cmn, Wn);
+    }
+    if (hm) {
+        mm = __ldg(A.wchunk + c + 2 * NW);
+        mm1 = __ldg(A.wchunk + c + 2 * NW + 1);
     }
     for (;;) {
-        const bool more = c + NW < cend;
         PmRec<T> nxt;
-        if (more) load_rec<T>(A, mn.y + ((lane < mn1.y - mn.y) ? lane : 0), nxt);
-        int2 mm = mn1, mm1 = mn1;
-        if (c + 2 * NW < cend) {
-            mm = __ldg(A.wchunk + c + 2 * NW);
-            mm1 = __ldg(A.wchunk + c + 2 * NW + 1);
+        if (hn) load_pt<T>(A, d, pcn, cmn, Wn, nxt);
+        int2 pcm = make_int2(0, 0);
+        int cmm = 0;
+        T Wm = T(1);
+        if (hm) load_idx<T>(A, lane_obs(mm, mm1), pcm, cmm, Wm);
+        const bool hq = c + 3 * NW < cend;
+        int2 mq = mm1, mq1 = mm1;
+        if (hq) {
+            mq = __ldg(A.wchunk + c + 3 * NW);
+            mq1 = __ldg(A.wchunk + c + 3 * NW + 1);
         }
         const int o0 = mc.y, m = mc1.y - mc.y;
         if (m <= 32) {
@@ -533,7 +573,7 @@ __device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDes
             for (int base = 0; base < m; base += 32) {
                 if (base + lane < m) {
                     PmRec<T> r;
-                    load_rec<T>(A, o0 + base + lane, r);
+                    load_rec<T>(A, d, o0 + base + lane, r);
                     ObsJ<T> J;
                     T a0, a1, u[3];
                     rec_u<T>(M, r, J, a0, a1, u);
@@ -544,7 +584,7 @@ __device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDes
             }
             warp_allsum<T, 3>(a);
             PmRec<T> r0;
-            load_rec<T>(A, o0, r0);
+            load_rec<T>(A, d, o0, r0);
 #pragma unroll
             for (int q = 0; q < 6; ++q) cc[q] = r0.c[q];
             T b[3];
@@ -552,7 +592,7 @@ __device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDes
             for (int base = 0; base < m; base += 32) {
                 if (base + lane < m) {
                     PmRec<T> r;
-                    load_rec<T>(A, o0 + base + lane, r);
+                    load_rec<T>(A, d, o0 + base + lane, r);
                     ObsJ<T> J;
                     obs_jac<T, false>(M.tabT + (r.key & 63) * kTabS, r.X0, r.X1, r.X2, T(0), T(0), J);
                     T2 sv;
@@ -562,13 +602,20 @@ __device__ void iter_points(const BatchArgs &A, const WinMem<T> &M, const WinDes
                 }
             }
         }
-        if (!more) break;
+        if (!hn) break;
         c += NW;
+        cur = nxt;
         mc = mn;
         mc1 = mn1;
         mn = mm;
         mn1 = mm1;
-        cur = nxt;
+        pcn = pcm;
+        cmn = cmm;
+        Wn = Wm;
+        hn = hm;
+        mm = mq;
+        mm1 = mq1;
+        hm = hq;
     }
 }
 
@@ -594,7 +641,7 @@ __device__ double back_points(const BatchArgs &A, const WinMem<T> &M, const WinD
         ObsJ<T> J;
         for (int base = 0; base < m; base += 32) {
             const bool act = base + lane < m;
-            load_rec<T>(A, o0 + base + (act ? lane : 0), r);
+            load_rec<T>(A, d, o0 + base + (act ? lane : 0), r);
             T uu[3];
             rec_u<T>(M, r, J, a0, a1, uu);
             if (act) {
@@ -639,7 +686,7 @@ __device__ double back_points(const BatchArgs &A, const WinMem<T> &M, const WinD
             const bool act = base + lane < m;
             const int o = o0 + base + (act ? lane : 0);
             if (m > 32) {
-                load_rec<T>(A, o, r);
+                load_rec<T>(A, d, o, r);
                 T uu[3];
                 rec_u<T>(M, r, J, a0, a1, uu);
             }
@@ -669,7 +716,7 @@ __device__ double back_points(const BatchArgs &A, const WinMem<T> &M, const WinD
 // entries of B = sum W Jc^T Jc and v = -sum W Jc^T e (54 per slot);
 // otherwise sum Jc^T s (9 per slot).
 template <typename T, int NT, bool LIN>
-__device__ void camera_pass(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+__device__ void camera_pass(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, bool wj = false) {
     using T2 = typename V2<T>::type;
     constexpr int NW = NT / 32;
     constexpr int K = LIN ? 54 : 9;
@@ -687,21 +734,26 @@ __device__ void camera_pass(const BatchArgs &A, const WinMem<T> &M, const WinDes
         T acc[K];
 #pragma unroll
         for (int q = 0; q < K; ++q) acc[q] = T(0);
-#pragma unroll 2
-        for (int c = beg + lane; c < end; c += 32) {
-            const int gc = d.obs0 + c;
-            T X0, X1, X2;
-            if (LIN) {
+        if (LIN) {
+            for (int c = beg + lane; c < end; c += 32) {
+                const int gc = d.obs0 + c;
                 const int pt = __ldg(A.cm_pt + gc), pm = __ldg(A.cm2pm + gc);
-                X0 = (T)A.pts[3 * (int64_t)pt];
-                X1 = (T)A.pts[3 * (int64_t)pt + 1];
-                X2 = (T)A.pts[3 * (int64_t)pt + 2];
+                const T X0 = (T)A.pts[3 * (int64_t)pt], X1 = (T)A.pts[3 * (int64_t)pt + 1],
+                        X2 = (T)A.pts[3 * (int64_t)pt + 2];
                 st4<T>(cmX + 4 * (int64_t)gc, X0, X1, X2, T(0));
                 const double2 uv = __ldg(A.pm_uv + pm);
                 T e[2], Jc[18], Jp[6];
                 project<T, true>(ct, X0, X1, X2, (T)uv.x, (T)uv.y, e, Jc, Jp);
                 T rho, W;
                 loss_weight<T>(A.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+                if (wj) {
+                    const T sw = sqrt(W);
+                    T *jo = (T *)A.Jcm + 24 * (int64_t)gc;
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) st4<T>(jo + q, sw * Jc[q], sw * Jc[q + 1], sw * Jc[q + 2], sw * Jc[q + 3]);
+                    st4<T>(jo + 16, sw * Jc[16], sw * Jc[17], sw * Jp[0], sw * Jp[1]);
+                    st4<T>(jo + 20, sw * Jp[2], sw * Jp[3], sw * Jp[4], sw * Jp[5]);
+                }
                 int idx = 0;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
@@ -710,14 +762,29 @@ __device__ void camera_pass(const BatchArgs &A, const WinMem<T> &M, const WinDes
                     for (int b = a; b < 9; ++b) acc[idx++] += w0 * Jc[b] + w1 * Jc[9 + b];
                     acc[45 + a] -= w0 * e[0] + w1 * e[1];
                 }
-            } else {
-                T unused;
-                ld4<T>(cmX + 4 * (int64_t)gc, X0, X1, X2, unused);
-                const T2 sv = cms[gc];
+            }
+        } else {
+            // the next step's X and s are loaded before the current step is computed
+            int c = beg + lane;
+            T X0 = T(0), X1 = T(0), X2 = T(0), unused;
+            T2 sv;
+            sv.x = T(0);
+            sv.y = T(0);
+            if (c < end) {
+                ld4<T>(cmX + 4 * (int64_t)(d.obs0 + c), X0, X1, X2, unused);
+                sv = cms[d.obs0 + c];
+            }
+            for (; c < end; c += 32) {
+                const T x0 = X0, x1 = X1, x2 = X2;
+                const T2 s_ = sv;
+                if (c + 32 < end) {
+                    ld4<T>(cmX + 4 * (int64_t)(d.obs0 + c + 32), X0, X1, X2, unused);
+                    sv = cms[d.obs0 + c + 32];
+                }
                 T y[9];
-                jct_apply<T>(ct, X0, X1, X2, sv.x, sv.y, y);
+                jct_apply<T>(ct, x0, x1, x2, s_.x, s_.y, y);
 #pragma unroll
-                for (int q = 0; q < 9; ++q) acc[q] += y[q];
+                for (int q = 0; q < K; ++q) acc[q] += y[q];
             }
         }
         warp_allsum<T, K>(acc);
@@ -773,7 +840,7 @@ __device__ __forceinline__ double2 precond(const WinMem<T> &M, int nc) {
 }
 
 template <typename T, int NT>
-__device__ void linearize(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+__device__ void linearize(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, bool xs) {
     for (int t = threadIdx.x; t < d.nc * kCamTab; t += NT) {
         const int i = t / kCamTab, q = t - kCamTab * (t / kCamTab);
         M.tabT[i * kTabS + q] = (T)M.tab64[t];
@@ -781,7 +848,7 @@ __device__ void linearize(const BatchArgs &A, const WinMem<T> &M, const WinDesc 
     __syncthreads();
     lin_points<T, NT>(A, M, d);
     __syncthreads();
-    camera_pass<T, NT, true>(A, M, d);
+    camera_pass<T, NT, true>(A, M, d, xs);
     __syncthreads();
     for (int t = threadIdx.x; t < d.nc * 54; t += NT) {
         const int i = t / 54, q = t - 54 * (t / 54);
@@ -858,11 +925,125 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Explicit reduced camera matrix S~ = B~ - E C~^-1 E^T (Sec. 3 Eq. 3) of one
+// window, formed once per damped solve.  Block (i, k), i <= k, is
+//   B~_i [i = k] - sum over points j seen by both of Jc~_ij^T G Jc~_kj,
+//   G = Jp~_ij C~_j^-1 Jp~_kj^T (2x2),
+// accumulated in the order of the block's pair list (one warp per block, no
+// shared accumulators).  S~ p is then the same product as the implicit form of
+// Alg. 3, with the point side folded in once instead of per iteration.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int blk_index(int i, int k, int nc) { return i * nc - (i * (i - 1)) / 2 + (k - i); }
+
+template <typename T, int NT>
+__device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, double mu, int damping) {
+    constexpr int NW = NT / 32;
+    constexpr int SP = Stage<T>::pairs, SS = Stage<T>::stride;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nc = d.nc, nb = nc * (nc + 1) / 2;
+    T *S = (T *)A.S + A.smax * (int64_t)blockIdx.x;
+    T *st = M.stage + wid * SP * SS;
+    const T *Jcm = (const T *)A.Jcm;
+    const T *Ci = (const T *)A.Cinv;
+    const int a = lane / 3, b0 = 3 * (lane - 3 * (lane / 3));
+    int bi = 0, bk = 0, bcur = 0;  // (i, k) of block bcur, advanced incrementally
+    for (int blk = wid; blk < nb; blk += NW) {
+        while (bcur < blk) {
+            ++bk;
+            if (bk == nc) {
+                ++bi;
+                bk = bi;
+            }
+            ++bcur;
+        }
+        const int p0 = __ldg(A.blk_ptr + d.blk0 + blk), p1 = __ldg(A.blk_ptr + d.blk0 + blk + 1);
+        T acc[3] = {T(0), T(0), T(0)};
+        for (int base = p0; base < p1; base += SP) {
+            const int cnt = min(SP, p1 - base);
+            if (lane < cnt) {
+                const int2 pr = __ldg(A.pairs + base + lane);
+                const T *J1 = Jcm + 24 * (int64_t)pr.x, *J2 = Jcm + 24 * (int64_t)pr.y;
+                T c[6];
+                ld_c<T>(Ci, __ldg(A.cm_pt + pr.x), c);
+                T q0[3], q1[3];  // Q = Jp~_1 C~^-1 (2x3)
+                sym3_mul<T>(c, J1[18], J1[19], J1[20], q0);
+                sym3_mul<T>(c, J1[21], J1[22], J1[23], q1);
+                const T g00 = q0[0] * J2[18] + q0[1] * J2[19] + q0[2] * J2[20];
+                const T g01 = q0[0] * J2[21] + q0[1] * J2[22] + q0[2] * J2[23];
+                const T g10 = q1[0] * J2[18] + q1[1] * J2[19] + q1[2] * J2[20];
+                const T g11 = q1[0] * J2[21] + q1[1] * J2[22] + q1[2] * J2[23];
+                T *sp = st + lane * SS;
+#pragma unroll
+                for (int b = 0; b < 9; ++b) {
+                    const T x0 = J2[b], x1 = J2[9 + b];
+                    sp[b] = J1[b];
+                    sp[9 + b] = J1[9 + b];
+                    sp[18 + b] = g00 * x0 + g01 * x1;
+                    sp[27 + b] = g10 * x0 + g11 * x1;
+                }
+            }
+            __syncwarp();
+            if (lane < 27)
+                for (int p = 0; p < cnt; ++p) {
+                    const T *sp = st + p * SS;
+                    const T j0 = sp[a], j1 = sp[9 + a];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) acc[cc] += j0 * sp[18 + b0 + cc] + j1 * sp[27 + b0 + cc];
+                }
+            __syncwarp();
+        }
+        if (lane < 27) {
+            T *Sb = S + 81 * (int64_t)blk + 9 * a + b0;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                double v = -(double)acc[cc];
+                if (bi == bk) {
+                    const double *Hi = M.Hpp + 45 * bi;
+                    v += Hi[sym9(a, b0 + cc)];
+                    if (a == b0 + cc) v += mu * damp_term_b(damping, Hi[sym9(a, a)]);
+                }
+                Sb[cc] = (T)v;
+            }
+        }
+    }
+}
+
+// q = S~ p (p given in M.pv as T); returns this thread's share of p.q.
+template <typename T, int NT>
+__device__ double s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    const int nc = d.nc;
+    const T *S = (const T *)A.S + A.smax * (int64_t)blockIdx.x;
+    const T *pT = M.pv;
+    double pq = 0.0;
+    for (int r = threadIdx.x; r < 9 * nc; r += NT) {
+        const int i = r / 9, a = r - 9 * (r / 9);
+        T acc = T(0);
+        for (int k = 0; k < i; ++k) {  // column a of block (k, i)
+            const T *Sb = S + 81 * (int64_t)blk_index(k, i, nc) + a;
+            const T *pk = pT + 9 * k;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) acc += Sb[9 * b] * pk[b];
+        }
+        for (int k = i; k < nc; ++k) {  // row a of block (i, k)
+            const T *Sb = S + 81 * (int64_t)blk_index(i, k, nc) + 9 * a;
+            const T *pk = pT + 9 * k;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) acc += Sb[b] * pk[b];
+        }
+        const double q = (double)acc;
+        M.q[r] = q;
+        pq = fma(M.p[r], q, pq);
+    }
+    return pq;
+}
+
 // PCG of Alg. 2 on S x = g, g = vvec - E C~^-1 wvec (Sec. 3 Eq. 3), x0 = 0;
-// leaves x in M.x and returns the iteration count.
+// leaves x in M.x and returns the iteration count.  The product S p is the
+// implicit two-pass form of Alg. 3, or the explicit S~ of s_build.
 template <typename T, int NT>
 __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *vvec, const double *wvec,
-                   double mu, int damping, int max_iter, double tol) {
+                   double mu, int damping, int max_iter, double tol, bool xs) {
     const int m9 = 9 * d.nc;
     rhs_points<T, NT>(A, M, d, wvec);
     __syncthreads();
@@ -883,6 +1064,16 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
         for (;;) {
             if (!isfinite(rho)) break;
             const double beta = n == 0 ? 0.0 : rho / rho_prev;
+            double pq = 0.0;
+            if (xs) {
+                for (int t = threadIdx.x; t < m9; t += NT) {
+                    const double pn = n == 0 ? M.z[t] : fma(beta, M.p[t], M.z[t]);
+                    M.p[t] = pn;
+                    M.pv[t] = (T)pn;
+                }
+                __syncthreads();
+                pq = s_matvec<T, NT>(A, M, d);
+            } else {
             for (int t = threadIdx.x; t < m9; t += NT) M.p[t] = n == 0 ? M.z[t] : fma(beta, M.p[t], M.z[t]);
             __syncthreads();
             make_pv<T, NT>(M, M.p, d.nc);
@@ -891,7 +1082,6 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
             __syncthreads();
             camera_pass<T, NT, false>(A, M, d);
             __syncthreads();
-            double pq = 0.0;
             for (int t = threadIdx.x; t < m9; t += NT) {
                 const int i = t / 9, a = t - 9 * (t / 9);
                 const double *Hi = M.Hpp + 45 * i;
@@ -903,6 +1093,7 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
                 const double q = bp - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
                 M.q[t] = q;
                 pq = fma(M.p[t], q, pq);
+            }
             }
             pq = cta_sum2<NT>(pq, 0.0, M.sb).x;
             if (!(pq > 0.0) || !isfinite(pq)) break;
@@ -1008,14 +1199,19 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
     for (int it = 0; it < O.max_iter; ++it) {
         if (S.done) break;
         if (S.relin) {
-            linearize<T, NT>(A, M, d);
+            linearize<T, NT>(A, M, d, O.explicit_schur != 0);
             if (tid == 0) S.relin = 0;
         }
         const double mu = 1.0 / S.radius;
         damp<T, NT>(A, M, S, d, mu, O.damping);
         __syncthreads();
         if (S.status != MBA_OK) break;
-        const int np_ = pcg<T, NT>(A, M, d, M.v, A.wv, mu, O.damping, O.pcg_max_iter, O.pcg_tol);
+        if (O.explicit_schur) {
+            s_build<T, NT>(A, M, d, mu, O.damping);
+            __syncthreads();
+        }
+        const int np_ = pcg<T, NT>(A, M, d, M.v, A.wv, mu, O.damping, O.pcg_max_iter, O.pcg_tol,
+                                   O.explicit_schur != 0);
         make_pv<T, NT>(M, M.x, d.nc);
         __syncthreads();
         double ld = back_points<T, NT>(A, M, d, A.wv, false);
@@ -1065,15 +1261,19 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
             tables64<T, NT>(M, M.cams, d.nc);
             __syncthreads();
             if (S.relin) {
-                linearize<T, NT>(A, M, d);
+                linearize<T, NT>(A, M, d, O.explicit_schur != 0);
                 if (tid == 0) S.relin = 0;
             }
             const double mu = O.adj_mu >= 0.0 ? O.adj_mu : S.mu_acc;
             damp<T, NT>(A, M, S, d, mu, O.damping);
             __syncthreads();
             if (S.status == MBA_OK) {
+                if (O.explicit_schur) {
+                    s_build<T, NT>(A, M, d, mu, O.damping);
+                    __syncthreads();
+                }
                 const int na = pcg<T, NT>(A, M, d, A.gbar_c + 9 * (int64_t)d.cam0, A.gbar_p, mu, O.damping,
-                                          O.adj_pcg_max, O.adj_pcg_tol);
+                                          O.adj_pcg_max, O.adj_pcg_tol, O.explicit_schur != 0);
                 make_pv<T, NT>(M, M.x, d.nc);
                 __syncthreads();
                 back_points<T, NT>(A, M, d, A.gbar_p, true);
@@ -1131,8 +1331,8 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
     __syncthreads();
 }
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) batch_kernel(BatchArgs A) {
+template <typename T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WinState S;
     WinMem<T> M;
@@ -1154,9 +1354,16 @@ size_t smem_bytes(int ncmax) {
     return win_carve<T>(nullptr, ncmax, NT / 32, m);
 }
 
-const void *kernel_ptr(bool fp32, int nt) {
-    if (fp32) return nt == 256 ? (const void *)batch_kernel<float, 256> : (const void *)batch_kernel<float, 512>;
-    return nt == 256 ? (const void *)batch_kernel<double, 256> : (const void *)batch_kernel<double, 512>;
+// Instances: (threads per CTA, CTAs per SM the register budget is cut for).
+// 256 threads: up to 2 resident CTAs (<= 128 registers) or 3 (<= 85);
+// 512 threads: 1 (<= 128).
+const void *kernel_ptr(bool fp32, int nt, int cps) {
+    if (fp32) {
+        if (nt == 512) return (const void *)batch_kernel<float, 512, 1>;
+        return cps >= 3 ? (const void *)batch_kernel<float, 256, 3> : (const void *)batch_kernel<float, 256, 2>;
+    }
+    if (nt == 512) return (const void *)batch_kernel<double, 512, 1>;
+    return cps >= 3 ? (const void *)batch_kernel<double, 256, 3> : (const void *)batch_kernel<double, 256, 2>;
 }
 
 size_t kernel_smem(bool fp32, int nt, int ncmax) {
@@ -1187,14 +1394,18 @@ struct mba_batch {
     mba_window_summary *out = nullptr;
     double *cams0 = nullptr, *pts0 = nullptr, *cams_bak = nullptr, *pts_bak = nullptr;
     double *gbar_c = nullptr, *gbar_p = nullptr;
+    bool explicit_ok = false;       // pair lists and S~ scratch exist
+    int schur = 0;                  // schedule: 1 implicit, 2 explicit Schur product
     int sms = 0;
     int nt = 0, cps = 0;            // schedule in use
     cudaGraphExec_t gexec = nullptr;
-    int g_nt = 0, g_grid = 0;       // schedule the graph was captured with
+    int g_nt = 0, g_grid = 0, g_cps = 0;  // schedule the graph was captured with
     bool has_grads = false;
 };
 
 namespace {
+
+constexpr int kMaxCtasPerSm = 4;  // S~ scratch is sized for this many resident CTAs per SM
 
 #define BCK(call)                                                                              \
     do {                                                                                       \
@@ -1202,8 +1413,9 @@ namespace {
         if (e_ != cudaSuccess) return api_fail(MBA_ERR_CUDA, (std::string(#call) + ": " + cudaGetErrorString(e_)).c_str()); \
     } while (0)
 
-int max_ctas_per_sm(const mba_batch *b, int nt) {
-    const void *k = kernel_ptr(b->fp32, nt);
+// Resident CTAs per SM of the kernel instance used for (nt, cps).
+int max_ctas_per_sm(const mba_batch *b, int nt, int cps) {
+    const void *k = kernel_ptr(b->fp32, nt, cps);
     const size_t sm = kernel_smem(b->fp32, nt, b->ncmax);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int blocks = 0;
@@ -1212,14 +1424,20 @@ int max_ctas_per_sm(const mba_batch *b, int nt) {
 }
 
 // Resolves a requested schedule to an admissible one (0 fields: automatic).
-mba_status resolve_schedule(const mba_batch *b, int want_nt, int want_cps, int *nt, int *cps) {
+mba_status resolve_schedule(const mba_batch *b, int want_nt, int want_cps, int want_schur, int *nt, int *cps,
+                            int *schur) {
     if (want_nt != 0 && want_nt != 256 && want_nt != 512)
         return api_fail(MBA_ERR_INVALID_ARG, "threads_per_cta must be 0, 256 or 512");
-    if (want_cps < 0 || want_cps > 8) return api_fail(MBA_ERR_INVALID_ARG, "ctas_per_sm must be in 0..8");
+    if (want_cps < 0 || want_cps > kMaxCtasPerSm) return api_fail(MBA_ERR_INVALID_ARG, "ctas_per_sm must be in 0..4");
+    if (want_schur < 0 || want_schur > 2) return api_fail(MBA_ERR_INVALID_ARG, "schur must be 0, 1 or 2");
+    if (want_schur == 2 && !b->explicit_ok)
+        return api_fail(MBA_ERR_INVALID_ARG, "the explicit Schur product is not available for this batch");
+    *schur = want_schur ? want_schur : (b->explicit_ok ? 2 : 1);
     const int t = want_nt ? want_nt : 256;
-    const int occ = max_ctas_per_sm(b, t);
+    const int want = want_cps ? want_cps : 2;
+    const int occ = max_ctas_per_sm(b, t, want);
     if (occ < 1) return api_fail(MBA_ERR_INVALID_ARG, "the batched kernel cannot be resident with this schedule");
-    int c = want_cps ? want_cps : occ;
+    int c = want;
     if (c > occ) c = occ;
     *nt = t;
     *cps = c;
@@ -1229,12 +1447,12 @@ mba_status resolve_schedule(const mba_batch *b, int want_nt, int want_cps, int *
 mba_status build_graph(mba_batch *b) {
     const int grid_full = b->sms * b->cps;
     const int grid = grid_full < b->nw ? grid_full : b->nw;
-    if (b->gexec && b->g_nt == b->nt && b->g_grid == grid) return MBA_OK;
+    if (b->gexec && b->g_nt == b->nt && b->g_grid == grid && b->g_cps == b->cps) return MBA_OK;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
-    const void *k = kernel_ptr(b->fp32, b->nt);
+    const void *k = kernel_ptr(b->fp32, b->nt, b->cps);
     const size_t sm = kernel_smem(b->fp32, b->nt, b->ncmax);
     BCK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     cudaGraph_t g = nullptr;
@@ -1257,6 +1475,7 @@ mba_status build_graph(mba_batch *b) {
     }
     b->g_nt = b->nt;
     b->g_grid = grid;
+    b->g_cps = b->cps;
     return MBA_OK;
 }
 
@@ -1379,6 +1598,60 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
             return api_fail(MBA_ERR_INVALID_ARG, "too many warp chunks");
     }
     cam_ptr[(size_t)NC] = (int32_t)N;
+    // Schur-block pair lists (explicit S~): for each point, every ordered pair
+    // (u, v) of its observations with camera(u) < camera(v), or with the same
+    // camera (all ordered pairs), goes to the list of block (camera(u),
+    // camera(v)); lists are in point order.  Skipped (explicit form not
+    // offered) when they would be too large.
+    std::vector<int2> pairs;
+    std::vector<int32_t> blk_ptr;
+    bool explicit_ok = true;
+    {
+        int64_t total = 0;
+        for (int w = 0; w < nw && explicit_ok; ++w) {
+            const WinDesc &d = desc[w];
+            for (int32_t o = d.obs0; o < d.obs0 + d.n;) {
+                int32_t e = o;
+                while (e < d.obs0 + d.n && pm_pc[e].x == pm_pc[o].x) ++e;
+                for (int32_t u = o; u < e; ++u)
+                    for (int32_t v = o; v < e; ++v)
+                        if (pm_pc[u].y <= pm_pc[v].y) ++total;
+                o = e;
+            }
+            if (total > (int64_t(1) << 28)) explicit_ok = false;
+        }
+        if (explicit_ok) {
+            pairs.resize((size_t)total);
+            std::vector<int32_t> bcnt;
+            int64_t base = 0;
+            for (int w = 0; w < nw; ++w) {
+                WinDesc &d = desc[w];
+                const int32_t nb = d.nc * (d.nc + 1) / 2;
+                auto blk = [&](int32_t i, int32_t k) { return i * d.nc - (i * (i - 1)) / 2 + (k - i); };
+                bcnt.assign((size_t)nb + 1, 0);
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int32_t o = d.obs0; o < d.obs0 + d.n;) {
+                        int32_t e = o;
+                        while (e < d.obs0 + d.n && pm_pc[e].x == pm_pc[o].x) ++e;
+                        for (int32_t u = o; u < e; ++u)
+                            for (int32_t v = o; v < e; ++v) {
+                                const int32_t cu = pm_pc[u].y - d.cam0, cv = pm_pc[v].y - d.cam0;
+                                if (cu > cv) continue;
+                                if (pass == 0) ++bcnt[blk(cu, cv) + 1];
+                                else pairs[(size_t)(base + bcnt[blk(cu, cv)]++)] = make_int2(pm2cm[u], pm2cm[v]);
+                            }
+                        o = e;
+                    }
+                    if (pass == 0) {
+                        for (int32_t q = 0; q < nb; ++q) bcnt[q + 1] += bcnt[q];
+                        d.blk0 = (int32_t)blk_ptr.size();
+                        for (int32_t q = 0; q <= nb; ++q) blk_ptr.push_back((int32_t)(base + bcnt[q]));
+                    }
+                }
+                base = blk_ptr.back();
+            }
+        }
+    }
     std::vector<int32_t> order((size_t)nw);
     for (int w = 0; w < nw; ++w) order[w] = w;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return desc[a].n > desc[b].n; });
@@ -1393,6 +1666,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     b->fp32 = o.precision == MBA_FP32_MIXED;
     b->loss = o.loss;
     b->delta = o.huber_delta;
+    b->explicit_ok = explicit_ok;
     auto fail_free = [&](mba_status st, const std::string &msg) {
         mba_batch_destroy(b);
         return api_fail(st, msg.c_str());
@@ -1424,11 +1698,16 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                  o_camsb = take(72 * (size_t)NC), o_pts = take(24 * (size_t)NP), o_pts0 = take(24 * (size_t)NP),
                  o_ptsb = take(24 * (size_t)NP), o_ptsn = take(24 * (size_t)NP), o_dp = take(24 * (size_t)NP),
                  o_hll = take(48 * (size_t)NP), o_wv = take(24 * (size_t)NP), o_pm2cm = take(4 * (size_t)N),
-                 o_ci = take(6 * w * (size_t)NP), o_pmx = take(4 * w * (size_t)N), o_pmc = take(8 * w * (size_t)N),
+                 o_ci = take(6 * w * (size_t)NP), o_xw = take(4 * w * (size_t)NP),
                  o_cmx = take(4 * w * (size_t)N), o_cms = take(2 * w * (size_t)N),
                  o_W = o.loss != MBA_LOSS_NONE ? take(w * (size_t)N) : 0, o_gc = take(72 * (size_t)NC),
                  o_gp = take(24 * (size_t)NP), o_go = take(16 * (size_t)N), o_g0c = take(72 * (size_t)NC),
                  o_g0p = take(24 * (size_t)NP);
+    const int64_t smax = (int64_t)ncmax * (ncmax + 1) / 2 * 81;
+    const size_t o_pairs = explicit_ok ? take(sizeof(int2) * pairs.size()) : 0,
+                 o_bptr = explicit_ok ? take(4 * blk_ptr.size()) : 0,
+                 o_jcm = explicit_ok ? take(24 * w * (size_t)N) : 0,
+                 o_S = explicit_ok ? take(w * (size_t)smax * (size_t)b->sms * kMaxCtasPerSm) : 0;
     if (cudaMalloc(&b->pool, off) != cudaSuccess) {
         cudaGetLastError();
         return fail_free(MBA_ERR_OOM, "device allocation of the batch failed");
@@ -1469,8 +1748,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     A.wv = (double *)(base + o_wv);
     A.pm2cm = (const int32_t *)(base + o_pm2cm);
     A.Cinv = base + o_ci;
-    A.pmX = base + o_pmx;
-    A.pmC = base + o_pmc;
+    A.Xw = base + o_xw;
     A.cmX = base + o_cmx;
     A.cms = base + o_cms;
     A.Wpm = o.loss != MBA_LOSS_NONE ? (void *)(base + o_W) : nullptr;
@@ -1480,6 +1758,13 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     A.grad_c0 = (double *)(base + o_g0c);
     A.grad_p0 = (double *)(base + o_g0p);
     A.out = b->out;
+    if (explicit_ok) {
+        A.pairs = (const int2 *)(base + o_pairs);
+        A.blk_ptr = (const int32_t *)(base + o_bptr);
+        A.Jcm = base + o_jcm;
+        A.S = base + o_S;
+        A.smax = smax;
+    }
     cudaStream_t s = b->stream;
     auto up = [&](void *dst, const void *src, size_t bytes) { return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s); };
     cudaError_t e = cudaSuccess;
@@ -1493,6 +1778,8 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     if (e == cudaSuccess) e = up((void *)A.cm2pm, cm2pm.data(), 4 * (size_t)N);
     if (e == cudaSuccess) e = up((void *)A.pm2cm, pm2cm.data(), 4 * (size_t)N);
     if (e == cudaSuccess) e = up((void *)A.cam_ptr, cam_ptr.data(), 4 * ((size_t)NC + 1));
+    if (e == cudaSuccess && explicit_ok) e = up((void *)A.pairs, pairs.data(), sizeof(int2) * pairs.size());
+    if (e == cudaSuccess && explicit_ok) e = up((void *)A.blk_ptr, blk_ptr.data(), 4 * blk_ptr.size());
     if (e == cudaSuccess) e = up(A.cams, cameras, 72 * (size_t)NC);
     if (e == cudaSuccess) e = up(b->cams0, cameras, 72 * (size_t)NC);
     if (e == cudaSuccess) e = up(A.pts, points, 24 * (size_t)NP);
@@ -1502,7 +1789,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_p0, 0, 24 * (size_t)NP, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-    mba_status st = resolve_schedule(b, 0, 0, &b->nt, &b->cps);
+    mba_status st = resolve_schedule(b, 0, 0, 0, &b->nt, &b->cps, &b->schur);
     if (st != MBA_OK) {
         std::string msg = mba_last_error();
         mba_batch_destroy(b);
@@ -1534,11 +1821,12 @@ mba_status mba_batch_info(const mba_batch *b, int32_t *n_windows, int64_t *n_cam
 
 mba_status mba_batch_set_schedule(mba_batch *b, const mba_batch_schedule *sc) {
     if (!b || !sc) return api_fail(MBA_ERR_INVALID_ARG, "NULL argument");
-    int nt = 0, cps = 0;
-    mba_status st = resolve_schedule(b, sc->threads_per_cta, sc->ctas_per_sm, &nt, &cps);
+    int nt = 0, cps = 0, schur = 0;
+    mba_status st = resolve_schedule(b, sc->threads_per_cta, sc->ctas_per_sm, sc->schur, &nt, &cps, &schur);
     if (st != MBA_OK) return st;
     b->nt = nt;
     b->cps = cps;
+    b->schur = schur;
     return MBA_OK;
 }
 
@@ -1546,6 +1834,7 @@ mba_status mba_batch_get_schedule(const mba_batch *b, mba_batch_schedule *sc) {
     if (!b || !sc) return api_fail(MBA_ERR_INVALID_ARG, "NULL argument");
     sc->threads_per_cta = b->nt;
     sc->ctas_per_sm = b->cps;
+    sc->schur = b->schur;
     return MBA_OK;
 }
 
@@ -1573,6 +1862,7 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
     bo.function_tol = o.function_tol;
     bo.adj_pcg_tol = adj ? adj->pcg_rel_tol : 0.0;
     bo.adj_mu = adj ? adj->mu : -1.0;
+    bo.explicit_schur = b->schur == 2 ? 1 : 0;
     BCK(cudaMemcpyAsync(b->opts, &bo, sizeof(bo), cudaMemcpyHostToDevice, s));
     if (adj) {
         BCK(cudaMemcpyAsync(b->gbar_c, adj->grad_cameras, 72 * (size_t)b->nc, cudaMemcpyHostToDevice, s));
@@ -1615,15 +1905,17 @@ mba_status mba_batch_autotune(mba_batch *b, const mba_solver_options *opt, mba_b
     cudaStream_t s = b->stream;
     BCK(cudaMemcpyAsync(b->cams_bak, b->A.cams, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, s));
     BCK(cudaMemcpyAsync(b->pts_bak, b->A.pts, 24 * (size_t)b->np, cudaMemcpyDeviceToDevice, s));
-    const int nt0 = b->nt, cps0 = b->cps;
+    const int nt0 = b->nt, cps0 = b->cps, sc0 = b->schur;
     double best = -1.0;
-    int bnt = nt0, bcps = cps0;
+    int bnt = nt0, bcps = cps0, bsc = sc0;
     const int nts[2] = {256, 512};
+    for (int sch = b->explicit_ok ? 2 : 1; sch >= 1; --sch)
     for (int a = 0; a < 2; ++a) {
-        const int occ = max_ctas_per_sm(b, nts[a]);
-        for (int c = 1; c <= occ && c <= 8; ++c) {
+        for (int c = 1; c <= kMaxCtasPerSm; ++c) {
+            if (max_ctas_per_sm(b, nts[a], c) < c) break;
             b->nt = nts[a];
             b->cps = c;
+            b->schur = sch;
             double t = 0.0;
             mba_status st = mba_batch_solve(b, opt, nullptr, nullptr, &t);
             BCK(cudaMemcpyAsync(b->A.cams, b->cams_bak, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, s));
@@ -1632,20 +1924,24 @@ mba_status mba_batch_autotune(mba_batch *b, const mba_solver_options *opt, mba_b
             if (st != MBA_OK && st != MBA_ERR_NONFINITE) {
                 b->nt = nt0;
                 b->cps = cps0;
+                b->schur = sc0;
                 return st;
             }
             if (best < 0.0 || t < best) {
                 best = t;
                 bnt = nts[a];
                 bcps = c;
+                bsc = sch;
             }
         }
     }
     b->nt = bnt;
     b->cps = bcps;
+    b->schur = bsc;
     if (chosen) {
         chosen->threads_per_cta = bnt;
         chosen->ctas_per_sm = bcps;
+        chosen->schur = bsc;
     }
     if (ms_best) *ms_best = best;
     return MBA_OK;

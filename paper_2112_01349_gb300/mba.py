@@ -66,7 +66,7 @@ class WindowSummary(C.Structure):
 
 
 class BatchSchedule(C.Structure):
-    _fields_ = [("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+    _fields_ = [("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("schur", C.c_int32)]
 
 
 class BatchAdjoint(C.Structure):
@@ -443,15 +443,19 @@ def mba_batch_info(h):
     return dict(n_windows=nw.value, nc=nc.value, np=np_.value, n=n.value, max_window_cameras=mc.value)
 
 
-def mba_batch_set_schedule(h, threads_per_cta=0, ctas_per_sm=0):
-    sc = BatchSchedule(int(threads_per_cta), int(ctas_per_sm))
+SCHUR = {"auto": 0, "implicit": 1, "explicit": 2}
+
+
+def mba_batch_set_schedule(h, threads_per_cta=0, ctas_per_sm=0, schur="auto"):
+    sc = BatchSchedule(int(threads_per_cta), int(ctas_per_sm), SCHUR[schur] if isinstance(schur, str) else int(schur))
     _check(load().mba_batch_set_schedule(h, C.byref(sc)))
 
 
 def mba_batch_get_schedule(h):
     sc = BatchSchedule()
     _check(load().mba_batch_get_schedule(h, C.byref(sc)))
-    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm)
+    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm,
+                schur={1: "implicit", 2: "explicit"}.get(sc.schur, "auto"))
 
 
 def mba_batch_autotune(h, **opts):
@@ -459,7 +463,8 @@ def mba_batch_autotune(h, **opts):
     sc = BatchSchedule()
     ms = C.c_double()
     _check(load().mba_batch_autotune(h, C.byref(o), C.byref(sc), C.byref(ms)))
-    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm, ms=ms.value)
+    return dict(threads_per_cta=sc.threads_per_cta, ctas_per_sm=sc.ctas_per_sm,
+                schur={1: "implicit", 2: "explicit"}.get(sc.schur, "auto"), ms=ms.value)
 
 
 def _summaries(arr):
@@ -561,8 +566,8 @@ class Batch:
     def autotune(self, **opts):
         return mba_batch_autotune(self.handle, **opts)
 
-    def set_schedule(self, threads_per_cta=0, ctas_per_sm=0):
-        mba_batch_set_schedule(self.handle, threads_per_cta, ctas_per_sm)
+    def set_schedule(self, threads_per_cta=0, ctas_per_sm=0, schur="auto"):
+        mba_batch_set_schedule(self.handle, threads_per_cta, ctas_per_sm, schur)
 
     def schedule(self):
         return mba_batch_get_schedule(self.handle)

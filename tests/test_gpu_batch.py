@@ -36,10 +36,13 @@ def _oracle_solve(s, loss="none", delta=0.0, **kw):
     return oracle.lm_solve(s.cameras, s.points, s.observations, s.cam_idx, s.pt_idx, loss=loss, delta=delta, **o)
 
 
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
-def test_windows_match_oracle(mba, precision, tol):
+def test_windows_match_oracle(mba, precision, tol, schur):
     ws = _small()
     with mba.Batch(_tuples(ws), precision=precision) as b:
+        b.set_schedule(schur=schur)
+        assert b.schedule()["schur"] == schur
         r = b.solve(**OPTS)
         for w, s in enumerate(ws):
             ref = _oracle_solve(s)
@@ -55,22 +58,27 @@ def test_windows_match_oracle(mba, precision, tol):
             assert sm["final_cost"] < sm["initial_cost"]
 
 
-def test_windows_huber_match_oracle(mba):
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
+def test_windows_huber_match_oracle(mba, schur):
     ws = [make_scene(int(nc), int(npt), track=("geom", 1.0 / 3.0), sigma=1.0, outlier_frac=0.05, seed=100 + i)
           for i, (nc, npt) in enumerate([(6, 120), (9, 250), (14, 400), (5, 60)])]
     with mba.Batch(_tuples(ws), precision="fp64", loss="huber", huber_delta=2.0) as b:
+        b.set_schedule(schur=schur)
         r = b.solve(**OPTS)
     for w, s in enumerate(ws):
         ref = _oracle_solve(s, loss="huber", delta=2.0)
         rel_close(r["summaries"][w]["final_cost"], ref["final_cost"], 1e-6, f"huber window {w}")
 
 
-def test_window_long_tracks(mba):
-    """Points seen by more than 32 cameras take the long-track path of the point passes."""
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
+def test_window_long_tracks(mba, schur):
+    """Points seen by more than 32 cameras take the long-track path of the point
+    passes; 48 cameras give 1176 Schur blocks per window."""
     ws = [make_scene(48, 150, track=("fixed", 40), sigma=1.0, seed=61), make_scene(40, 80, track=("fixed", 36),
                                                                                    sigma=1.0, seed=62),
           make_scene(7, 90, sigma=1.0, seed=63)]
     with mba.Batch(_tuples(ws), precision="fp64") as b:
+        b.set_schedule(schur=schur)
         r = b.solve(**OPTS)
     for w, s in enumerate(ws):
         ref = _oracle_solve(s)
@@ -91,9 +99,10 @@ def test_batch_matches_single_problem_solver(mba):
     rel_close(pb, ps, 1e-7, "points")
 
 
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
 @pytest.mark.parametrize("precision,mu,tol,init", [("fp64", -1.0, 1e-6, True), ("fp64", 1e-2, 1e-6, True),
                                                    ("fp32", -1.0, 3e-3, False), ("fp32", 1e-2, 3e-3, True)])
-def test_batch_adjoint_matches_oracle(mba, precision, mu, tol, init):
+def test_batch_adjoint_matches_oracle(mba, precision, mu, tol, init, schur):
     """mu < 0: each window's last accepted mu (tiny after 8 good steps, so the
     damped system is nearly singular along the 7-DoF gauge).  The observation
     gradient W J v does not see the gauge and matches in both precisions; the
@@ -102,6 +111,7 @@ def test_batch_adjoint_matches_oracle(mba, precision, mu, tol, init):
     ws = _small(count=6, seed=31)
     rng = np.random.default_rng(9)
     with mba.Batch(_tuples(ws), precision=precision) as b:
+        b.set_schedule(schur=schur)
         gc = rng.normal(size=(b.info["nc"], 9))
         gp = rng.normal(size=(b.info["np"], 3))
         r = b.solve(gc, gp, adjoint_pcg_max_iter=1000, adjoint_pcg_rel_tol=1e-14, adjoint_mu=mu, **OPTS)
@@ -136,8 +146,8 @@ def test_schedules_agree_and_repeat_bit_exactly(mba):
     ws = _small(count=10, seed=51)
     out = {}
     with mba.Batch(_tuples(ws), precision="fp32") as b:
-        for nt in (256, 512):
-            b.set_schedule(nt, 1)
+        for nt, schur in ((256, "implicit"), (512, "implicit"), (256, "explicit"), (512, "explicit")):
+            b.set_schedule(nt, 1, schur)
             res = []
             for _ in range(2):
                 b.reset()
@@ -145,11 +155,13 @@ def test_schedules_agree_and_repeat_bit_exactly(mba):
             (r1, (c1, p1)), (r2, (c2, p2)) = res
             assert np.array_equal(c1, c2) and np.array_equal(p1, p2), f"schedule {nt} is not deterministic"
             assert [s["final_cost"] for s in r1["summaries"]] == [s["final_cost"] for s in r2["summaries"]]
-            out[nt] = np.array([s["final_cost"] for s in r1["summaries"]])
+            out[(nt, schur)] = np.array([s["final_cost"] for s in r1["summaries"]])
         best = b.autotune(**OPTS)
         assert best["threads_per_cta"] in (256, 512) and best["ctas_per_sm"] >= 1 and best["ms"] > 0
+        assert best["schur"] in ("implicit", "explicit")
         assert b.schedule()["threads_per_cta"] == best["threads_per_cta"]
-    rel_close(out[256], out[512], 1e-4, "final costs across schedules")
+    for k in out:
+        rel_close(out[k], out[(256, "implicit")], 1e-4, f"final costs, schedule {k}")
 
 
 def test_invalid_batches(mba):
