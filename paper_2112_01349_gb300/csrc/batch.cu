@@ -83,7 +83,7 @@ struct BatchArgs {
     // explicit Schur complement (when selected)
     void *Jcm;                // [n][24] T: sqrt(W)-scaled Jc (18) and Jp (6), camera-major (per linearisation)
     const int32_t *blk_ptr;   // pair offsets of each upper 9x9 block (i <= k) of each window
-    const int2 *pairs;        // (camera-major position in camera i, in camera k) of one point, per block
+    const int4 *pairs;        // (camera-major position in camera i, in camera k, point, 0), per block
     void *S;                  // per CTA: packed upper blocks of S~ (smax values of T)
     int64_t smax;
     const double *gbar_c, *gbar_p;
@@ -106,7 +106,7 @@ struct V2<double> {
 template <typename T>
 struct WinMem {
     double *cams, *camn, *tab64, *Hpp, *v, *Binv, *x, *r, *z, *p, *q, *slot, *sb;
-    T *tabT, *pv, *stage;
+    T *tabT, *pv, *stage, *BinvT;
     int32_t *cptr, *wf, *wl, *wcam0;
 };
 
@@ -140,7 +140,7 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
     m.p = (double *)take(8 * c9);
     m.q = (double *)take(8 * c9);
     m.slot = (double *)take(8 * 54 * (size_t)(nwarp + ncmax));
-    m.sb = (double *)take(8 * 2 * (size_t)nwarp);
+    m.sb = (double *)take(8 * 2 * (size_t)(nwarp + 1));
     m.tabT = (T *)take(sizeof(T) * kTabS * (size_t)ncmax);
     m.pv = (T *)take(sizeof(T) * c9);
     m.cptr = (int32_t *)take(4 * (size_t)(ncmax + 1));
@@ -148,6 +148,7 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
     m.wl = (int32_t *)take(4 * (size_t)ncmax);
     m.wcam0 = (int32_t *)take(4 * (size_t)nwarp);
     m.stage = (T *)take(sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp);
+    m.BinvT = (T *)take(sizeof(T) * 45 * (size_t)ncmax);
     return (size_t)off;
 }
 
@@ -171,21 +172,29 @@ __device__ __forceinline__ double2 cta_sum2(double a, double b, double *sb) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         sb[2 * wid] = a;
         sb[2 * wid + 1] = b;
     }
     __syncthreads();
-    double x = 0.0, y = 0.0;
+    if (wid == 0) {
+        double x = lane < NW ? sb[2 * lane] : 0.0, y = lane < NW ? sb[2 * lane + 1] : 0.0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        x += sb[2 * w];
-        y += sb[2 * w + 1];
+        for (int o = NW / 2; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) {
+            sb[2 * NW] = x;
+            sb[2 * NW + 1] = y;
+        }
     }
     __syncthreads();
-    return make_double2(x, y);
+    return make_double2(sb[2 * NW], sb[2 * NW + 1]);
 }
+
 
 template <typename T>
 __device__ __forceinline__ void ld_c(const T *Ci, int pt, T *c) {
@@ -821,17 +830,19 @@ __device__ __forceinline__ void make_pv(const WinMem<T> &M, const double *vec, i
     }
 }
 
-// z = B~^-1 r per camera (packed symmetric inverse); returns (r.r, r.z) partials.
+// z = B~^-1 r per camera, with B~^-1 (inverted in FP64) applied in the
+// problem's precision T; returns (r.r, r.z) partials in FP64.
 template <typename T, int NT>
 __device__ __forceinline__ double2 precond(const WinMem<T> &M, int nc) {
     double rr = 0.0, rz = 0.0;
     for (int t = threadIdx.x; t < 9 * nc; t += NT) {
         const int i = t / 9, a = t - 9 * (t / 9);
-        const double *Bi = M.Binv + 45 * i;
+        const T *Bi = M.BinvT + 45 * i;
         const double *ri = M.r + 9 * i;
-        double z = 0.0;
+        T zt = T(0);
 #pragma unroll
-        for (int b = 0; b < 9; ++b) z = fma(Bi[sym9(a, b)], ri[b], z);
+        for (int b = 0; b < 9; ++b) zt = fma(Bi[sym9(a, b)], (T)ri[b], zt);
+        const double z = (double)zt;
         M.z[t] = z;
         rr = fma(M.r[t], M.r[t], rr);
         rz = fma(M.r[t], z, rz);
@@ -868,6 +879,7 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
             for (int b = 0; b < 9; ++b) L[a * 9 + b] = M.Hpp[45 * i + sym9(a, b)];
         for (int a = 0; a < 9; ++a) L[a * 10] += mu * damp_term_b(damping, L[a * 10]);
         bool ok = true;
+        double il[9];  // reciprocals of the Cholesky diagonal
         for (int j = 0; j < 9 && ok; ++j) {
             double s = L[j * 9 + j];
             for (int k = 0; k < j; ++k) s -= L[j * 9 + k] * L[j * 9 + k];
@@ -876,11 +888,12 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
                 break;
             }
             const double l = sqrt(s);
+            il[j] = 1.0 / l;
             L[j * 9 + j] = l;
             for (int r = j + 1; r < 9; ++r) {
                 double t = L[r * 9 + j];
                 for (int k = 0; k < j; ++k) t -= L[r * 9 + k] * L[j * 9 + k];
-                L[r * 9 + j] = t / l;
+                L[r * 9 + j] = t * il[j];
             }
         }
         if (!ok) {
@@ -892,14 +905,17 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
             for (int r = 0; r < 9; ++r) {
                 double s = (r == col) ? 1.0 : 0.0;
                 for (int k = 0; k < r; ++k) s -= L[r * 9 + k] * y[k];
-                y[r] = s / L[r * 9 + r];
+                y[r] = s * il[r];
             }
             for (int r = 8; r >= 0; --r) {
                 double s = y[r];
                 for (int k = r + 1; k < 9; ++k) s -= L[k * 9 + r] * y[k];
-                y[r] = s / L[r * 9 + r];
+                y[r] = s * il[r];
             }
-            for (int r = col; r < 9; ++r) M.Binv[45 * i + sym9(col, r)] = y[r];
+            for (int r = col; r < 9; ++r) {
+                M.Binv[45 * i + sym9(col, r)] = y[r];
+                M.BinvT[45 * i + sym9(col, r)] = (T)y[r];
+            }
         }
     }
     T *Ci = (T *)A.Cinv;
@@ -962,10 +978,10 @@ __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d
         for (int base = p0; base < p1; base += SP) {
             const int cnt = min(SP, p1 - base);
             if (lane < cnt) {
-                const int2 pr = __ldg(A.pairs + base + lane);
+                const int4 pr = __ldg(A.pairs + base + lane);
                 const T *J1 = Jcm + 24 * (int64_t)pr.x, *J2 = Jcm + 24 * (int64_t)pr.y;
                 T c[6];
-                ld_c<T>(Ci, __ldg(A.cm_pt + pr.x), c);
+                ld_c<T>(Ci, pr.z, c);
                 T q0[3], q1[3];  // Q = Jp~_1 C~^-1 (2x3)
                 sym3_mul<T>(c, J1[18], J1[19], J1[20], q0);
                 sym3_mul<T>(c, J1[21], J1[22], J1[23], q1);
@@ -1009,13 +1025,12 @@ __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d
     }
 }
 
-// q = S~ p (p given in M.pv as T); returns this thread's share of p.q.
+// q = S~ p (p given in M.pv as T) into M.q.
 template <typename T, int NT>
-__device__ double s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+__device__ void s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
     const int nc = d.nc;
     const T *S = (const T *)A.S + A.smax * (int64_t)blockIdx.x;
     const T *pT = M.pv;
-    double pq = 0.0;
     for (int r = threadIdx.x; r < 9 * nc; r += NT) {
         const int i = r / 9, a = r - 9 * (r / 9);
         T acc = T(0);
@@ -1025,17 +1040,15 @@ __device__ double s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc
 #pragma unroll
             for (int b = 0; b < 9; ++b) acc += Sb[9 * b] * pk[b];
         }
+        const T *Sr = S + 81 * (int64_t)blk_index(i, i, nc) + 9 * a;  // blocks (i, k >= i) are consecutive
         for (int k = i; k < nc; ++k) {  // row a of block (i, k)
-            const T *Sb = S + 81 * (int64_t)blk_index(i, k, nc) + 9 * a;
+            const T *Sb = Sr + 81 * (int64_t)(k - i);
             const T *pk = pT + 9 * k;
 #pragma unroll
             for (int b = 0; b < 9; ++b) acc += Sb[b] * pk[b];
         }
-        const double q = (double)acc;
-        M.q[r] = q;
-        pq = fma(M.p[r], q, pq);
+        M.q[r] = (double)acc;
     }
-    return pq;
 }
 
 // PCG of Alg. 2 on S x = g, g = vvec - E C~^-1 wvec (Sec. 3 Eq. 3), x0 = 0;
@@ -1072,7 +1085,8 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
                     M.pv[t] = (T)pn;
                 }
                 __syncthreads();
-                pq = s_matvec<T, NT>(A, M, d);
+                s_matvec<T, NT>(A, M, d);
+                for (int t = threadIdx.x; t < m9; t += NT) pq = fma(M.p[t], M.q[t], pq);
             } else {
             for (int t = threadIdx.x; t < m9; t += NT) M.p[t] = n == 0 ? M.z[t] : fma(beta, M.p[t], M.z[t]);
             __syncthreads();
@@ -1603,7 +1617,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     // camera (all ordered pairs), goes to the list of block (camera(u),
     // camera(v)); lists are in point order.  Skipped (explicit form not
     // offered) when they would be too large.
-    std::vector<int2> pairs;
+    std::vector<int4> pairs;
     std::vector<int32_t> blk_ptr;
     bool explicit_ok = true;
     {
@@ -1638,7 +1652,9 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                                 const int32_t cu = pm_pc[u].y - d.cam0, cv = pm_pc[v].y - d.cam0;
                                 if (cu > cv) continue;
                                 if (pass == 0) ++bcnt[blk(cu, cv) + 1];
-                                else pairs[(size_t)(base + bcnt[blk(cu, cv)]++)] = make_int2(pm2cm[u], pm2cm[v]);
+                                else
+                                    pairs[(size_t)(base + bcnt[blk(cu, cv)]++)] =
+                                        make_int4(pm2cm[u], pm2cm[v], pm_pc[u].x, 0);
                             }
                         o = e;
                     }
@@ -1704,7 +1720,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                  o_gp = take(24 * (size_t)NP), o_go = take(16 * (size_t)N), o_g0c = take(72 * (size_t)NC),
                  o_g0p = take(24 * (size_t)NP);
     const int64_t smax = (int64_t)ncmax * (ncmax + 1) / 2 * 81;
-    const size_t o_pairs = explicit_ok ? take(sizeof(int2) * pairs.size()) : 0,
+    const size_t o_pairs = explicit_ok ? take(sizeof(int4) * pairs.size()) : 0,
                  o_bptr = explicit_ok ? take(4 * blk_ptr.size()) : 0,
                  o_jcm = explicit_ok ? take(24 * w * (size_t)N) : 0,
                  o_S = explicit_ok ? take(w * (size_t)smax * (size_t)b->sms * kMaxCtasPerSm) : 0;
@@ -1759,7 +1775,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     A.grad_p0 = (double *)(base + o_g0p);
     A.out = b->out;
     if (explicit_ok) {
-        A.pairs = (const int2 *)(base + o_pairs);
+        A.pairs = (const int4 *)(base + o_pairs);
         A.blk_ptr = (const int32_t *)(base + o_bptr);
         A.Jcm = base + o_jcm;
         A.S = base + o_S;
@@ -1778,7 +1794,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     if (e == cudaSuccess) e = up((void *)A.cm2pm, cm2pm.data(), 4 * (size_t)N);
     if (e == cudaSuccess) e = up((void *)A.pm2cm, pm2cm.data(), 4 * (size_t)N);
     if (e == cudaSuccess) e = up((void *)A.cam_ptr, cam_ptr.data(), 4 * ((size_t)NC + 1));
-    if (e == cudaSuccess && explicit_ok) e = up((void *)A.pairs, pairs.data(), sizeof(int2) * pairs.size());
+    if (e == cudaSuccess && explicit_ok) e = up((void *)A.pairs, pairs.data(), sizeof(int4) * pairs.size());
     if (e == cudaSuccess && explicit_ok) e = up((void *)A.blk_ptr, blk_ptr.data(), 4 * blk_ptr.size());
     if (e == cudaSuccess) e = up(A.cams, cameras, 72 * (size_t)NC);
     if (e == cudaSuccess) e = up(b->cams0, cameras, 72 * (size_t)NC);
