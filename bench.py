@@ -64,14 +64,33 @@ def pcg_bytes_per_iter(sc, w: int) -> float:
 # FP32 non-tensor peak derived from unit counts and clocks: 152 SMs x 128 FP32
 # lanes x 2 FLOP (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# Batched windows: FP32 operations of one PCG iteration per observation in the
-# matrix-free passes (projection, D and Jp: 88; Jc p: 42; W Jp^T t: 14; scan
-# adds: 15; C~^-1: 18; s = W Jp b: 14; camera pass Jc^T s with its projection:
-# 115), and the bytes that pass must move per observation: (point, camera) 8,
-# camera-major position 4, s written 8 and read 8, camera-major X 16, plus per
-# point X 16 and C~^-1 24 (amortised over the track, mean 4.03).
-BATCH_FLOP_PER_OBS_ITER = 305
-BATCH_BYTES_PER_OBS_ITER = 8 + 4 + 8 + 8 + 16 + 40 / 4.03
+# Batched windows, counted FP32 operations:
+#  implicit product, per observation per PCG iteration: projection, D and Jp 88;
+#    Jc p 42; W Jp^T t 14; scan adds 15; C~^-1 18; s = W Jp b 14; camera pass
+#    Jc^T s with its projection 115 (also the right-hand side of every solve);
+#  explicit S~, per (observation pair of one point) per damped solve: Q = Jp C~^-1
+#    36, G 24, F = G Jc 72, the 81 block entries 324;
+#  explicit product, per PCG iteration: 2 (9 nc)^2;
+#  per observation per LM iteration: linearisation (two projections with
+#    Jacobians, the 9 point and 54 camera block terms) 450, back-substitution 380.
+BATCH_FLOP_IMPLICIT_OBS_ITER = 305
+BATCH_FLOP_PAIR = 456
+BATCH_FLOP_OBS_LM = 830
+
+
+def batch_flops(ws, summaries, schur: str) -> float:
+    """Counted FP32 operations of one batched solve (forward + adjoint)."""
+    tot = 0.0
+    for w, sm in zip(ws, summaries):
+        solves = sm["iterations"] + (1 if sm["adjoint_pcg_iters"] > 0 else 0)
+        iters = sm["pcg_iters_total"] + sm["adjoint_pcg_iters"]
+        tot += sm["iterations"] * w.n * BATCH_FLOP_OBS_LM + solves * w.n * BATCH_FLOP_IMPLICIT_OBS_ITER
+        if schur == "explicit":
+            L = np.bincount(w.pt_idx)
+            tot += solves * float((L * (L + 1) // 2).sum()) * BATCH_FLOP_PAIR + iters * 2.0 * (9 * w.nc) ** 2
+        else:
+            tot += iters * w.n * BATCH_FLOP_IMPLICIT_OBS_ITER
+    return tot
 
 
 def pcg_flops_per_iter(sc) -> float:
@@ -368,9 +387,6 @@ def main():
         nobs = sum(w.n for w in ws)
         pcg_b = sum(x["pcg_iters_total"] for x in sm_b)
         adj_b = sum(x["adjoint_pcg_iters"] for x in sm_b)
-        # obs-iterations of the PCG passes (forward right-hand sides + iterations, adjoint the same)
-        obs_it = sum(w.n * (x["pcg_iters_total"] + x["iterations"] + x["adjoint_pcg_iters"] + 1)
-                     for w, x in zip(ws, sm_b))
         t_full = statistics.median(full_ms)
         # end to end: pinned host buffers -> create (layout + H2D) -> solve + adjoint -> D2H of the
         # parameters and gradients -> destroy
@@ -397,7 +413,7 @@ def main():
         for _ in range(2):
             batch_e2e()
         e2e_b = (time.perf_counter() - t0b) / 2
-        flops = obs_it * BATCH_FLOP_PER_OBS_ITER
+        flops = batch_flops(ws, sm_b, tune["schur"])
         batched = {
             "workload": f"batched local BA: {len(ws)} windows (cameras U[5,30], points U[200,3000], track 2+Geom "
                         f"mean 4, 1 px noise), {bt.info['nc']} cameras, {bt.info['np']} points, {nobs} observations "
@@ -407,15 +423,16 @@ def main():
             "window_lm_iterations_per_s": sum(x["iterations"] for x in sm_b) / (t_full / 1e3),
             "pcg_iters_forward": pcg_b, "pcg_iters_adjoint": adj_b,
             "schedule": {"threads_per_cta": tune["threads_per_cta"], "ctas_per_sm": tune["ctas_per_sm"],
-                         "autotune_ms": tune["ms"]},
+                         "schur": tune["schur"], "autotune_ms": tune["ms"]},
             "launch": "one CUDA graph replay (claim-counter reset + one persistent kernel)",
             "gpu_launches": 1,
             "roofline": {"kernel": "batch_kernel (persistent, one window per CTA)", "bound": "alu",
                          "achieved": flops / (t_full / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops / (t_full / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                          "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
-                         "hbm_gbs": obs_it * BATCH_BYTES_PER_OBS_ITER / (t_full / 1e3) / 1e9,
-                         "note": "whole launch time; latency-bound (see profiles/)"},
+                         "counted": "FP32 operations of the schedule's Schur form (see batch_flops)",
+                         "note": "whole launch time; the launch is latency-bound (FP64 vector chains, CTA "
+                                 "barriers), see profiles/batch_kernel_windows512.md"},
             "e2e": {"ms": 1e3 * e2e_b, "windows_per_s": len(ws) / e2e_b, "h2d_bytes_per_step": h2d_b,
                     "d2h_bytes_per_step": d2h_b},
         }

@@ -60,7 +60,7 @@ struct BatchOpts {
 };
 
 struct BatchArgs {
-    int32_t nw, ncmax, loss, pad;
+    int32_t nw, ncmax, loss, s_smem;  // s_smem: explicit S~ held in shared memory
     double delta;
     const WinDesc *desc;
     const int32_t *order;     // claim order (windows by decreasing observation count)
@@ -105,8 +105,9 @@ struct V2<double> {
 // Shared memory of one CTA, carved from the dynamic allocation.
 template <typename T>
 struct WinMem {
-    double *cams, *camn, *tab64, *Hpp, *v, *Binv, *x, *r, *z, *p, *q, *slot, *sb;
+    double *cams, *camn, *tab64, *Hpp, *v, *x, *r, *z, *p, *q, *slot, *sb;
     T *tabT, *pv, *stage, *BinvT;
+    T *S;  // explicit S~ in shared memory (NULL: the CTA's global scratch)
     int32_t *cptr, *wf, *wl, *wcam0;
 };
 
@@ -119,7 +120,7 @@ struct Stage {
 };
 
 template <typename T>
-__host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int nwarp, WinMem<T> &m) {
+__host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int nwarp, int64_t svals, WinMem<T> &m) {
     uintptr_t off = 0;
     const uintptr_t b = (uintptr_t)base;
     auto take = [&](size_t bytes) -> void * {
@@ -133,22 +134,25 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
     m.tab64 = (double *)take(8 * (size_t)kCamTab * ncmax);
     m.Hpp = (double *)take(8 * 45 * (size_t)ncmax);
     m.v = (double *)take(8 * c9);
-    m.Binv = (double *)take(8 * 45 * (size_t)ncmax);
     m.x = (double *)take(8 * c9);
     m.r = (double *)take(8 * c9);
     m.z = (double *)take(8 * c9);
     m.p = (double *)take(8 * c9);
     m.q = (double *)take(8 * c9);
-    m.slot = (double *)take(8 * 54 * (size_t)(nwarp + ncmax));
-    m.sb = (double *)take(8 * 2 * (size_t)(nwarp + 1));
+    // camera-pass slots and the Schur-build staging are never live together
+    const size_t slot_b = 8 * 54 * (size_t)(nwarp + ncmax),
+                 stage_b = sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp;
+    m.slot = (double *)take(slot_b > stage_b ? slot_b : stage_b);
+    m.stage = (T *)m.slot;
+    m.sb = (double *)take(8 * (2 * 32 * (size_t)nwarp + 2));
     m.tabT = (T *)take(sizeof(T) * kTabS * (size_t)ncmax);
     m.pv = (T *)take(sizeof(T) * c9);
     m.cptr = (int32_t *)take(4 * (size_t)(ncmax + 1));
     m.wf = (int32_t *)take(4 * (size_t)ncmax);
     m.wl = (int32_t *)take(4 * (size_t)ncmax);
     m.wcam0 = (int32_t *)take(4 * (size_t)nwarp);
-    m.stage = (T *)take(sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp);
     m.BinvT = (T *)take(sizeof(T) * 45 * (size_t)ncmax);
+    m.S = svals > 0 ? (T *)take(sizeof(T) * (size_t)svals) : nullptr;
     return (size_t)off;
 }
 
@@ -164,37 +168,46 @@ __device__ __forceinline__ double damp_term_b(int damping, double d) {
 }
 
 // Block-wide sums of two doubles; every thread gets the result.  Fixed order:
-// a butterfly in each warp, then the warp sums in warp order.
+// the per-thread values go through shared memory, warp 0 adds them (lane l
+// takes threads l, l + 32, ...) and finishes with a butterfly.  One warp does
+// all the FP64 additions: on this GPU each warp-wide FP64 instruction holds
+// the SM's FP64 pipe for 16 cycles, so spreading the tree over every warp costs
+// several times more pipe time.  sb holds 2 NT + 2 doubles.
 template <int NT>
 __device__ __forceinline__ double2 cta_sum2(double a, double b, double *sb) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    constexpr int NW = NT / 32;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        sb[2 * wid] = a;
-        sb[2 * wid + 1] = b;
-    }
+    sb[threadIdx.x] = a;
+    sb[NT + threadIdx.x] = b;
     __syncthreads();
-    if (wid == 0) {
-        double x = lane < NW ? sb[2 * lane] : 0.0, y = lane < NW ? sb[2 * lane + 1] : 0.0;
+    if (threadIdx.x < 32) {
+        // pairwise tree over the NT / 32 values of the lane (short dependency chain)
+        const int lane = threadIdx.x;
+        double xv[NT / 32], yv[NT / 32];
 #pragma unroll
-        for (int o = NW / 2; o > 0; o >>= 1) {
+        for (int k = 0; k < NT / 32; ++k) {
+            xv[k] = sb[lane + 32 * k];
+            yv[k] = sb[NT + lane + 32 * k];
+        }
+#pragma unroll
+        for (int h = NT / 64; h > 0; h >>= 1)
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                xv[k] += xv[k + h];
+                yv[k] += yv[k + h];
+            }
+        double x = xv[0], y = yv[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_xor_sync(0xffffffffu, x, o);
             y += __shfl_xor_sync(0xffffffffu, y, o);
         }
         if (lane == 0) {
-            sb[2 * NW] = x;
-            sb[2 * NW + 1] = y;
+            sb[2 * NT] = x;
+            sb[2 * NT + 1] = y;
         }
     }
     __syncthreads();
-    return make_double2(sb[2 * NW], sb[2 * NW + 1]);
+    return make_double2(sb[2 * NT], sb[2 * NT + 1]);
 }
-
 
 template <typename T>
 __device__ __forceinline__ void ld_c(const T *Ci, int pt, T *c) {
@@ -912,10 +925,7 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
                 for (int k = r + 1; k < 9; ++k) s -= L[k * 9 + r] * y[k];
                 y[r] = s * il[r];
             }
-            for (int r = col; r < 9; ++r) {
-                M.Binv[45 * i + sym9(col, r)] = y[r];
-                M.BinvT[45 * i + sym9(col, r)] = (T)y[r];
-            }
+            for (int r = col; r < 9; ++r) M.BinvT[45 * i + sym9(col, r)] = (T)y[r];
         }
     }
     T *Ci = (T *)A.Cinv;
@@ -958,7 +968,7 @@ __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d
     constexpr int SP = Stage<T>::pairs, SS = Stage<T>::stride;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nc = d.nc, nb = nc * (nc + 1) / 2;
-    T *S = (T *)A.S + A.smax * (int64_t)blockIdx.x;
+    T *S = M.S ? M.S : (T *)A.S + A.smax * (int64_t)blockIdx.x;
     T *st = M.stage + wid * SP * SS;
     const T *Jcm = (const T *)A.Jcm;
     const T *Ci = (const T *)A.Cinv;
@@ -1029,7 +1039,7 @@ __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d
 template <typename T, int NT>
 __device__ void s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
     const int nc = d.nc;
-    const T *S = (const T *)A.S + A.smax * (int64_t)blockIdx.x;
+    const T *S = M.S ? M.S : (const T *)A.S + A.smax * (int64_t)blockIdx.x;
     const T *pT = M.pv;
     for (int r = threadIdx.x; r < 9 * nc; r += NT) {
         const int i = r / 9, a = r - 9 * (r / 9);
@@ -1350,7 +1360,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WinState S;
     WinMem<T> M;
-    win_carve<T>(smem_raw, A.ncmax, NT / 32, M);
+    win_carve<T>(smem_raw, A.ncmax, NT / 32, A.s_smem ? A.smax : 0, M);
     const BatchOpts O = *A.opts;
     for (;;) {
         if (threadIdx.x == 0) S.win = atomicAdd(A.counter, 1);
@@ -1363,9 +1373,9 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchArgs A) {
 }
 
 template <typename T, int NT>
-size_t smem_bytes(int ncmax) {
+size_t smem_bytes(int ncmax, int64_t svals) {
     WinMem<T> m;
-    return win_carve<T>(nullptr, ncmax, NT / 32, m);
+    return win_carve<T>(nullptr, ncmax, NT / 32, svals, m);
 }
 
 // Instances: (threads per CTA, CTAs per SM the register budget is cut for).
@@ -1380,9 +1390,10 @@ const void *kernel_ptr(bool fp32, int nt, int cps) {
     return cps >= 3 ? (const void *)batch_kernel<double, 256, 3> : (const void *)batch_kernel<double, 256, 2>;
 }
 
-size_t kernel_smem(bool fp32, int nt, int ncmax) {
-    if (fp32) return nt == 256 ? smem_bytes<float, 256>(ncmax) : smem_bytes<float, 512>(ncmax);
-    return nt == 256 ? smem_bytes<double, 256>(ncmax) : smem_bytes<double, 512>(ncmax);
+// Dynamic shared memory of a launch; svals > 0 also holds S~ (svals values of T).
+size_t kernel_smem(bool fp32, int nt, int ncmax, int64_t svals) {
+    if (fp32) return nt == 256 ? smem_bytes<float, 256>(ncmax, svals) : smem_bytes<float, 512>(ncmax, svals);
+    return nt == 256 ? smem_bytes<double, 256>(ncmax, svals) : smem_bytes<double, 512>(ncmax, svals);
 }
 
 size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -1414,6 +1425,7 @@ struct mba_batch {
     int nt = 0, cps = 0;            // schedule in use
     cudaGraphExec_t gexec = nullptr;
     int g_nt = 0, g_grid = 0, g_cps = 0;  // schedule the graph was captured with
+    bool g_ssm = false;
     bool has_grads = false;
 };
 
@@ -1428,9 +1440,13 @@ constexpr int kMaxCtasPerSm = 4;  // S~ scratch is sized for this many resident 
     } while (0)
 
 // Resident CTAs per SM of the kernel instance used for (nt, cps).
-int max_ctas_per_sm(const mba_batch *b, int nt, int cps) {
+int max_ctas_per_sm(const mba_batch *b, int nt, int cps, bool s_smem = false) {
     const void *k = kernel_ptr(b->fp32, nt, cps);
-    const size_t sm = kernel_smem(b->fp32, nt, b->ncmax);
+    const size_t sm = kernel_smem(b->fp32, nt, b->ncmax, s_smem ? b->A.smax : 0);
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (sm > (size_t)optin) return 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, nt, sm) != cudaSuccess) return 0;
@@ -1458,21 +1474,28 @@ mba_status resolve_schedule(const mba_batch *b, int want_nt, int want_cps, int w
     return MBA_OK;
 }
 
+// The explicit S~ goes to shared memory when cps CTAs of that size still fit.
+bool s_in_smem(const mba_batch *b) {
+    return b->schur == 2 && b->explicit_ok && max_ctas_per_sm(b, b->nt, b->cps, true) >= b->cps;
+}
+
 mba_status build_graph(mba_batch *b) {
     const int grid_full = b->sms * b->cps;
     const int grid = grid_full < b->nw ? grid_full : b->nw;
-    if (b->gexec && b->g_nt == b->nt && b->g_grid == grid && b->g_cps == b->cps) return MBA_OK;
+    const bool ssm = s_in_smem(b);
+    if (b->gexec && b->g_nt == b->nt && b->g_grid == grid && b->g_cps == b->cps && b->g_ssm == ssm) return MBA_OK;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
     const void *k = kernel_ptr(b->fp32, b->nt, b->cps);
-    const size_t sm = kernel_smem(b->fp32, b->nt, b->ncmax);
+    const size_t sm = kernel_smem(b->fp32, b->nt, b->ncmax, ssm ? b->A.smax : 0);
     BCK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(int32_t), b->stream);
     BatchArgs args = b->A;
+    args.s_smem = ssm ? 1 : 0;
     void *kargs[] = {(void *)&args};
     cudaError_t e2 = cudaLaunchKernel(k, dim3(grid), dim3(b->nt), kargs, sm, b->stream);
     cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
@@ -1490,6 +1513,7 @@ mba_status build_graph(mba_batch *b) {
     b->g_nt = b->nt;
     b->g_grid = grid;
     b->g_cps = b->cps;
+    b->g_ssm = ssm;
     return MBA_OK;
 }
 
