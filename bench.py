@@ -93,6 +93,14 @@ def batch_flops(ws, summaries, schur: str) -> float:
     return tot
 
 
+# DRAM bytes per observation per PCG pass of pcg_kernel, measured by ncu on the
+# same kernel (profiles/pcg_kernel_fp32_venice_0.3.md: 5.317 GB read + 32.1 MB
+# written over 31 passes of 1,501,396 observations; FP64: 16.32 GB + 52.1 MB).
+# Traffic grows with the observation count, so a full launch moves this many
+# bytes per observation per pass.
+PCG_TRAFFIC_B_PER_OBS_PASS = {4: (5.317e9 + 32.1e6) / 31 / 1501396, 8: (16.32e9 + 52.1e6) / 31 / 1501396}
+
+
 def pcg_flops_per_iter(sc) -> float:
     """48 FMA per observation (E^T p and E b), 9 per point (C~^-1), 2 x 81 per camera."""
     return 2.0 * (48 * sc.n + 9 * sc.np_ + 162 * sc.nc)
@@ -226,6 +234,33 @@ def profile_case(precision: str, scale: float) -> int:
     return 0
 
 
+def profile_batch(windows: int) -> int:
+    """A batched solve for ncu captures: the first `windows` windows of the
+    512-window workload (largest sizes mixed as in the full batch), fixed
+    schedule (256 threads x 2 CTAs per SM, explicit Schur form), one warm-up
+    replay and one measured replay, 8 LM iterations + adjoint each."""
+    import torch
+
+    from paper_2112_01349_gb300 import _build, mba
+    from scenes import make_windows
+
+    torch.cuda.set_device(0)
+    _build.build()
+    ws = make_windows(512)[:windows]
+    tup = [(w.cameras, w.points, w.observations, w.cam_idx, w.pt_idx) for w in ws]
+    rng = np.random.default_rng(5)
+    with mba.Batch(tup, precision="fp32") as bt:
+        bt.set_schedule(256, 2, "explicit")
+        gc, gp = rng.normal(size=(bt.info["nc"], 9)), rng.normal(size=(bt.info["np"], 3))
+        ms = []
+        for _ in range(2):
+            bt.reset()
+            ms.append(bt.solve(gc, gp, max_iter=8, pcg_max_iter=PCG_MAX, pcg_rel_tol=1e-10)["ms"])
+        info = bt.info
+    print(json.dumps({"profile_case": "batch", "windows": windows, "n": info["n"], "ms": ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,11 +268,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["fp32", "fp64"], default=None,
-                    help="profiling aid: run one small solve of the workload (see --scale) and exit; "
+    ap.add_argument("--profile-case", choices=["fp32", "fp64", "batch"], default=None,
+                    help="profiling aid: run one small solve of the workload (see --scale, --windows) and exit; "
                          "prints no bench line")
-    ap.add_argument("--scale", type=float, default=0.3, help="camera/point scale of --profile-case")
+    ap.add_argument("--scale", type=float, default=0.3, help="camera/point scale of --profile-case fp32/fp64")
+    ap.add_argument("--windows", type=int, default=128, help="windows of --profile-case batch")
     args = ap.parse_args()
+    if args.profile_case == "batch":
+        return profile_batch(args.windows)
     if args.profile_case:
         return profile_case(args.profile_case, args.scale)
     if args.warmup < 3:
@@ -303,6 +341,8 @@ def main():
         alg_flops = (pcg_iters + launches) * pcg_flops_per_iter(sc)
         return dict(value=value, ms_per_step=ms / args.steps, pcg_ms=pcg_ms, pcg_iters=pcg_iters,
                     pcg_launches=launches, gbs=alg_bytes / (pcg_ms / 1e3) / 1e9,
+                    traffic_per_launch=PCG_TRAFFIC_B_PER_OBS_PASS[w] * sc.n * (pcg_iters + launches) / launches,
+                    alg_bytes_per_launch=alg_bytes / launches,
                     tflops=alg_flops / (pcg_ms / 1e3) / 1e12,
                     us_per_pcg_iter=1e3 * pcg_ms / max(1, pcg_iters + launches),
                     final_cost=sums[-1]["final_cost"], kernel_launches=sum(s["kernel_launches"] for s in sums),
@@ -432,7 +472,7 @@ def main():
                          "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
                          "counted": "FP32 operations of the schedule's Schur form (see batch_flops)",
                          "note": "whole launch time; the launch is latency-bound (FP64 vector chains, CTA "
-                                 "barriers), see profiles/batch_kernel_windows512.md"},
+                                 "barriers), see profiles/batch_kernel_windows128.md"},
             "e2e": {"ms": 1e3 * e2e_b, "windows_per_s": len(ws) / e2e_b, "h2d_bytes_per_step": h2d_b,
                     "d2h_bytes_per_step": d2h_b},
         }
@@ -459,7 +499,10 @@ def main():
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"kernel": "pcg_kernel (persistent PCG, implicit Schur product)", "bound": "hbm",
                      "achieved": a32["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": a32["gbs"] / hbm_peak,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind, "traffic": a32["traffic_per_launch"],
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write per observation per pass on the "
+                                     "0.3-scale case, scaled by observations and passes; profiles/)",
+                     "algorithmic_bytes_per_launch": a32["alg_bytes_per_launch"],
                      "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"]},
         "fp64": {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms_per_step"],
                  "final_cost": a64["final_cost"],
