@@ -144,7 +144,7 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
                  stage_b = sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp;
     m.slot = (double *)take(slot_b > stage_b ? slot_b : stage_b);
     m.stage = (T *)m.slot;
-    m.sb = (double *)take(8 * (2 * 32 * (size_t)nwarp + 2));
+    m.sb = (double *)take(8 * (2 * 32 * (size_t)nwarp + 4));
     m.tabT = (T *)take(sizeof(T) * kTabS * (size_t)ncmax);
     m.pv = (T *)take(sizeof(T) * c9);
     m.cptr = (int32_t *)take(4 * (size_t)(ncmax + 1));
@@ -207,6 +207,40 @@ __device__ __forceinline__ double2 cta_sum2(double a, double b, double *sb) {
     }
     __syncthreads();
     return make_double2(sb[2 * NT], sb[2 * NT + 1]);
+}
+
+// The same sum, with fin(x, y) run by thread 0 on the result before the
+// closing barrier (the PCG's scalar recurrences: one thread evaluates the
+// divisions and square roots and publishes the outcome in shared memory).
+template <int NT, typename F>
+__device__ __forceinline__ void cta_sum2f(double a, double b, double *sb, F &&fin) {
+    sb[threadIdx.x] = a;
+    sb[NT + threadIdx.x] = b;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double xv[NT / 32], yv[NT / 32];
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) {
+            xv[k] = sb[lane + 32 * k];
+            yv[k] = sb[NT + lane + 32 * k];
+        }
+#pragma unroll
+        for (int h = NT / 64; h > 0; h >>= 1)
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                xv[k] += xv[k + h];
+                yv[k] += yv[k + h];
+            }
+        double x = xv[0], y = yv[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) fin(x, y);
+    }
+    __syncthreads();
 }
 
 template <typename T>
@@ -1078,15 +1112,25 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
         M.x[t] = 0.0;
     }
     __syncthreads();
-    double2 s0 = precond<T, NT>(M, d.nc);
-    s0 = cta_sum2<NT>(s0.x, s0.y, M.sb);
-    const double r0 = sqrt(s0.x);
-    double rho = s0.y, rho_prev = 0.0, rn = r0;
+    // scalar recurrences in thread 0 (see cta_sum2f): sc[0] holds beta or alpha,
+    // *go the continue flag
+    double *sc = M.sb + 2 * NT + 2;
+    int *go = reinterpret_cast<int *>(M.sb + 2 * NT + 3);
+    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;  // meaningful in thread 0
     int n = 0;
-    if (r0 > 0.0) {
+    {
+        const double2 s0 = precond<T, NT>(M, d.nc);
+        cta_sum2f<NT>(s0.x, s0.y, M.sb, [&](double x, double y) {
+            r0 = sqrt(x);
+            rho = y;
+            rn = r0;
+            *go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
+            sc[0] = 0.0;
+        });
+    }
+    if (*go) {
         for (;;) {
-            if (!isfinite(rho)) break;
-            const double beta = n == 0 ? 0.0 : rho / rho_prev;
+            const double beta = sc[0];
             double pq = 0.0;
             if (xs) {
                 for (int t = threadIdx.x; t < m9; t += NT) {
@@ -1119,21 +1163,29 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
                 pq = fma(M.p[t], q, pq);
             }
             }
-            pq = cta_sum2<NT>(pq, 0.0, M.sb).x;
-            if (!(pq > 0.0) || !isfinite(pq)) break;
-            const double alpha = rho / pq;
+            cta_sum2f<NT>(pq, 0.0, M.sb, [&](double x, double) {
+                const bool ok = x > 0.0 && isfinite(x);
+                *go = ok ? 1 : 0;
+                sc[0] = ok ? rho / x : 0.0;
+            });
+            if (!*go) break;
+            const double alpha = sc[0];
             for (int t = threadIdx.x; t < m9; t += NT) {
                 M.x[t] = fma(alpha, M.p[t], M.x[t]);
                 M.r[t] = fma(-alpha, M.q[t], M.r[t]);
             }
             __syncthreads();
-            double2 s = precond<T, NT>(M, d.nc);
-            s = cta_sum2<NT>(s.x, s.y, M.sb);
+            const double2 s = precond<T, NT>(M, d.nc);
             ++n;
-            rho_prev = rho;
-            rho = s.y;
-            rn = sqrt(s.x);
-            if (rn <= tol * r0 || n >= max_iter) break;
+            cta_sum2f<NT>(s.x, s.y, M.sb, [&](double x, double y) {
+                rho_prev = rho;
+                rho = y;
+                rn = sqrt(x);
+                const bool ok = !(rn <= tol * r0 || n >= max_iter) && isfinite(rho);
+                *go = ok ? 1 : 0;
+                sc[0] = ok ? rho / rho_prev : 0.0;
+            });
+            if (!*go) break;
         }
     }
     return n;

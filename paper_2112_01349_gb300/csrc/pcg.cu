@@ -732,18 +732,29 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
         ok = barrier();
     }
 
+    // The scalar recurrences (r0, rho, alpha, beta, the stopping test) run in
+    // thread 0 alone and are broadcast through shared memory: on this GPU each
+    // warp-wide FP64 instruction holds the SM's FP64 pipe for 16 cycles and a
+    // division or square root is a chain of about ten of them, so evaluating
+    // them redundantly in all 1024 threads would stall every CTA for microseconds.
+    __shared__ double s_alpha, s_beta;
+    __shared__ int s_go;
     int n = 0;
-    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;
+    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;  // meaningful in thread 0
     if (ok) {
         const double2 s0 = sum_parts2(part_rr, part_rho, G, sb);
-        r0 = sqrt(s0.x);
-        rho = s0.y;
-        rn = r0;
+        if (threadIdx.x == 0) {
+            r0 = sqrt(s0.x);
+            rho = s0.y;
+            rn = r0;
+            s_go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
+            s_beta = 0.0;
+        }
+        __syncthreads();
     }
-    if (ok && r0 > 0.0) {
+    if (ok && s_go) {
         for (;;) {
-            if (!isfinite(rho)) break;
-            const double beta = n == 0 ? 0.0 : rho / rho_prev;
+            const double beta = s_beta;
             double *p_cur = (n & 1) ? P.p2 : P.p;
             const double *p_prev = (n & 1) ? P.p : P.p2;
             T *pT_cur = (n & 1) ? (T *)P.pT2 : pT;
@@ -763,8 +774,14 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             }
             if (!(ok = barrier())) break;
             const double pq = sum_parts(part_pq, G, sb);
-            if (!(pq > 0.0) || !isfinite(pq)) break;
-            const double alpha = rho / pq;
+            if (threadIdx.x == 0) {
+                const bool go = (pq > 0.0) && isfinite(pq);
+                s_go = go ? 1 : 0;
+                s_alpha = go ? rho / pq : 0.0;
+            }
+            __syncthreads();
+            if (!s_go) break;
+            const double alpha = s_alpha;
             // x += alpha p; r -= alpha q; z = B~^-1 r; partial r.r and r.z, over this
             // CTA's own cameras (three per warp)
             {
@@ -802,11 +819,17 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             }
             if (!(ok = barrier())) break;
             ++n;
-            rho_prev = rho;
-            double2 sums = sum_parts2(part_rho, part_rr, G, sb);
-            rho = sums.x;
-            rn = sqrt(sums.y);
-            if (rn <= tol * r0 || n >= max_iter) break;
+            const double2 sums = sum_parts2(part_rho, part_rr, G, sb);
+            if (threadIdx.x == 0) {
+                rho_prev = rho;
+                rho = sums.x;
+                rn = sqrt(sums.y);
+                const bool go = !(rn <= tol * r0 || n >= max_iter) && isfinite(rho);
+                s_go = go ? 1 : 0;
+                s_beta = go ? rho / rho_prev : 0.0;
+            }
+            __syncthreads();
+            if (!s_go) break;
         }
     }
     if (!ok) atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
