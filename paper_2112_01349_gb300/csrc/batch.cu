@@ -30,11 +30,13 @@
 // Summation orders are fixed by the launch schedule (threads per CTA), so a
 // schedule gives the same bits on every run.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mba_internal.cuh"
@@ -1569,6 +1571,32 @@ mba_status build_graph(mba_batch *b) {
     return MBA_OK;
 }
 
+// Runs f(0..n-1) over the host's cores (dynamic claiming; each call of f
+// touches its own data).
+template <typename F>
+void parallel_for(int n, F &&f) {
+    unsigned hw = std::thread::hardware_concurrency();
+    int nt = (int)(hw ? hw : 4);
+    if (nt > 32) nt = 32;
+    if (nt > n) nt = n;
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt);
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&]() {
+            for (;;) {
+                const int i = next.fetch_add(1);
+                if (i >= n) break;
+                f(i);
+            }
+        });
+    for (auto &t : th) t.join();
+}
+
 bool finite_all(const double *a, int64_t m) {
     for (int64_t i = 0; i < m; ++i)
         if (!std::isfinite(a[i])) return false;
@@ -1614,38 +1642,49 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
         return api_fail(MBA_ERR_NONFINITE, "non-finite camera, point or observation");
 
     // ---- host layout: per window, stable point-major and camera-major orders ----
+    // Windows are independent and each writes its own ranges of the global
+    // arrays, so the work is spread over host threads (window by window).
     std::vector<int2> pm_pc((size_t)N);
     std::vector<double2> pm_uv((size_t)N);
     std::vector<int32_t> pm_orig((size_t)N), cm_pt((size_t)N), cm2pm((size_t)N), pm2cm((size_t)N),
         cam_ptr((size_t)NC + 1);
-    std::vector<int2> wchunk;
     std::vector<WinDesc> desc((size_t)nw);
-    wchunk.reserve((size_t)(N / 8 + 2 * nw + 16));
-    std::vector<int32_t> cntp, cntc, posp, posc, pmpos;
-    for (int w = 0; w < nw; ++w) {
+    std::vector<std::vector<int2>> wch_w((size_t)nw);   // warp chunks of each window (+ its end entry)
+    std::vector<std::vector<int32_t>> bcnt_w((size_t)nw);  // Schur-block pair offsets of each window
+    std::vector<int64_t> npairs_w((size_t)nw, 0);
+    std::vector<int> err_w((size_t)nw, 0);  // 0, or 1 + index into msgs
+    static const char *msgs[] = {"observation index out of its window's range", "a point without observations",
+                                 "a camera without observations"};
+    parallel_for(nw, [&](int w) {
         const int32_t c0 = (int32_t)cam_offsets[w], p0 = (int32_t)pt_offsets[w], o0 = (int32_t)obs_offsets[w];
         const int32_t nc = (int32_t)(cam_offsets[w + 1] - c0), np = (int32_t)(pt_offsets[w + 1] - p0),
                       n = (int32_t)(obs_offsets[w + 1] - o0);
-        cntp.assign((size_t)np + 1, 0);
-        cntc.assign((size_t)nc + 1, 0);
+        std::vector<int32_t> cntp((size_t)np + 1, 0), cntc((size_t)nc + 1, 0);
         for (int32_t k = 0; k < n; ++k) {
             const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
-            if (ci < 0 || ci >= nc || pi < 0 || pi >= np)
-                return api_fail(MBA_ERR_INVALID_ARG, "observation index out of its window's range");
+            if (ci < 0 || ci >= nc || pi < 0 || pi >= np) {
+                err_w[w] = 1;
+                return;
+            }
             cntp[pi + 1]++;
             cntc[ci + 1]++;
         }
         for (int32_t j = 0; j < np; ++j) {
-            if (cntp[j + 1] == 0) return api_fail(MBA_ERR_INVALID_ARG, "a point without observations");
+            if (cntp[j + 1] == 0) {
+                err_w[w] = 2;
+                return;
+            }
             cntp[j + 1] += cntp[j];
         }
         for (int32_t i = 0; i < nc; ++i) {
-            if (cntc[i + 1] == 0) return api_fail(MBA_ERR_INVALID_ARG, "a camera without observations");
+            if (cntc[i + 1] == 0) {
+                err_w[w] = 3;
+                return;
+            }
             cntc[i + 1] += cntc[i];
         }
-        posp.assign(cntp.begin(), cntp.end() - 1);
-        posc.assign(cntc.begin(), cntc.end() - 1);
-        pmpos.resize((size_t)n);
+        std::vector<int32_t> posp(cntp.begin(), cntp.end() - 1), posc(cntc.begin(), cntc.end() - 1),
+            pmpos((size_t)n);
         for (int32_t k = 0; k < n; ++k) {
             const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
             const int32_t pp = o0 + posp[pi]++;
@@ -1662,7 +1701,6 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
             pm2cm[pmpos[k]] = cp;
         }
         for (int32_t i = 0; i < nc; ++i) cam_ptr[c0 + i] = o0 + cntc[i];
-        // warp chunks: greedy runs of whole points with <= 32 observations
         WinDesc &d = desc[w];
         d.cam0 = c0;
         d.nc = nc;
@@ -1670,10 +1708,11 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
         d.np = np;
         d.obs0 = o0;
         d.n = n;
-        d.wch0 = (int32_t)wchunk.size();
+        // warp chunks: greedy runs of whole points with <= 32 observations
+        std::vector<int2> &wc = wch_w[w];
         int32_t j = 0;
         while (j < np) {
-            wchunk.push_back(make_int2(p0 + j, o0 + cntp[j]));
+            wc.push_back(make_int2(p0 + j, o0 + cntp[j]));
             int32_t len = cntp[j + 1] - cntp[j];
             ++j;
             if (len <= 32)
@@ -1682,67 +1721,75 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                     ++j;
                 }
         }
-        d.nwch = (int32_t)wchunk.size() - d.wch0;
-        wchunk.push_back(make_int2(p0 + np, o0 + n));
-        if ((int64_t)wchunk.size() >= (int64_t(1) << 31) - 64)
-            return api_fail(MBA_ERR_INVALID_ARG, "too many warp chunks");
-    }
+        d.nwch = (int32_t)wc.size();
+        wc.push_back(make_int2(p0 + np, o0 + n));
+        // Schur-block pair counts (explicit S~): for each point, every ordered
+        // pair (u, v) of its observations with camera(u) < camera(v), or with
+        // the same camera (all ordered pairs), goes to block (camera(u), camera(v))
+        const int32_t nb = nc * (nc + 1) / 2;
+        std::vector<int32_t> &bc = bcnt_w[w];
+        bc.assign((size_t)nb + 1, 0);
+        for (int32_t o = o0; o < o0 + n;) {
+            int32_t e = o;
+            while (e < o0 + n && pm_pc[e].x == pm_pc[o].x) ++e;
+            for (int32_t u = o; u < e; ++u)
+                for (int32_t v = o; v < e; ++v) {
+                    const int32_t cu = pm_pc[u].y - c0, cv = pm_pc[v].y - c0;
+                    if (cu <= cv) ++bc[cu * nc - (cu * (cu - 1)) / 2 + (cv - cu) + 1];
+                }
+            o = e;
+        }
+        for (int32_t q = 0; q < nb; ++q) bc[q + 1] += bc[q];
+        npairs_w[w] = bc[nb];
+    });
+    for (int w = 0; w < nw; ++w)
+        if (err_w[w]) return api_fail(MBA_ERR_INVALID_ARG, msgs[err_w[w] - 1]);
     cam_ptr[(size_t)NC] = (int32_t)N;
-    // Schur-block pair lists (explicit S~): for each point, every ordered pair
-    // (u, v) of its observations with camera(u) < camera(v), or with the same
-    // camera (all ordered pairs), goes to the list of block (camera(u),
-    // camera(v)); lists are in point order.  Skipped (explicit form not
-    // offered) when they would be too large.
+    std::vector<int2> wchunk;
+    {
+        int64_t tot = 0;
+        for (int w = 0; w < nw; ++w) tot += (int64_t)wch_w[w].size();
+        if (tot >= (int64_t(1) << 31) - 64) return api_fail(MBA_ERR_INVALID_ARG, "too many warp chunks");
+        wchunk.reserve((size_t)tot);
+        for (int w = 0; w < nw; ++w) {
+            desc[w].wch0 = (int32_t)wchunk.size();
+            wchunk.insert(wchunk.end(), wch_w[w].begin(), wch_w[w].end());
+            std::vector<int2>().swap(wch_w[w]);
+        }
+    }
+    // Schur-block pair lists, in point order inside each block (skipped, and the
+    // explicit form not offered, when they would be too large)
     std::vector<int4> pairs;
     std::vector<int32_t> blk_ptr;
-    bool explicit_ok = true;
-    {
-        int64_t total = 0;
-        for (int w = 0; w < nw && explicit_ok; ++w) {
+    int64_t total_pairs = 0;
+    for (int w = 0; w < nw; ++w) total_pairs += npairs_w[w];
+    const bool explicit_ok = total_pairs <= (int64_t(1) << 28);
+    if (explicit_ok) {
+        pairs.resize((size_t)total_pairs);
+        std::vector<int64_t> base_w((size_t)nw);
+        int64_t base = 0;
+        for (int w = 0; w < nw; ++w) {
+            desc[w].blk0 = (int32_t)blk_ptr.size();
+            for (const int32_t c : bcnt_w[w]) blk_ptr.push_back((int32_t)(base + c));
+            base_w[w] = base;
+            base += npairs_w[w];
+        }
+        parallel_for(nw, [&](int w) {
             const WinDesc &d = desc[w];
+            std::vector<int32_t> &pos = bcnt_w[w];
             for (int32_t o = d.obs0; o < d.obs0 + d.n;) {
                 int32_t e = o;
                 while (e < d.obs0 + d.n && pm_pc[e].x == pm_pc[o].x) ++e;
                 for (int32_t u = o; u < e; ++u)
-                    for (int32_t v = o; v < e; ++v)
-                        if (pm_pc[u].y <= pm_pc[v].y) ++total;
+                    for (int32_t v = o; v < e; ++v) {
+                        const int32_t cu = pm_pc[u].y - d.cam0, cv = pm_pc[v].y - d.cam0;
+                        if (cu > cv) continue;
+                        pairs[(size_t)(base_w[w] + pos[cu * d.nc - (cu * (cu - 1)) / 2 + (cv - cu)]++)] =
+                            make_int4(pm2cm[u], pm2cm[v], pm_pc[u].x, 0);
+                    }
                 o = e;
             }
-            if (total > (int64_t(1) << 28)) explicit_ok = false;
-        }
-        if (explicit_ok) {
-            pairs.resize((size_t)total);
-            std::vector<int32_t> bcnt;
-            int64_t base = 0;
-            for (int w = 0; w < nw; ++w) {
-                WinDesc &d = desc[w];
-                const int32_t nb = d.nc * (d.nc + 1) / 2;
-                auto blk = [&](int32_t i, int32_t k) { return i * d.nc - (i * (i - 1)) / 2 + (k - i); };
-                bcnt.assign((size_t)nb + 1, 0);
-                for (int pass = 0; pass < 2; ++pass) {
-                    for (int32_t o = d.obs0; o < d.obs0 + d.n;) {
-                        int32_t e = o;
-                        while (e < d.obs0 + d.n && pm_pc[e].x == pm_pc[o].x) ++e;
-                        for (int32_t u = o; u < e; ++u)
-                            for (int32_t v = o; v < e; ++v) {
-                                const int32_t cu = pm_pc[u].y - d.cam0, cv = pm_pc[v].y - d.cam0;
-                                if (cu > cv) continue;
-                                if (pass == 0) ++bcnt[blk(cu, cv) + 1];
-                                else
-                                    pairs[(size_t)(base + bcnt[blk(cu, cv)]++)] =
-                                        make_int4(pm2cm[u], pm2cm[v], pm_pc[u].x, 0);
-                            }
-                        o = e;
-                    }
-                    if (pass == 0) {
-                        for (int32_t q = 0; q < nb; ++q) bcnt[q + 1] += bcnt[q];
-                        d.blk0 = (int32_t)blk_ptr.size();
-                        for (int32_t q = 0; q <= nb; ++q) blk_ptr.push_back((int32_t)(base + bcnt[q]));
-                    }
-                }
-                base = blk_ptr.back();
-            }
-        }
+        });
     }
     std::vector<int32_t> order((size_t)nw);
     for (int w = 0; w < nw; ++w) order[w] = w;
