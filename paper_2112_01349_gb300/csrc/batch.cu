@@ -117,7 +117,7 @@ struct WinMem {
 // staged pair (Jc~ of the first observation, F = G Jc~ of the second; padded).
 template <typename T>
 struct Stage {
-    static constexpr int pairs = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int pairs = sizeof(T) == 4 ? 32 : 16;
     static constexpr int stride = 37;
 };
 
@@ -998,6 +998,30 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int blk_index(int i, int k, int nc) { return i * nc - (i * (i - 1)) / 2 + (k - i); }
 
+// 24 consecutive values (16-byte aligned) with vector loads
+template <typename T>
+__device__ __forceinline__ void ld24(const T *p, T *o);
+template <>
+__device__ __forceinline__ void ld24<float>(const float *p, float *o) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[q];
+        o[4 * q] = v.x;
+        o[4 * q + 1] = v.y;
+        o[4 * q + 2] = v.z;
+        o[4 * q + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void ld24<double>(const double *p, double *o) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[q];
+        o[2 * q] = v.x;
+        o[2 * q + 1] = v.y;
+    }
+}
+
 template <typename T, int NT>
 __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, double mu, int damping) {
     constexpr int NW = NT / 32;
@@ -1025,7 +1049,9 @@ __device__ void s_build(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d
             const int cnt = min(SP, p1 - base);
             if (lane < cnt) {
                 const int4 pr = __ldg(A.pairs + base + lane);
-                const T *J1 = Jcm + 24 * (int64_t)pr.x, *J2 = Jcm + 24 * (int64_t)pr.y;
+                T J1[24], J2[24];
+                ld24<T>(Jcm + 24 * (int64_t)pr.x, J1);
+                ld24<T>(Jcm + 24 * (int64_t)pr.y, J2);
                 T c[6];
                 ld_c<T>(Ci, pr.z, c);
                 T q0[3], q1[3];  // Q = Jp~_1 C~^-1 (2x3)
