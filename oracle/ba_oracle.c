@@ -480,6 +480,34 @@ static int damp(const lin_t *L, double mu, int damping, damped_t *D) {
     return ORC_OK;
 }
 
+/* Schur-Jacobi preconditioner (a solver variant beside Alg. 2's block-Jacobi
+ * on B~): the camera blocks S~_ii = B~_i - sum_k E_k C~_j(k)^-1 E_k^T over the
+ * observations k of camera i.  When every (camera, point) pair is observed at
+ * most once these are exactly the diagonal blocks of S = B~ - E C~^-1 E^T (Eq. 3).
+ * Their Cholesky factors replace those of B~ in D->Lb; a block that is not
+ * positive definite keeps the factor of B~_i.  Blocks are written to Sjd
+ * (nc*81) if it is not NULL. */
+static void schur_jacobi(const lin_t *L, damped_t *D, double *Sjd) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int32_t i = 0; i < L->nc; ++i) {
+        double S[81];
+        memcpy(S, D->Bd + 81 * (int64_t)i, sizeof(S));
+        for (int32_t s = L->cam_ptr[i]; s < L->cam_ptr[i + 1]; ++s) {
+            const int64_t k = L->cam_perm[s];
+            const double *Ek = L->E + 27 * k, *Ci = D->Cinv + 9 * (int64_t)L->pt_idx[k];
+            double EC[27];
+            matmul(Ek, Ci, EC, 9, 3, 3);
+            for (int a = 0; a < 9; ++a)
+                for (int b = 0; b < 9; ++b)
+                    S[a * 9 + b] -= EC[a * 3] * Ek[b * 3] + EC[a * 3 + 1] * Ek[b * 3 + 1] + EC[a * 3 + 2] * Ek[b * 3 + 2];
+        }
+        if (Sjd) memcpy(Sjd + 81 * (int64_t)i, S, sizeof(S));
+        double F[81];
+        memcpy(F, S, sizeof(F));
+        if (cholesky(F, 9)) memcpy(D->Lb + 81 * (int64_t)i, F, sizeof(F));
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Schur elimination (Eqs. 3, 4; Alg. 3).                                    */
 /* ------------------------------------------------------------------------ */
@@ -684,14 +712,27 @@ static double model_decrease(const lin_t *L, const double *dc, const double *dp,
 /* One damped step at the current linearisation: solve (H + mu D) dx = g by
  * Schur elimination.  schur_mode: 0 = PCG with the implicit product (Alg. 2+3),
  * 1 = PCG with the explicit dense S, 2 = dense Cholesky of S. */
+/* One damped solve.  precond: 0 block-Jacobi on B~ (Alg. 2), 1 Schur-Jacobi.
+ * g0n != NULL turns on the inexact-Newton forcing sequence: the PCG tolerance
+ * becomes max(pcg_tol, min(0.1, sqrt(|g| / |g_first|))), |g| the norm of this
+ * solve's reduced right-hand side and |g_first| that of the first solve
+ * (*g0n <= 0 on entry marks the first solve; it is then set). */
 static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, int pcg_max, double pcg_tol,
-                       double *dc, double *dp, int *pcg_iters, double *rel_res) {
+                       double *dc, double *dp, int *pcg_iters, double *rel_res, int precond, double *g0n) {
     damped_t D;
     int rc = damp(L, mu, damping, &D);
     if (rc) return rc;
+    if (precond == 1) schur_jacobi(L, &D, NULL);
     const int64_t m = 9 * (int64_t)L->nc;
     double *g = malloc(sizeof(double) * m), *sb = malloc(sizeof(double) * 3 * (size_t)L->np);
     schur_rhs(L, &D, g, sb);
+    if (g0n) {
+        const double gn = sqrt(vdot(g, g, m));
+        if (!(*g0n > 0.0)) *g0n = gn;
+        const double eta = *g0n > 0.0 ? sqrt(gn / *g0n) : 0.0;
+        const double t = eta < 0.1 ? eta : 0.1;
+        if (t > pcg_tol) pcg_tol = t;
+    }
     *pcg_iters = 0;
     if (rel_res) *rel_res = 0.0;
     if (schur_mode == 0) {
@@ -714,16 +755,34 @@ static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, i
 int orc_step(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
              const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
              int schur_mode, int pcg_max, double pcg_tol, double *dc, double *dp, int *pcg_iters, double *rel_res,
-             double *model_dec) {
+             double *model_dec, int precond) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
     linearise(&L, cams, pts, obs, loss, delta);
-    rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, pcg_iters, rel_res);
+    rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, pcg_iters, rel_res, precond, NULL);
     if (!rc && model_dec) {
         double *scr = malloc(sizeof(double) * n);
         *model_dec = model_decrease(&L, dc, dp, scr);
         free(scr);
+    }
+    lin_free(&L);
+    return rc;
+}
+
+/* Public: the Schur-Jacobi camera blocks S~_ii (nc*81, row-major) at damping mu. */
+int orc_schur_jacobi_blocks(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts,
+                            const double *obs, const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta,
+                            double mu, int damping, double *blocks) {
+    lin_t L;
+    int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
+    if (rc) return rc;
+    linearise(&L, cams, pts, obs, loss, delta);
+    damped_t D;
+    rc = damp(&L, mu, damping, &D);
+    if (!rc) {
+        schur_jacobi(&L, &D, blocks);
+        damped_free(&D);
     }
     lin_free(&L);
     return rc;
@@ -764,7 +823,7 @@ int orc_schur(int32_t nc, int32_t np, int64_t n, const double *cams, const doubl
 int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
                 const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
                 int pcg_max, double pcg_tol, const double *gbar_c, const double *gbar_p, double *grad_obs,
-                double *grad_c0, double *grad_p0, int *pcg_iters) {
+                double *grad_c0, double *grad_p0, int *pcg_iters, int precond) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
@@ -779,7 +838,7 @@ int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const dou
     memcpy(L.v, gbar_c, sizeof(double) * 9 * (size_t)nc);
     memcpy(L.w, gbar_p, sizeof(double) * 3 * (size_t)np);
     int it = 0;
-    rc = damped_step(&L, mu, damping, 0, pcg_max, pcg_tol, vc, vp, &it, NULL);
+    rc = damped_step(&L, mu, damping, 0, pcg_max, pcg_tol, vc, vp, &it, NULL, precond, NULL);
     if (!rc) {
         for (int64_t k = 0; k < n; ++k) {
             const double *Jc = L.Jc + 18 * k, *Jp = L.Jp + 6 * k;
@@ -820,7 +879,8 @@ typedef struct {
 int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, const double *obs,
                  const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, int max_iter, int pcg_max,
                  double pcg_tol, int damping, double initial_radius, double min_rel_dec, double function_tol,
-                 int schur_mode, orc_trace_t *trace, int *iterations, double *final_cost, double *final_radius) {
+                 int schur_mode, orc_trace_t *trace, int *iterations, double *final_cost, double *final_radius,
+                 int precond, int forcing) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
@@ -830,14 +890,15 @@ int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, c
     if (!cand_c || !cand_p || !dc || !dp || !scr) { rc = ORC_ERR_OOM; goto done; }
 
     double F = cost_only(n, cams, pts, obs, cam_idx, pt_idx, loss, delta, scr);
-    double radius = initial_radius, factor = 2.0;
+    double radius = initial_radius, factor = 2.0, g0n = 0.0;
     int relin = 1, it = 0;
     for (it = 0; it < max_iter; ++it) {
         if (relin) { linearise(&L, cams, pts, obs, loss, delta); relin = 0; }
         double mu = 1.0 / radius;
         int pcg_iters = 0;
         double rel_res = 0.0;
-        rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, &pcg_iters, &rel_res);
+        rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, &pcg_iters, &rel_res, precond,
+                         forcing ? &g0n : NULL);
         if (rc) goto done;
         double ldec = model_decrease(&L, dc, dp, scr);
         for (int64_t t = 0; t < 9 * (int64_t)nc; ++t) cand_c[t] = cams[t] + dc[t];

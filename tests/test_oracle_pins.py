@@ -293,3 +293,65 @@ def test_adjoint_matches_dense_implicit_function_gradient(loss):
     g0 = mu * d * v
     np.testing.assert_allclose(np.concatenate([r["grad_c0"].reshape(-1), r["grad_p0"].reshape(-1)]), g0,
                                atol=1e-8 * np.abs(g0).max())
+
+
+# ---------------------------------------------------------------------------
+# Schur-Jacobi preconditioner and forcing sequence (solver variants beside
+# Alg. 2's block-Jacobi preconditioner and fixed tolerance)
+# ---------------------------------------------------------------------------
+def test_schur_jacobi_blocks_are_the_diagonal_blocks_of_the_dense_complement():
+    """With every (camera, point) pair observed once, the Schur-Jacobi camera
+    blocks are the 9x9 diagonal blocks of S = B~ - E C~^-1 E^T formed densely."""
+    sc = make_scene(5, 60, track=("fixed", 3), sigma=1.0, seed=71)
+    mu = 1e-2
+    blocks = oracle.schur_jacobi_blocks(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu)
+    S = oracle.schur(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, dense=True)["S"]
+    for i in range(sc.nc):
+        np.testing.assert_allclose(blocks[i], S[9 * i:9 * i + 9, 9 * i:9 * i + 9], rtol=1e-12,
+                                   atol=1e-12 * np.abs(S).max())
+
+
+def _single_camera(sc, cam):
+    keep = sc.cam_idx == cam
+    pts_used = np.unique(sc.pt_idx[keep])
+    remap = -np.ones(sc.np_, dtype=np.int64)
+    remap[pts_used] = np.arange(len(pts_used))
+    return (sc.cameras[cam:cam + 1], sc.points[pts_used], sc.observations[keep],
+            np.zeros(int(keep.sum()), dtype=np.int32), remap[sc.pt_idx[keep]].astype(np.int32))
+
+
+def test_schur_jacobi_is_exact_for_one_camera():
+    """With one camera S has a single block, so the Schur-Jacobi preconditioner
+    is S^-1 and PCG stops after one step; block-Jacobi on B~ needs more."""
+    sc = make_scene(3, 80, track=("fixed", 2), sigma=1.0, seed=72)
+    prob = _single_camera(sc, 1)
+    sj = oracle.step(*prob, mu=1e-3, pcg_max=50, pcg_tol=1e-10, precond="schur_jacobi")
+    bj = oracle.step(*prob, mu=1e-3, pcg_max=50, pcg_tol=1e-10, precond="block_jacobi")
+    assert sj["pcg_iters"] == 1 and sj["rel_res"] < 1e-10
+    assert bj["pcg_iters"] > 1
+    np.testing.assert_allclose(sj["dc"], bj["dc"], rtol=1e-6, atol=1e-9 * np.abs(bj["dc"]).max())
+
+
+def test_schur_jacobi_step_equals_direct_solve():
+    sc = make_scene(6, 120, track=("geom", 0.25), sigma=1.0, seed=73)
+    mu = 1e-3
+    ref = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, schur="dense")
+    got = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, pcg_max=500, pcg_tol=1e-14,
+                      precond="schur_jacobi")
+    np.testing.assert_allclose(got["dc"], ref["dc"], rtol=1e-7, atol=1e-9 * np.abs(ref["dc"]).max())
+    np.testing.assert_allclose(got["dp"], ref["dp"], rtol=1e-7, atol=1e-9 * np.abs(ref["dp"]).max())
+
+
+def test_forcing_sequence_loosens_early_solves():
+    """Forcing tolerance max(tol, min(0.1, sqrt(|g_k| / |g_0|))): the first solve
+    stops at relative residual 0.1, the LM still lowers the cost monotonically."""
+    sc = make_scene(8, 300, track=("geom", 0.25), sigma=1.0, seed=74)
+    fixed = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=6, pcg_max=200)
+    forced = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=6, pcg_max=200,
+                             forcing=True)
+    t0 = forced["trace"][0]
+    assert t0["pcg_rel_res"] <= 0.1 and t0["pcg_rel_res"] > 1e-3
+    assert t0["pcg_iters"] < fixed["trace"][0]["pcg_iters"]
+    costs = [t["cost_new"] for t in forced["trace"] if t["accepted"]]
+    assert costs and all(b < a for a, b in zip(costs, costs[1:]))
+    assert forced["final_cost"] < forced["trace"][0]["cost"]
