@@ -54,6 +54,12 @@ typedef enum { MBA_LOSS_NONE = 0, MBA_LOSS_HUBER = 1 } mba_loss;
 /* Damping: DIAG adds mu * clamp(diag(H), 1e-6, 1e32) (the Ceres trust-region form the
  * supplement names); IDENTITY adds mu * I (the form written in Sec. 3). */
 typedef enum { MBA_DAMP_DIAG = 0, MBA_DAMP_IDENTITY = 1 } mba_damping;
+/* PCG preconditioner.  BLOCK_JACOBI: M = blockdiag(B~_i), as Alg. 2 writes it (default).
+ * SCHUR_JACOBI (solver variant, not in the paper): M = blockdiag(S~_ii) with
+ * S~_ii = B~_i - sum over the observations k of camera i of E_k C~^-1 E_k^T, the exact
+ * diagonal blocks of S when each (camera, point) pair is observed once; a block that is
+ * not positive definite falls back to B~_i.  Inverted in FP64 in both forms. */
+typedef enum { MBA_PRECOND_BLOCK_JACOBI = 0, MBA_PRECOND_SCHUR_JACOBI = 1 } mba_preconditioner;
 
 typedef struct {
     int32_t precision;   /* mba_precision.  FP32_MIXED: Jacobian, Hessian blocks and the
@@ -74,6 +80,11 @@ typedef struct {
     double function_tol;           /* > 0: stop after an accepted step with |dF|/F < tol; 0: run max_iter */
     int64_t barrier_spin_limit;    /* polls before a grid barrier gives up (MBA_ERR_TIMEOUT); 0 = default */
     int32_t collect_timing;        /* 1: fill the ms_* fields of mba_summary with CUDA-event times */
+    int32_t preconditioner;        /* mba_preconditioner (default BLOCK_JACOBI) */
+    int32_t forcing;               /* 1: inexact-Newton forcing sequence (solver variant): each solve's
+                                      PCG tolerance is max(pcg_rel_tol, min(0.1, sqrt(|g|/|g_1|))), |g| the
+                                      norm of its reduced right-hand side, |g_1| that of the solve's first
+                                      damped step; 0: pcg_rel_tol throughout (default) */
 } mba_solver_options;
 
 /* One LM iteration as recorded by mba_solve. */

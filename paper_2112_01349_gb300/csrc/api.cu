@@ -90,6 +90,8 @@ void mba_solver_options_default(mba_solver_options *o) {
     o->function_tol = 0.0;
     o->barrier_spin_limit = 0;
     o->collect_timing = 0;
+    o->preconditioner = MBA_PRECOND_BLOCK_JACOBI;
+    o->forcing = 0;
 }
 
 const char *mba_status_string(mba_status s) {
@@ -421,20 +423,22 @@ mba_status check_device_state(mba_problem *pr, DevState *hs) {
 }
 
 // linearise at the current parameters with mu, and form the damped blocks
-mba_status prepare_step(mba_problem *pr, double mu, int damping) {
+mba_status prepare_step(mba_problem *pr, double mu, int damping, int precond = MBA_PRECOND_BLOCK_JACOBI) {
     Prob &P = pr->P;
     cudaStream_t s = pr->stream;
     CK(launch_state_init(P, 1.0, mu, 0, s));
     CK(launch_camera_tables_forced(P, P.cams, s));
     CK(launch_linearize_impl(P, pr->cfirst, 1, s));
-    CK(launch_damp(P, damping, s));
+    CK(launch_damp(P, damping, precond, pr->cfirst, s));
     return MBA_OK;
 }
 
 bool valid_solver_opts(const mba_solver_options &o) {
     return o.max_iter >= 0 && o.pcg_max_iter >= 0 && o.pcg_rel_tol >= 0.0 &&
            (o.damping == MBA_DAMP_DIAG || o.damping == MBA_DAMP_IDENTITY) && o.initial_radius > 0.0 &&
-           o.function_tol >= 0.0 && o.barrier_spin_limit >= 0;
+           o.function_tol >= 0.0 && o.barrier_spin_limit >= 0 &&
+           (o.preconditioner == MBA_PRECOND_BLOCK_JACOBI || o.preconditioner == MBA_PRECOND_SCHUR_JACOBI) &&
+           (o.forcing == 0 || o.forcing == 1);
 }
 
 }  // namespace
@@ -583,7 +587,7 @@ mba_status mba_step(mba_problem *pr, double mu, const mba_solver_options *opt, d
     if (!valid_solver_opts(o) || !(mu >= 0.0)) return fail(MBA_ERR_INVALID_ARG, "bad solver options or mu");
     Prob &P = pr->P;
     cudaStream_t s = pr->stream;
-    mba_status st = prepare_step(pr, mu, o.damping);
+    mba_status st = prepare_step(pr, mu, o.damping, o.preconditioner);
     if (st) return st;
     const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
     CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
@@ -628,9 +632,9 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         CK(launch_camera_tables(P, P.cams, true, s));
         CK(launch_linearize_impl(P, pr->cfirst, 0, s));
         CK(rec(2 + 4 * it));
-        CK(launch_damp(P, o.damping, s));
+        CK(launch_damp(P, o.damping, o.preconditioner, pr->cfirst, s));
         CK(rec(3 + 4 * it));
-        CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+        CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s, o.forcing));
         CK(rec(4 + 4 * it));
         CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
         CK(launch_camera_tables(P, P.cams_new, false, s));
@@ -642,7 +646,7 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
     // state_init, camera table, 2 cost kernels; per iteration: camera table, 3
     // linearisation, 2 damping, PCG, 3 back-substitution, camera table, 2 cost,
     // LM update, accept
-    const int launches = 4 + 15 * o.max_iter;
+    const int launches = 4 + (15 + (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI ? 2 : 0)) * o.max_iter;
     DevState hs;
     mba_status st = check_device_state(pr, &hs);
     if (summary) {
@@ -696,7 +700,7 @@ mba_status mba_adjoint(mba_problem *pr, const mba_solver_options *opt, double mu
     if (!(mu >= 0.0)) return fail(MBA_ERR_INVALID_ARG, "mu < 0 and no accepted step of a previous solve");
     Prob &P = pr->P;
     cudaStream_t s = pr->stream;
-    mba_status st = prepare_step(pr, mu, o.damping);
+    mba_status st = prepare_step(pr, mu, o.damping, o.preconditioner);
     if (st) return st;
     // right-hand side gbar in place of the gradient (v for cameras, w for points)
     CK(cudaMemcpyAsync(P.v, grad_cameras, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyHostToDevice, s));

@@ -2012,6 +2012,8 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
     if (o.max_iter < 0 || o.pcg_max_iter < 0 || !(o.pcg_rel_tol >= 0.0) || !(o.initial_radius > 0.0) ||
         (o.damping != MBA_DAMP_DIAG && o.damping != MBA_DAMP_IDENTITY))
         return api_fail(MBA_ERR_INVALID_ARG, "bad solver options");
+    if (o.preconditioner != MBA_PRECOND_BLOCK_JACOBI || o.forcing != 0)
+        return api_fail(MBA_ERR_INVALID_ARG, "batched windows use the block-Jacobi preconditioner and a fixed tolerance");
     if (adj && (!adj->grad_cameras || !adj->grad_points || adj->pcg_max_iter < 0 || !(adj->pcg_rel_tol >= 0.0)))
         return api_fail(MBA_ERR_INVALID_ARG, "bad adjoint arguments");
     cudaStream_t s = b->stream;

@@ -36,6 +36,7 @@ struct DevState {
     double pcg_rel_res;
     double mu_override;   // >= 0: use this mu instead of 1/radius
     double mu_accepted;   // mu of the last accepted step (the step that produced the current x)
+    double g0;            // norm of the first reduced right-hand side of the solve (forcing sequence)
     int32_t relin;        // 1: the linearisation must be rebuilt before the next solve
     int32_t accepted;     // decision of the last iteration
     int32_t done;         // 1: stop issuing work (function_tol met or error)
@@ -370,9 +371,9 @@ cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_
 
 // pcg.cu
 enum PcgMode { PCG_SOLVE = 0, PCG_RHS_ONLY = 1, PCG_MATVEC = 2 };
-cudaError_t launch_damp(const Prob &P, int damping, cudaStream_t s);
+cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *cfirst, cudaStream_t s);
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
-                       cudaStream_t s);
+                       cudaStream_t s, int forcing = 0);
 int pcg_grid_size(const Prob &P);
 void plan_pcg_smem(Prob &P);
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s);

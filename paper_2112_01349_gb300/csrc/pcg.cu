@@ -109,6 +109,131 @@ __global__ void damp_points_kernel(Prob P, int damping) {
 }
 
 // ---------------------------------------------------------------------------
+// Schur-Jacobi preconditioner (solver variant): S~_ii = B~_i - sum_k
+// Jc~_k^T G_k Jc~_k over the observations k of camera i, G_k = Jp~_k C~_j^-1
+// Jp~_k^T (2x2).  Camera-major chunks recompute the Jacobian (as the
+// linearisation's camera pass does) and write 45 packed chunk sums; each
+// camera then subtracts its chunk sums from B~_i in chunk order and, if the
+// result is positive definite, replaces the preconditioner block by its
+// inverse (Cholesky, FP64).  Otherwise B~_i^-1 stays.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
+    if (P.st->done) return;
+    __shared__ T ctab[kCamTab];
+    __shared__ double red[kWarps][45];
+    const T *__restrict__ camtab = (const T *)P.camtab;
+    const T *__restrict__ Ci = (const T *)P.Cinv;
+    const T delta = (T)P.delta;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = blockIdx.x; c < P.n_cchunks; c += gridDim.x) {
+        const int cam = P.cchunk_cam[c];
+        const int b0 = P.cchunk_beg[c], b1 = P.cchunk_beg[c + 1];
+        __syncthreads();
+        if (threadIdx.x < kCamTab) ctab[threadIdx.x] = camtab[(int64_t)cam * kCamTab + threadIdx.x];
+        __syncthreads();
+        T acc[45];
+#pragma unroll
+        for (int q = 0; q < 45; ++q) acc[q] = T(0);
+        for (int s = b0 + threadIdx.x; s < b1; s += kBlock) {
+            const int pt = P.cm_pt[s];
+            const double2 uv = P.cm_uv[s];
+            T e[2], Jc[18], Jp[6];
+            project<T, true>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+                             (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+            T rho, W;
+            loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+            T c6[6], q0[3], q1[3];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) c6[q] = Ci[6 * (int64_t)pt + q];
+            // Q = Jp C~^-1 (rows), G = W^2 Q Jp^T
+            q0[0] = c6[0] * Jp[0] + c6[1] * Jp[1] + c6[2] * Jp[2];
+            q0[1] = c6[1] * Jp[0] + c6[3] * Jp[1] + c6[4] * Jp[2];
+            q0[2] = c6[2] * Jp[0] + c6[4] * Jp[1] + c6[5] * Jp[2];
+            q1[0] = c6[0] * Jp[3] + c6[1] * Jp[4] + c6[2] * Jp[5];
+            q1[1] = c6[1] * Jp[3] + c6[3] * Jp[4] + c6[4] * Jp[5];
+            q1[2] = c6[2] * Jp[3] + c6[4] * Jp[4] + c6[5] * Jp[5];
+            const T w2 = W * W;
+            const T g00 = w2 * (q0[0] * Jp[0] + q0[1] * Jp[1] + q0[2] * Jp[2]);
+            const T g01 = w2 * (q0[0] * Jp[3] + q0[1] * Jp[4] + q0[2] * Jp[5]);
+            const T g11 = w2 * (q1[0] * Jp[3] + q1[1] * Jp[4] + q1[2] * Jp[5]);
+            T F0[9], F1[9];
+#pragma unroll
+            for (int b = 0; b < 9; ++b) {
+                F0[b] = g00 * Jc[b] + g01 * Jc[9 + b];
+                F1[b] = g01 * Jc[b] + g11 * Jc[9 + b];
+            }
+            int idx = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = a; b < 9; ++b) acc[idx++] += Jc[a] * F0[b] + Jc[9 + a] * F1[b];
+        }
+#pragma unroll
+        for (int q = 0; q < 45; ++q) {
+            T v = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[wid][q] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 45) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+            P.cpart[54 * (int64_t)c + threadIdx.x] = s;
+        }
+    }
+}
+
+__global__ void sj_finalize_kernel(Prob P, const int32_t *__restrict__ cfirst) {
+    if (P.st->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nc; i += gridDim.x * blockDim.x) {
+        double A[81];
+        for (int q = 0; q < 81; ++q) A[q] = P.Bd[81 * (int64_t)i + q];
+        for (int a = 0; a < 9; ++a)
+            for (int b = a; b < 9; ++b) {
+                double s = 0.0;
+                for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) s += P.cpart[54 * (int64_t)c + sym9(a, b)];
+                A[a * 9 + b] -= s;
+                if (b != a) A[b * 9 + a] -= s;
+            }
+        bool ok = true;
+        double il[9];
+        for (int j = 0; j < 9 && ok; ++j) {
+            double s = A[j * 9 + j];
+            for (int k = 0; k < j; ++k) s -= A[j * 9 + k] * A[j * 9 + k];
+            if (!(s > 0.0) || !isfinite(s)) {
+                ok = false;
+                break;
+            }
+            const double l = sqrt(s);
+            il[j] = 1.0 / l;
+            A[j * 9 + j] = l;
+            for (int r = j + 1; r < 9; ++r) {
+                double t = A[r * 9 + j];
+                for (int k = 0; k < j; ++k) t -= A[r * 9 + k] * A[j * 9 + k];
+                A[r * 9 + j] = t * il[j];
+            }
+        }
+        if (!ok) continue;  // keep B~_i^-1
+        for (int col = 0; col < 9; ++col) {
+            double y[9];
+            for (int r = 0; r < 9; ++r) {
+                double s = (r == col) ? 1.0 : 0.0;
+                for (int k = 0; k < r; ++k) s -= A[r * 9 + k] * y[k];
+                y[r] = s * il[r];
+            }
+            for (int r = 8; r >= 0; --r) {
+                double s = y[r];
+                for (int k = r + 1; k < 9; ++k) s -= A[k * 9 + r] * y[k];
+                y[r] = s * il[r];
+            }
+            for (int r = 0; r < 9; ++r) P.Binv[81 * (int64_t)i + r * 9 + col] = y[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // shared pieces of the point-major passes
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -671,7 +796,7 @@ __device__ __forceinline__ double sum_parts(const double *parts, int n, double *
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
-    pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin) {
+    pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin, int forcing) {
     using T2 = typename V2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double sb[64];
@@ -741,12 +866,19 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     __shared__ int s_go;
     int n = 0;
     double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;  // meaningful in thread 0
+    // forcing sequence: the first solve's right-hand side norm as it was before
+    // this launch (written below by block 0 only, after the last barrier)
+    const double g0 = forcing ? st->g0 : 0.0;
     if (ok) {
         const double2 s0 = sum_parts2(part_rr, part_rho, G, sb);
         if (threadIdx.x == 0) {
             r0 = sqrt(s0.x);
             rho = s0.y;
             rn = r0;
+            if (forcing) {
+                const double eta = fmin(0.1, sqrt(r0 / (g0 > 0.0 ? g0 : r0)));
+                tol = fmax(tol, eta);
+            }
             s_go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
             s_beta = 0.0;
         }
@@ -836,6 +968,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
         st->pcg_iters = n;
         st->pcg_rel_res = r0 > 0.0 ? rn / r0 : 0.0;
+        if (forcing && !(g0 > 0.0)) st->g0 = r0;
     }
 }
 
@@ -948,12 +1081,18 @@ bool g_pcg_attr[2] = {false, false};
 
 }  // namespace
 
-cudaError_t launch_damp(const Prob &P, int damping, cudaStream_t s) {
+cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *cfirst, cudaStream_t s) {
     damp_cameras_kernel<<<(P.nc + 127) / 128, 128, 0, s>>>(P, damping);
     const int64_t nb = (P.np + kBlock - 1) / kBlock;
     const unsigned g = (unsigned)(nb > 152 * 16 ? 152 * 16 : nb);
     if (P.fp32) damp_points_kernel<float><<<g, kBlock, 0, s>>>(P, damping);
     else damp_points_kernel<double><<<g, kBlock, 0, s>>>(P, damping);
+    if (precond == MBA_PRECOND_SCHUR_JACOBI) {
+        const unsigned gc = (unsigned)(P.n_cchunks < 152 * 4 ? (P.n_cchunks > 0 ? P.n_cchunks : 1) : 152 * 4);
+        if (P.fp32) sj_camera_kernel<float><<<gc, kBlock, 0, s>>>(P);
+        else sj_camera_kernel<double><<<gc, kBlock, 0, s>>>(P);
+        sj_finalize_kernel<<<(P.nc + 63) / 64, 64, 0, s>>>(P, cfirst);
+    }
     return cudaGetLastError();
 }
 
@@ -991,13 +1130,13 @@ int pcg_grid_size(const Prob &P) {
 }
 
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
-                       cudaStream_t s) {
+                       cudaStream_t s, int forcing) {
     const size_t smem = (size_t)P.pcg_smem;
     // the barrier targets count arrivals from zero in every launch
     cudaError_t e = cudaMemsetAsync(&P.st->barrier, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     Prob Pc = P;
-    void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit};
+    void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit, (void *)&forcing};
     if (P.fp32)
         return cudaLaunchCooperativeKernel((const void *)pcg_kernel<float>, dim3(grid), dim3(pcg_block(P)), args, smem,
                                            s);

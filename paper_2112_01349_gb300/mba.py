@@ -24,6 +24,8 @@ MBA_DAMP_DIAG, MBA_DAMP_IDENTITY = 0, 1
 PRECISION = {"fp64": MBA_FP64, "fp32": MBA_FP32_MIXED, "fp32_mixed": MBA_FP32_MIXED}
 LOSS = {"none": MBA_LOSS_NONE, "huber": MBA_LOSS_HUBER}
 DAMPING = {"diag": MBA_DAMP_DIAG, "identity": MBA_DAMP_IDENTITY}
+MBA_PRECOND_BLOCK_JACOBI, MBA_PRECOND_SCHUR_JACOBI = 0, 1
+PRECONDITIONER = {"block_jacobi": MBA_PRECOND_BLOCK_JACOBI, "schur_jacobi": MBA_PRECOND_SCHUR_JACOBI}
 
 
 class MbaError(RuntimeError):
@@ -40,7 +42,8 @@ class ProblemOptions(C.Structure):
 class SolverOptions(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("pcg_max_iter", C.c_int32), ("pcg_rel_tol", C.c_double),
                 ("damping", C.c_int32), ("initial_radius", C.c_double), ("min_relative_decrease", C.c_double),
-                ("function_tol", C.c_double), ("barrier_spin_limit", C.c_int64), ("collect_timing", C.c_int32)]
+                ("function_tol", C.c_double), ("barrier_spin_limit", C.c_int64), ("collect_timing", C.c_int32),
+                ("preconditioner", C.c_int32), ("forcing", C.c_int32)]
 
 
 class Iteration(C.Structure):
@@ -230,6 +233,10 @@ def solver_options(**kw) -> SolverOptions:
     for k, v in kw.items():
         if k == "damping" and isinstance(v, str):
             v = DAMPING[v]
+        if k == "preconditioner" and isinstance(v, str):
+            v = PRECONDITIONER[v]
+        if k == "forcing":
+            v = int(bool(v))
         if not hasattr(o, k):
             raise TypeError(f"unknown solver option {k}")
         setattr(o, k, v)
