@@ -59,6 +59,7 @@ struct WinDesc {
 struct BatchOpts {
     int32_t max_iter, pcg_max_iter, damping, adjoint, adj_pcg_max, explicit_schur;
     double pcg_tol, initial_radius, min_rel_dec, function_tol, adj_pcg_tol, adj_mu;
+    int32_t precond, forcing;  // mba_preconditioner; 1: forcing sequence for the forward solves
 };
 
 struct BatchArgs {
@@ -161,6 +162,7 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
 // Per-window control state (shared, written by thread 0 between barriers).
 struct WinState {
     double radius, factor, mu, F, F0, Fn, ldec, mu_acc;
+    double g0;  // norm of the window's first reduced right-hand side (forcing sequence)
     int32_t win, relin, done, iter, acc_total, pcg_total, status, accept, adj_iters, pad;
 };
 
@@ -1123,12 +1125,57 @@ __device__ void s_matvec(const BatchArgs &A, const WinMem<T> &M, const WinDesc &
     }
 }
 
+// Schur-Jacobi preconditioner (solver variant) from the explicit S~: the
+// inverse (Cholesky, FP64) of each diagonal block replaces B~_i^-1; a block that
+// is not positive definite keeps B~_i^-1.  One thread per camera.
+template <typename T, int NT>
+__device__ void sj_from_s(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d) {
+    const T *S = M.S ? M.S : (const T *)A.S + A.smax * (int64_t)blockIdx.x;
+    for (int i = threadIdx.x; i < d.nc; i += NT) {
+        const T *Sb = S + 81 * (int64_t)blk_index(i, i, d.nc);
+        double L[81], il[9];
+        for (int q = 0; q < 81; ++q) L[q] = (double)Sb[q];
+        bool ok = true;
+        for (int j = 0; j < 9 && ok; ++j) {
+            double s = L[j * 9 + j];
+            for (int k = 0; k < j; ++k) s -= L[j * 9 + k] * L[j * 9 + k];
+            if (!(s > 0.0) || !isfinite(s)) {
+                ok = false;
+                break;
+            }
+            const double l = sqrt(s);
+            il[j] = 1.0 / l;
+            L[j * 9 + j] = l;
+            for (int r = j + 1; r < 9; ++r) {
+                double t = L[r * 9 + j];
+                for (int k = 0; k < j; ++k) t -= L[r * 9 + k] * L[j * 9 + k];
+                L[r * 9 + j] = t * il[j];
+            }
+        }
+        if (!ok) continue;
+        for (int col = 0; col < 9; ++col) {
+            double y[9];
+            for (int r = 0; r < 9; ++r) {
+                double s = (r == col) ? 1.0 : 0.0;
+                for (int k = 0; k < r; ++k) s -= L[r * 9 + k] * y[k];
+                y[r] = s * il[r];
+            }
+            for (int r = 8; r >= 0; --r) {
+                double s = y[r];
+                for (int k = r + 1; k < 9; ++k) s -= L[k * 9 + r] * y[k];
+                y[r] = s * il[r];
+            }
+            for (int r = col; r < 9; ++r) M.BinvT[45 * i + sym9(col, r)] = (T)y[r];
+        }
+    }
+}
+
 // PCG of Alg. 2 on S x = g, g = vvec - E C~^-1 wvec (Sec. 3 Eq. 3), x0 = 0;
 // leaves x in M.x and returns the iteration count.  The product S p is the
 // implicit two-pass form of Alg. 3, or the explicit S~ of s_build.
 template <typename T, int NT>
 __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *vvec, const double *wvec,
-                   double mu, int damping, int max_iter, double tol, bool xs) {
+                   double mu, int damping, int max_iter, double tol, bool xs, double *g0) {
     const int m9 = 9 * d.nc;
     rhs_points<T, NT>(A, M, d, wvec);
     __syncthreads();
@@ -1152,6 +1199,10 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
             r0 = sqrt(x);
             rho = y;
             rn = r0;
+            if (g0) {  // forcing sequence: tol = max(tol, min(0.1, sqrt(|g| / |g_first|)))
+                if (!(*g0 > 0.0)) *g0 = r0;
+                tol = fmax(tol, fmin(0.1, *g0 > 0.0 ? sqrt(r0 / *g0) : 0.0));
+            }
             *go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
             sc[0] = 0.0;
         });
@@ -1278,6 +1329,7 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
         S.status = MBA_OK;
         S.accept = 0;
         S.adj_iters = 0;
+        S.g0 = 0.0;
     }
     __syncthreads();
     for (int i = tid; i < d.nc; i += NT) {
@@ -1313,9 +1365,13 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
         if (O.explicit_schur) {
             s_build<T, NT>(A, M, d, mu, O.damping);
             __syncthreads();
+            if (O.precond == MBA_PRECOND_SCHUR_JACOBI) {
+                sj_from_s<T, NT>(A, M, d);
+                __syncthreads();
+            }
         }
         const int np_ = pcg<T, NT>(A, M, d, M.v, A.wv, mu, O.damping, O.pcg_max_iter, O.pcg_tol,
-                                   O.explicit_schur != 0);
+                                   O.explicit_schur != 0, O.forcing ? &S.g0 : nullptr);
         make_pv<T, NT>(M, M.x, d.nc);
         __syncthreads();
         double ld = back_points<T, NT>(A, M, d, A.wv, false);
@@ -1375,9 +1431,13 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
                 if (O.explicit_schur) {
                     s_build<T, NT>(A, M, d, mu, O.damping);
                     __syncthreads();
+                    if (O.precond == MBA_PRECOND_SCHUR_JACOBI) {
+                        sj_from_s<T, NT>(A, M, d);
+                        __syncthreads();
+                    }
                 }
                 const int na = pcg<T, NT>(A, M, d, A.gbar_c + 9 * (int64_t)d.cam0, A.gbar_p, mu, O.damping,
-                                          O.adj_pcg_max, O.adj_pcg_tol, O.explicit_schur != 0);
+                                          O.adj_pcg_max, O.adj_pcg_tol, O.explicit_schur != 0, nullptr);
                 make_pv<T, NT>(M, M.x, d.nc);
                 __syncthreads();
                 back_points<T, NT>(A, M, d, A.gbar_p, true);
@@ -2012,8 +2072,11 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
     if (o.max_iter < 0 || o.pcg_max_iter < 0 || !(o.pcg_rel_tol >= 0.0) || !(o.initial_radius > 0.0) ||
         (o.damping != MBA_DAMP_DIAG && o.damping != MBA_DAMP_IDENTITY))
         return api_fail(MBA_ERR_INVALID_ARG, "bad solver options");
-    if (o.preconditioner != MBA_PRECOND_BLOCK_JACOBI || o.forcing != 0)
-        return api_fail(MBA_ERR_INVALID_ARG, "batched windows use the block-Jacobi preconditioner and a fixed tolerance");
+    if ((o.preconditioner != MBA_PRECOND_BLOCK_JACOBI && o.preconditioner != MBA_PRECOND_SCHUR_JACOBI) ||
+        (o.forcing != 0 && o.forcing != 1))
+        return api_fail(MBA_ERR_INVALID_ARG, "bad preconditioner or forcing option");
+    if (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI && !b->explicit_ok)
+        return api_fail(MBA_ERR_INVALID_ARG, "the Schur-Jacobi preconditioner needs the explicit Schur form");
     if (adj && (!adj->grad_cameras || !adj->grad_points || adj->pcg_max_iter < 0 || !(adj->pcg_rel_tol >= 0.0)))
         return api_fail(MBA_ERR_INVALID_ARG, "bad adjoint arguments");
     cudaStream_t s = b->stream;
@@ -2029,7 +2092,10 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
     bo.function_tol = o.function_tol;
     bo.adj_pcg_tol = adj ? adj->pcg_rel_tol : 0.0;
     bo.adj_mu = adj ? adj->mu : -1.0;
-    bo.explicit_schur = b->schur == 2 ? 1 : 0;
+    // the Schur-Jacobi blocks come from the explicit S~, so that variant runs the explicit form
+    bo.explicit_schur = (b->schur == 2 || o.preconditioner == MBA_PRECOND_SCHUR_JACOBI) ? 1 : 0;
+    bo.precond = o.preconditioner;
+    bo.forcing = o.forcing;
     BCK(cudaMemcpyAsync(b->opts, &bo, sizeof(bo), cudaMemcpyHostToDevice, s));
     if (adj) {
         BCK(cudaMemcpyAsync(b->gbar_c, adj->grad_cameras, 72 * (size_t)b->nc, cudaMemcpyHostToDevice, s));

@@ -203,3 +203,27 @@ def test_full_batch_sampled_windows(mba):
     for w in [int(order[0]), int(order[255]), int(order[-1]), 7]:
         ref = _oracle_solve(ws[w])
         rel_close(sm[w]["final_cost"], ref["final_cost"], 1e-4, f"window {w}")
+
+
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
+def test_batch_schur_jacobi_matches_oracle(mba, schur):
+    """Schur-Jacobi preconditioner (solver variant) per window; it runs the
+    explicit form whatever the schedule."""
+    ws = _small(count=6, seed=61)
+    with mba.Batch(_tuples(ws), precision="fp64") as b:
+        b.set_schedule(schur=schur)
+        r = b.solve(preconditioner="schur_jacobi", **OPTS)
+    for w, s in enumerate(ws):
+        ref = _oracle_solve(s, precond="schur_jacobi")
+        rel_close(r["summaries"][w]["final_cost"], ref["final_cost"], 1e-6, f"window {w} final cost")
+        assert r["summaries"][w]["accepted"] == sum(t["accepted"] for t in ref["trace"])
+
+
+def test_batch_forcing_matches_oracle(mba):
+    ws = _small(count=6, seed=62)
+    with mba.Batch(_tuples(ws), precision="fp64") as b:
+        r = b.solve(forcing=1, **OPTS)
+    for w, s in enumerate(ws):
+        ref = _oracle_solve(s, forcing=True)
+        rel_close(r["summaries"][w]["final_cost"], ref["final_cost"], 1e-6, f"window {w} final cost")
+        assert abs(r["summaries"][w]["pcg_iters_total"] - sum(t["pcg_iters"] for t in ref["trace"])) <= 4
