@@ -61,6 +61,15 @@ typedef enum { MBA_DAMP_DIAG = 0, MBA_DAMP_IDENTITY = 1 } mba_damping;
  * not positive definite falls back to B~_i.  Inverted in FP64 in both forms. */
 typedef enum { MBA_PRECOND_BLOCK_JACOBI = 0, MBA_PRECOND_SCHUR_JACOBI = 1 } mba_preconditioner;
 
+/* Source of the residuals and Jacobians (Sec. 3.2).  ANALYTIC: the hand-derived chain
+ * rule of the BAL camera (the paper's "-m" form, default).  AUTODIFF: the edge is
+ * written once as a functor over a generic scalar and evaluated on forward-mode
+ * dual numbers (mba_jet.cuh), which yields the value and both Jacobian blocks (the
+ * paper's "-a" form).  Both give the same Jacobian up to rounding; AUTODIFF costs
+ * more arithmetic per linearisation and, in FP32_MIXED, an extra stored camera-major
+ * Jacobian (72 bytes per observation) for the PCG camera pass. */
+typedef enum { MBA_JACOBIAN_ANALYTIC = 0, MBA_JACOBIAN_AUTODIFF = 1 } mba_jacobian;
+
 typedef struct {
     int32_t precision;   /* mba_precision.  FP32_MIXED: Jacobian, Hessian blocks and the
                             PCG Schur product in FP32; block inversions, PCG dot
@@ -68,6 +77,8 @@ typedef struct {
     int32_t loss;        /* mba_loss; cost F = 1/2 sum rho(|e|^2) (Eq. 1 with Sigma = I) */
     double huber_delta;  /* Huber threshold in pixels (MBA_LOSS_HUBER) */
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream */
+    int32_t jacobian;    /* mba_jacobian (default ANALYTIC); batches accept ANALYTIC only */
+    int32_t pad;
 } mba_problem_options;
 
 typedef struct {

@@ -36,7 +36,9 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [HEADER]
+    inc = os.path.dirname(HEADER)
+    deps = (sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] +
+            [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith((".h", ".cuh"))])
     return any(os.path.getmtime(d) > t for d in deps)
 
 

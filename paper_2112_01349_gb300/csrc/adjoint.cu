@@ -24,7 +24,7 @@ __device__ __forceinline__ double damp_diag(int damping, double d) {
 // dL/du_k = W_k (Jc_k v_c + Jp_k v_p) for a slice of observations in the
 // caller's order; the Jacobian and W are recomputed at x* in the problem's
 // precision, the product is accumulated in FP64.
-template <typename T>
+template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) adjoint_obs_kernel(Prob P, const int32_t *__restrict__ ci,
                                                               const int32_t *__restrict__ pi,
                                                               const double2 *__restrict__ uvs, int64_t m,
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kBlock) adjoint_obs_kernel(Prob P, const int32
         const int cam = ci[k], pt = pi[k];
         const double2 uv = uvs[k];
         T e[2], Jc[18], Jp[6];
-        project<T, true>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+        edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
         T rho, W;
         loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
@@ -76,8 +76,14 @@ cudaError_t launch_adjoint_obs(const Prob &P, const int32_t *ci, const int32_t *
     int64_t g = (m + kBlock - 1) / kBlock;
     if (g > 152 * 16) g = 152 * 16;
     if (g < 1) g = 1;
-    if (P.fp32) adjoint_obs_kernel<float><<<(unsigned)g, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
-    else adjoint_obs_kernel<double><<<(unsigned)g, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
+    const unsigned gu = (unsigned)g;
+    if (P.fp32) {
+        if (P.autodiff) adjoint_obs_kernel<float, true><<<gu, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
+        else adjoint_obs_kernel<float, false><<<gu, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
+    } else {
+        if (P.autodiff) adjoint_obs_kernel<double, true><<<gu, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
+        else adjoint_obs_kernel<double, false><<<gu, kBlock, 0, s>>>(P, ci, pi, uv, m, out);
+    }
     return cudaGetLastError();
 }
 

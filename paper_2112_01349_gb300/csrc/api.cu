@@ -77,6 +77,8 @@ void mba_problem_options_default(mba_problem_options *o) {
     o->loss = MBA_LOSS_NONE;
     o->huber_delta = 0.0;
     o->cuda_stream = nullptr;
+    o->jacobian = MBA_JACOBIAN_ANALYTIC;
+    o->pad = 0;
 }
 
 void mba_solver_options_default(mba_solver_options *o) {
@@ -132,6 +134,8 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     if (o.precision != MBA_FP64 && o.precision != MBA_FP32_MIXED) return fail(MBA_ERR_INVALID_ARG, "bad precision");
     if (o.loss != MBA_LOSS_NONE && o.loss != MBA_LOSS_HUBER) return fail(MBA_ERR_INVALID_ARG, "bad loss");
     if (o.loss == MBA_LOSS_HUBER && !(o.huber_delta > 0.0)) return fail(MBA_ERR_INVALID_ARG, "huber_delta must be > 0");
+    if (o.jacobian != MBA_JACOBIAN_ANALYTIC && o.jacobian != MBA_JACOBIAN_AUTODIFF)
+        return fail(MBA_ERR_INVALID_ARG, "bad jacobian source");
 
     mba_problem *pr = new mba_problem();
     Prob &P = pr->P;
@@ -145,6 +149,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     P.fp32 = o.precision == MBA_FP32_MIXED;
     P.loss = o.loss;
     P.delta = o.huber_delta;
+    P.autodiff = o.jacobian == MBA_JACOBIAN_AUTODIFF;
     const size_t w = P.fp32 ? 4 : 8;
     const int64_t pbound = (n + 512) / 513 + 2;                 // point chunks (stride >= 513)
     const int64_t cbound = n / kCamChunk + (int64_t)nc + 2;     // camera chunks
@@ -210,11 +215,15 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
         P.cm2pm = c.take<int32_t>(n);
-        P.Xcm = P.fp32 ? c.take<float4>((size_t)P.npad) : nullptr;
+        // camera-major copies for the PCG camera pass: the stored Jacobian (FP64, or
+        // FP32-mixed with dual numbers), else the point and sqrt(W) (analytic FP32)
+        const bool f32_chain = P.fp32 && !P.autodiff;
+        P.Xcm = f32_chain ? c.take<float4>((size_t)P.npad) : nullptr;
         P.zT = P.fp32 ? c.take<float>((size_t)nc * kVec) : nullptr;
         P.pT2 = c.take<char>((size_t)nc * kVec * w);
-        P.swc = (P.fp32 && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
+        P.swc = (f32_chain && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
         P.Jcm = P.fp32 ? nullptr : c.take<double>(18 * (size_t)P.npad);
+        P.JcmT = P.fp32 ? (P.autodiff ? (void *)c.take<float>(18 * (size_t)P.npad) : nullptr) : (void *)P.Jcm;
         P.dp = c.take<double>(3 * (size_t)np);
         P.red = c.take<double>(red_len);
         pr->part_a = c.take<double>(8192);

@@ -41,7 +41,7 @@ __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc,
     }
 }
 
-template <typename T>
+template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
             const int cam = P.pm_cam[o], pt = P.pm_pt[o];
             const double2 uv = P.pm_uv[o];
             T e[2], Jc[18], Jp[6];
-            project<T, true>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
+            edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
                              (T)P.pts[3 * (int64_t)pt + 1], (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc,
                              Jp);
             T rho, W;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
     }
 }
 
-template <typename T>
+template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
     __shared__ T ctab[kCamTab];
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             const int pt = P.cm_pt[s];
             const double2 uv = P.cm_uv[s];
             T e[2], Jc[18], Jp[6];
-            project<T, true>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
-                             (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+            edge_eval<T, AD, true, false>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+                                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);
@@ -140,13 +140,15 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             for (int q = 0; q < 18; ++q) Jc[q] *= sw;
             e[0] *= sw;
             e[1] *= sw;
-            // copies the PCG camera pass reads in camera-major order
-            if (sizeof(T) == 8 && P.Jcm) {
+            // copies the PCG camera pass reads in camera-major order: the stored
+            // Jacobian (FP64, or any dual-number Jacobian), else the point and
+            // sqrt(W) from which the FP32 pass re-derives Jc~^T s
+            if ((sizeof(T) == 8 || AD) && P.JcmT) {
 #pragma unroll
-                for (int q = 0; q < 18; ++q) P.Jcm[(int64_t)q * P.npad + s] = (double)Jc[q];
+                for (int q = 0; q < 18; ++q) ((T *)P.JcmT)[(int64_t)q * P.npad + s] = Jc[q];
             }
-            if (sizeof(T) == 4 && P.swc) ((float *)P.swc)[s] = (float)sw;
-            if (sizeof(T) == 4 && P.Xcm)
+            if (sizeof(T) == 4 && !AD && P.swc) ((float *)P.swc)[s] = (float)sw;
+            if (sizeof(T) == 4 && !AD && P.Xcm)
                 ((float4 *)P.Xcm)[s] = make_float4((float)P.pts[3 * (int64_t)pt], (float)P.pts[3 * (int64_t)pt + 1],
                                                    (float)P.pts[3 * (int64_t)pt + 2], 0.f);
             int idx = 0;
@@ -186,6 +188,7 @@ __global__ void cam_finalize_kernel(Prob P, const int32_t *__restrict__ cfirst, 
 }
 
 // FP64 cost over the point-major observations; fixed grid and order.
+template <bool AD>
 __global__ void __launch_bounds__(kBlock) cost_partial_kernel(Prob P, const double *__restrict__ pts,
                                                                double *__restrict__ partial, int gate) {
     __shared__ double sred[kWarps];
@@ -195,8 +198,8 @@ __global__ void __launch_bounds__(kBlock) cost_partial_kernel(Prob P, const doub
         const int cam = P.pm_cam[o], pt = P.pm_pt[o];
         const double2 uv = P.pm_uv[o];
         double e[2];
-        project<double, false>(P.camtab64 + (int64_t)cam * kCamTab, pts[3 * (int64_t)pt], pts[3 * (int64_t)pt + 1],
-                               pts[3 * (int64_t)pt + 2], uv.x, uv.y, e, nullptr, nullptr);
+        edge_residual<double, AD>(P.camtab64 + (int64_t)cam * kCamTab, pts[3 * (int64_t)pt],
+                                  pts[3 * (int64_t)pt + 1], pts[3 * (int64_t)pt + 2], uv.x, uv.y, e);
         double rho, W;
         loss_weight<double>(P.loss, P.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
         acc += rho;
@@ -218,7 +221,7 @@ __global__ void cost_final_kernel(const double *__restrict__ partial, int nb, do
     }
 }
 
-template <typename T>
+template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) evaluate_slice_kernel(Prob P, const int32_t *__restrict__ ci,
                                                                  const int32_t *__restrict__ pi,
                                                                  const double2 *__restrict__ uvs, int64_t m,
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) evaluate_slice_kernel(Prob P, const in
         const int cam = ci[k], pt = pi[k];
         const double2 uv = uvs[k];
         T e[2], Jc[18], Jp[6];
-        project<T, true>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+        edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
         eo[2 * k] = (double)e[0];
         eo[2 * k + 1] = (double)e[1];
@@ -266,26 +269,27 @@ cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaS
     return cudaGetLastError();
 }
 
-static bool g_attr_done[2] = {false, false};
+template <typename T, bool AD>
+static void launch_lin_pair(const Prob &P, int force, cudaStream_t s) {
+    static bool attr_done = false;
+    const int nb = 152 * 4;
+    const size_t sm = sizeof(T) * 9 * (size_t)P.cap;
+    if (!attr_done) {
+        cudaFuncSetAttribute(lin_point_kernel<T, AD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(9 * sizeof(T) * 2048));
+        attr_done = true;
+    }
+    lin_point_kernel<T, AD><<<nb, kBlock, sm, s>>>(P, force);
+    lin_camera_kernel<T, AD><<<nb, kBlock, 0, s>>>(P, force);
+}
 
 cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s) {
-    const int nb = 152 * 4;
     if (P.fp32) {
-        const size_t sm = sizeof(float) * 9 * (size_t)P.cap;
-        if (!g_attr_done[0]) {
-            cudaFuncSetAttribute(lin_point_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 4 * 2048);
-            g_attr_done[0] = true;
-        }
-        lin_point_kernel<float><<<nb, kBlock, sm, s>>>(P, force);
-        lin_camera_kernel<float><<<nb, kBlock, 0, s>>>(P, force);
+        if (P.autodiff) launch_lin_pair<float, true>(P, force, s);
+        else launch_lin_pair<float, false>(P, force, s);
     } else {
-        const size_t sm = sizeof(double) * 9 * (size_t)P.cap;
-        if (!g_attr_done[1]) {
-            cudaFuncSetAttribute(lin_point_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 8 * 2048);
-            g_attr_done[1] = true;
-        }
-        lin_point_kernel<double><<<nb, kBlock, sm, s>>>(P, force);
-        lin_camera_kernel<double><<<nb, kBlock, 0, s>>>(P, force);
+        if (P.autodiff) launch_lin_pair<double, true>(P, force, s);
+        else launch_lin_pair<double, false>(P, force, s);
     }
     cam_finalize_kernel<<<grid_for((int64_t)P.nc * 54), kBlock, 0, s>>>(P, cfirst, force);
     return cudaGetLastError();
@@ -294,7 +298,8 @@ cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int forc
 cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, double *out, double *out2, int gate,
                              cudaStream_t s) {
     const int nb = cost_grid(P);
-    cost_partial_kernel<<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
+    if (P.autodiff) cost_partial_kernel<true><<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
+    else cost_partial_kernel<false><<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
     cost_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, out, out2, P.st, gate);
     return cudaGetLastError();
 }
@@ -302,8 +307,13 @@ cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, 
 cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_t *pi, const double2 *uv, int64_t m,
                                   double *e, double *jc, double *jp, cudaStream_t s) {
     const unsigned g = grid_for(m);
-    if (P.fp32) evaluate_slice_kernel<float><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
-    else evaluate_slice_kernel<double><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+    if (P.fp32) {
+        if (P.autodiff) evaluate_slice_kernel<float, true><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+        else evaluate_slice_kernel<float, false><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+    } else {
+        if (P.autodiff) evaluate_slice_kernel<double, true><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+        else evaluate_slice_kernel<double, false><<<g, kBlock, 0, s>>>(P, ci, pi, uv, m, e, jc, jp);
+    }
     return cudaGetLastError();
 }
 

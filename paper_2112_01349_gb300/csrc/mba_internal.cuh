@@ -9,6 +9,7 @@
 #include <cfloat>
 
 #include "../../include/mba.h"
+#include "edge_bal.cuh"
 
 namespace mba {
 
@@ -102,6 +103,9 @@ struct Prob {
     void *pT2;      // FP32-mixed: second float search-direction buffer (alternate iterations)
     void *swc;      // FP32-mixed with a loss: [npad] sqrt(W) in camera-major order
     double *Jcm;    // FP64: [18][npad] sqrt(W)-scaled camera Jacobian, camera-major
+    void *JcmT;     // [18][npad] sqrt(W)-scaled camera Jacobian in T, camera-major, that the PCG
+                    // camera pass reads: Jcm in FP64; FP32-mixed with autodiff only (else null)
+    int32_t autodiff;  // 1: every Jacobian comes from the edge functor on dual numbers
     // per-solve data
     double *Bd;     // [nc][81] damped B~
     double *Binv;   // [nc][81] inverse of B~ (block-Jacobi preconditioner)
@@ -135,7 +139,8 @@ __host__ __device__ __forceinline__ int sym3(int a, int b) {
 // the factor M of dP/dw = -R [X]_x M, M = (w w^T + (R^T - I)[w]_x) / |w|^2
 // (Gallego & Yezzi 2015) are tabulated in FP64; for |w|^2 <= DBL_EPSILON the
 // first-order form P = X + w x X + t is used (R = I + [w]_x, dP/dw = -[X]_x).
-// Table row: R[9] M[9] t[3] f k1 k2 small pad...
+// Table row: R[9] M[9] t[3] f k1 k2 small w[3] (w: the raw angle-axis, read by
+// the dual-number path, which evaluates the edge functor from the parameters).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void camera_table_row(const double *c, double *o) {
     const double w0 = c[0], w1 = c[1], w2 = c[2];
@@ -175,7 +180,7 @@ __device__ __forceinline__ void camera_table_row(const double *c, double *o) {
     for (int i = 0; i < 9; ++i) { o[i] = R[i]; o[9 + i] = M[i]; }
     o[18] = c[3]; o[19] = c[4]; o[20] = c[5];
     o[21] = c[6]; o[22] = c[7]; o[23] = c[8];
-    o[24] = small; o[25] = 0.0; o[26] = 0.0; o[27] = 0.0;
+    o[24] = small; o[25] = w0; o[26] = w1; o[27] = w2;
 }
 
 // Correctly rounded reciprocal (the same value as 1 / x, without the divide routine).
@@ -232,6 +237,41 @@ __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T 
         Jc[r * 9 + 7] = f * r2 * pr;
         Jc[r * 9 + 8] = f * r2 * r2 * pr;
     }
+}
+
+// Residual and Jacobians of one observation from either source: the analytic
+// chain rule (project) or the edge functor on dual numbers (AD), whose camera
+// parameters come from the table row (w at 25..27, t, f, k1, k2 at 18..23).
+// CAM / PT select the Jacobian blocks the dual-number path forms (kJetK
+// directions per pass); the analytic path forms both.
+constexpr int kJetK = 12;
+template <typename T, bool AD, bool CAM = true, bool PT = true>
+__device__ __forceinline__ void edge_eval(const T *__restrict__ ct, T X0, T X1, T X2, T u0, T u1, T *e, T *Jc,
+                                          T *Jp) {
+    if (!AD) {
+        project<T, true>(ct, X0, X1, X2, u0, u1, e, Jc, Jp);
+        return;
+    }
+    const T cam[9] = {ct[25], ct[26], ct[27], ct[18], ct[19], ct[20], ct[21], ct[22], ct[23]};
+    const T X[3] = {X0, X1, X2};
+    T pix[2];
+    jet_jacobian<(CAM && PT) ? kJetK : (CAM ? 9 : 3), CAM, PT>(BalEdge{}, cam, X, pix, Jc, Jp);
+    e[0] = pix[0] - u0;
+    e[1] = pix[1] - u1;
+}
+// Residual only.
+template <typename T, bool AD>
+__device__ __forceinline__ void edge_residual(const T *__restrict__ ct, T X0, T X1, T X2, T u0, T u1, T *e) {
+    if (!AD) {
+        project<T, false>(ct, X0, X1, X2, u0, u1, e, nullptr, nullptr);
+        return;
+    }
+    const T cam[9] = {ct[25], ct[26], ct[27], ct[18], ct[19], ct[20], ct[21], ct[22], ct[23]};
+    const T X[3] = {X0, X1, X2};
+    T pix[2];
+    BalEdge{}(cam, X, pix);
+    e[0] = pix[0] - u0;
+    e[1] = pix[1] - u1;
 }
 
 // Loss: rho(s) and IRLS weight rho'(s).  Plain: s, 1.  Huber: s, 1 for

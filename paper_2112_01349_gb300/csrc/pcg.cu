@@ -117,7 +117,7 @@ __global__ void damp_points_kernel(Prob P, int damping) {
 // result is positive definite, replaces the preconditioner block by its
 // inverse (Cholesky, FP64).  Otherwise B~_i^-1 stays.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
     if (P.st->done) return;
     __shared__ T ctab[kCamTab];
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
             const int pt = P.cm_pt[s];
             const double2 uv = P.cm_uv[s];
             T e[2], Jc[18], Jp[6];
-            project<T, true>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
+            edge_eval<T, AD>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
                              (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
@@ -456,28 +456,11 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
     }
 }
 
-// y = Jc~^T s for one camera-major observation.  FP32: from the camera table and
-// the observation's point by the transposed chain rule, without forming Jc:
-// v = D^T s is the translation block (D = d(pixel)/dP), y_w = M^T (X x (R^T v))
-// (X x v in the first-order branch), y_f = d (p.s), y_k1 = f |p|^2 (p.s),
-// y_k2 = f |p|^4 (p.s); s is scaled by sqrt(W) first.  FP64: the stored
-// camera-major Jacobian.
-template <typename T>
-__device__ __forceinline__ void camera_y(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *y);
-template <typename T>
-__device__ __forceinline__ void camera_acc(const Prob &P, const T *ct, int64_t s, T s0, T s1, T *acc);
-__device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, float s1, float *y);
-template <>
-__device__ __forceinline__ void camera_y<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
-                                                float *y) {
-    const float4 X = __ldcs((const float4 *)P.Xcm + s);
-    if (P.loss != MBA_LOSS_NONE) {
-        const float sw = __ldcs((const float *)P.swc + s);
-        s0 *= sw;
-        s1 *= sw;
-    }
-    camera_y_x(ct, X, s0, s1, y);
-}
+// y = Jc~^T s for one camera-major observation of the analytic FP32 form, from
+// the camera table and the observation's point by the transposed chain rule,
+// without forming Jc: v = D^T s is the translation block (D = d(pixel)/dP),
+// y_w = M^T (X x (R^T v)) (X x v in the first-order branch), y_f = d (p.s),
+// y_k1 = f |p|^2 (p.s), y_k2 = f |p|^4 (p.s); s arrives scaled by sqrt(W).
 __device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, float s1, float *y) {
     const float P0 = ct[0] * X.x + ct[1] * X.y + ct[2] * X.z + ct[18];
     const float P1 = ct[3] * X.x + ct[4] * X.y + ct[5] * X.z + ct[19];
@@ -511,21 +494,14 @@ __device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, 
     y[7] = f * r2 * pss;
     y[8] = f * r2 * r2 * pss;
 }
-template <>
-__device__ __forceinline__ void camera_acc<float>(const Prob &P, const float *ct, int64_t s, float s0, float s1,
-                                                  float *acc) {
-    float y[9];
-    camera_y<float>(P, ct, s, s0, s1, y);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) acc[a] += y[a];
-}
-// FP64: acc += Jc~^T s as 18 fused multiply-adds on the stored camera-major Jc~
-template <>
-__device__ __forceinline__ void camera_acc<double>(const Prob &P, const double *ct, int64_t s, double s0, double s1,
-                                                   double *acc) {
+// Stored form (FP64, and FP32-mixed with dual-number Jacobians): acc += Jc~^T s
+// as 18 fused multiply-adds on the stored camera-major Jc~ (sqrt(W) included).
+template <typename T>
+__device__ __forceinline__ void camera_acc_stored(const Prob &P, int64_t s, T s0, T s1, T *acc) {
+    const T *__restrict__ Jc = (const T *)P.JcmT;
 #pragma unroll
     for (int a = 0; a < 9; ++a)
-        acc[a] = fma(__ldcs(P.Jcm + a * P.npad + s), s0, fma(__ldcs(P.Jcm + (9 + a) * P.npad + s), s1, acc[a]));
+        acc[a] = fma(__ldcs(Jc + a * P.npad + s), s0, fma(__ldcs(Jc + (9 + a) * P.npad + s), s1, acc[a]));
 }
 
 enum CamMode { CAM_RHS = 0, CAM_ITER = 1, CAM_MATVEC = 2 };
@@ -541,7 +517,7 @@ __device__ __forceinline__ double2 cta_sum2(double x, double y, bool warp_data, 
 // timing.  CAM_RHS: g = v - c, x = 0, r = g, z = B~^-1 g; returns this CTA's
 // (r.r, r.z).  CAM_ITER: p = z + beta p_prev (p = z first), q = B~ p - c;
 // returns (p.q, 0).  CAM_MATVEC: q = B~ p - c with p given.
-template <typename T, int MODE>
+template <typename T, int MODE, bool JS>
 __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, const double *p_prev, double *p_cur,
                                T *pT_cur, double beta, bool first, double *cslot, double *sb) {
     using T2 = typename V2<T>::type;
@@ -563,7 +539,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
     for (int k = k0 + wid; k < k1;) {
         const int cam = P.cchunk_cam[k];
         const int b0 = P.cchunk_beg[k], b1 = P.cchunk_beg[k + 1];
-        if (sizeof(T) == 4 && cam != loaded) {
+        if (sizeof(T) == 4 && !JS && cam != loaded) {
             __syncwarp();
             if (lane < kCamTab) ct[lane] = __ldg(camtab + (int64_t)cam * kCamTab + lane);
             __syncwarp();
@@ -582,7 +558,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 const int s = s0 + u * 32 + lane;
                 const bool in = s < b1;
                 pm[u] = in ? __ldcs(P.cm2pm + s) : -1;
-                if (sizeof(T) == 4) {
+                if (sizeof(T) == 4 && !JS) {
                     X[u] = in ? __ldcs((const float4 *)P.Xcm + s) : make_float4(0.f, 0.f, -1.f, 0.f);
                     sw[u] = (in && P.loss != MBA_LOSS_NONE) ? __ldcs((const float *)P.swc + s) : 1.f;
                 }
@@ -594,13 +570,13 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (pm[u] >= 0) {
-                    if (sizeof(T) == 4) {
+                    if (sizeof(T) == 4 && !JS) {
                         float y[9];
                         camera_y_x((const float *)ct, X[u], (float)sv[u].x * sw[u], (float)sv[u].y * sw[u], y);
 #pragma unroll
                         for (int a = 0; a < 9; ++a) acc[a] += (T)y[a];
                     } else {
-                        camera_acc<T>(P, ct, s0 + u * 32 + lane, sv[u].x, sv[u].y, acc);
+                        camera_acc_stored<T>(P, s0 + u * 32 + lane, (T)sv[u].x, (T)sv[u].y, acc);
                     }
                 }
             }
@@ -794,7 +770,9 @@ __device__ __forceinline__ double sum_parts(const double *parts, int n, double *
 // ---------------------------------------------------------------------------
 // persistent PCG kernel (cooperative launch, one CTA per SM for the whole solve)
 // ---------------------------------------------------------------------------
-template <typename T>
+// JS: the camera pass reads the stored camera-major Jacobian (always in FP64;
+// in FP32-mixed when the Jacobian comes from dual numbers).
+template <typename T, bool JS>
 __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin, int forcing) {
     using T2 = typename V2<T>::type;
@@ -802,6 +780,11 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     __shared__ double sb[64];
     DevState *st = P.st;
     if (st->done) return;
+    // forcing sequence: the first solve's right-hand side norm as it was before
+    // this launch, read before the first grid barrier (block 0 writes it after
+    // the last one)
+    __shared__ double s_g0;
+    if (threadIdx.x == 0) s_g0 = forcing ? st->g0 : 0.0;
     uint32_t epoch = 0;
     const int G = gridDim.x;
     const int nwarp = blockDim.x >> 5;
@@ -840,7 +823,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
         }
         point_pass<T, false>(P, ps, pT, sbuf);
         if (!barrier()) return;
-        camera_pass<T, CAM_MATVEC>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
+        camera_pass<T, CAM_MATVEC, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         return;
     }
 
@@ -848,7 +831,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     point_pass<T, true>(P, nullptr, nullptr, sbuf);
     ok = barrier();
     if (ok) {
-        const double2 d = camera_pass<T, CAM_RHS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
+        const double2 d = camera_pass<T, CAM_RHS, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         if (mode == PCG_RHS_ONLY) return;
         if (threadIdx.x == 0) {
             stcg(part_rr + blockIdx.x, d.x);
@@ -862,24 +845,25 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     // warp-wide FP64 instruction holds the SM's FP64 pipe for 16 cycles and a
     // division or square root is a chain of about ten of them, so evaluating
     // them redundantly in all 1024 threads would stall every CTA for microseconds.
-    __shared__ double s_alpha, s_beta;
+    // Thread 0's state (r0, rho, |r|, the stopping threshold) also lives in
+    // shared memory, so that no register stays reserved for it through the loop.
+    __shared__ double s_alpha, s_beta, s_r0, s_rho, s_rn, s_stop;
     __shared__ int s_go;
     int n = 0;
-    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;  // meaningful in thread 0
-    // forcing sequence: the first solve's right-hand side norm as it was before
-    // this launch (written below by block 0 only, after the last barrier)
-    const double g0 = forcing ? st->g0 : 0.0;
     if (ok) {
         const double2 s0 = sum_parts2(part_rr, part_rho, G, sb);
         if (threadIdx.x == 0) {
-            r0 = sqrt(s0.x);
-            rho = s0.y;
-            rn = r0;
-            if (forcing) {
-                const double eta = fmin(0.1, sqrt(r0 / (g0 > 0.0 ? g0 : r0)));
-                tol = fmax(tol, eta);
+            const double r0 = sqrt(s0.x);
+            double t = tol;
+            if (forcing) {  // eta = min(0.1, sqrt(|g| / |g_first|)), |g_first| = r0 in the first solve
+                const double g0 = s_g0;
+                t = fmax(t, fmin(0.1, sqrt(r0 / (g0 > 0.0 ? g0 : r0))));
             }
-            s_go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
+            s_r0 = r0;
+            s_rho = s0.y;
+            s_rn = r0;
+            s_stop = t * r0;
+            s_go = (r0 > 0.0 && isfinite(s0.y)) ? 1 : 0;
             s_beta = 0.0;
         }
         __syncthreads();
@@ -900,7 +884,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             point_pass<T, false>(P, ps, pT, sbuf);
             if (!(ok = barrier())) break;
             {
-                const double2 d = camera_pass<T, CAM_ITER>(P, sbuf, p_prev, p_cur, sizeof(T) == 4 ? pT_cur : nullptr,
+                const double2 d = camera_pass<T, CAM_ITER, JS>(P, sbuf, p_prev, p_cur, sizeof(T) == 4 ? pT_cur : nullptr,
                                                            beta, n == 0, cslot, sb);
                 if (threadIdx.x == 0) stcg(part_pq + blockIdx.x, d.x);
             }
@@ -909,7 +893,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             if (threadIdx.x == 0) {
                 const bool go = (pq > 0.0) && isfinite(pq);
                 s_go = go ? 1 : 0;
-                s_alpha = go ? rho / pq : 0.0;
+                s_alpha = go ? s_rho / pq : 0.0;
             }
             __syncthreads();
             if (!s_go) break;
@@ -953,10 +937,10 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             ++n;
             const double2 sums = sum_parts2(part_rho, part_rr, G, sb);
             if (threadIdx.x == 0) {
-                rho_prev = rho;
-                rho = sums.x;
-                rn = sqrt(sums.y);
-                const bool go = !(rn <= tol * r0 || n >= max_iter) && isfinite(rho);
+                const double rho_prev = s_rho, rho = sums.x, rn = sqrt(sums.y);
+                s_rho = rho;
+                s_rn = rn;
+                const bool go = !(rn <= s_stop || n >= max_iter) && isfinite(rho);
                 s_go = go ? 1 : 0;
                 s_beta = go ? rho / rho_prev : 0.0;
             }
@@ -967,8 +951,8 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     if (!ok) atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
     if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
         st->pcg_iters = n;
-        st->pcg_rel_res = r0 > 0.0 ? rn / r0 : 0.0;
-        if (forcing && !(g0 > 0.0)) st->g0 = r0;
+        st->pcg_rel_res = s_r0 > 0.0 ? s_rn / s_r0 : 0.0;
+        if (forcing && !(s_g0 > 0.0)) st->g0 = s_r0;
     }
 }
 
@@ -1089,8 +1073,13 @@ cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *
     else damp_points_kernel<double><<<g, kBlock, 0, s>>>(P, damping);
     if (precond == MBA_PRECOND_SCHUR_JACOBI) {
         const unsigned gc = (unsigned)(P.n_cchunks < 152 * 4 ? (P.n_cchunks > 0 ? P.n_cchunks : 1) : 152 * 4);
-        if (P.fp32) sj_camera_kernel<float><<<gc, kBlock, 0, s>>>(P);
-        else sj_camera_kernel<double><<<gc, kBlock, 0, s>>>(P);
+        if (P.fp32) {
+            if (P.autodiff) sj_camera_kernel<float, true><<<gc, kBlock, 0, s>>>(P);
+            else sj_camera_kernel<float, false><<<gc, kBlock, 0, s>>>(P);
+        } else {
+            if (P.autodiff) sj_camera_kernel<double, true><<<gc, kBlock, 0, s>>>(P);
+            else sj_camera_kernel<double, false><<<gc, kBlock, 0, s>>>(P);
+        }
         sj_finalize_kernel<<<(P.nc + 63) / 64, 64, 0, s>>>(P, cfirst);
     }
     return cudaGetLastError();
@@ -1111,6 +1100,11 @@ void plan_pcg_smem(Prob &P) {
 
 int pcg_block(const Prob &P) { return P.fp32 ? PcgBlock<float>::value : PcgBlock<double>::value; }
 
+static const void *pcg_fn(const Prob &P) {
+    if (!P.fp32) return (const void *)pcg_kernel<double, true>;
+    return P.autodiff ? (const void *)pcg_kernel<float, true> : (const void *)pcg_kernel<float, false>;
+}
+
 // One CTA per SM (the camera partition is built for exactly that many);
 // returns 0 if the kernel cannot be resident with its shared memory.
 int pcg_grid_size(const Prob &P) {
@@ -1119,13 +1113,9 @@ int pcg_grid_size(const Prob &P) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = (size_t)P.pcg_smem;
     int blocks = 0;
-    if (P.fp32) {
-        cudaFuncSetAttribute(pcg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<float>, pcg_block(P), smem);
-    } else {
-        cudaFuncSetAttribute(pcg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pcg_kernel<double>, pcg_block(P), smem);
-    }
+    const void *fn = pcg_fn(P);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, pcg_block(P), smem);
     return blocks >= 1 ? sms : 0;
 }
 
@@ -1137,10 +1127,7 @@ cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long l
     if (e != cudaSuccess) return e;
     Prob Pc = P;
     void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit, (void *)&forcing};
-    if (P.fp32)
-        return cudaLaunchCooperativeKernel((const void *)pcg_kernel<float>, dim3(grid), dim3(pcg_block(P)), args, smem,
-                                           s);
-    return cudaLaunchCooperativeKernel((const void *)pcg_kernel<double>, dim3(grid), dim3(pcg_block(P)), args, smem, s);
+    return cudaLaunchCooperativeKernel(pcg_fn(P), dim3(grid), dim3(pcg_block(P)), args, smem, s);
 }
 
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s) {

@@ -26,6 +26,8 @@ LOSS = {"none": MBA_LOSS_NONE, "huber": MBA_LOSS_HUBER}
 DAMPING = {"diag": MBA_DAMP_DIAG, "identity": MBA_DAMP_IDENTITY}
 MBA_PRECOND_BLOCK_JACOBI, MBA_PRECOND_SCHUR_JACOBI = 0, 1
 PRECONDITIONER = {"block_jacobi": MBA_PRECOND_BLOCK_JACOBI, "schur_jacobi": MBA_PRECOND_SCHUR_JACOBI}
+MBA_JACOBIAN_ANALYTIC, MBA_JACOBIAN_AUTODIFF = 0, 1
+JACOBIAN = {"analytic": MBA_JACOBIAN_ANALYTIC, "autodiff": MBA_JACOBIAN_AUTODIFF}
 
 
 class MbaError(RuntimeError):
@@ -36,7 +38,7 @@ class MbaError(RuntimeError):
 
 class ProblemOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("loss", C.c_int32), ("huber_delta", C.c_double),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("jacobian", C.c_int32), ("pad", C.c_int32)]
 
 
 class SolverOptions(C.Structure):
@@ -182,7 +184,7 @@ def mba_solver_options_default() -> SolverOptions:
 
 
 def mba_problem_create(cameras, points, observations, cam_idx, pt_idx, precision="fp64", loss="none",
-                       huber_delta=0.0, stream=None) -> C.c_void_p:
+                       huber_delta=0.0, stream=None, jacobian="analytic") -> C.c_void_p:
     lib = load()
     pc, ac = _ptr(cameras, np.float64)
     pp, ap = _ptr(points, np.float64)
@@ -200,6 +202,7 @@ def mba_problem_create(cameras, points, observations, cam_idx, pt_idx, precision
     o.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
     o.huber_delta = float(huber_delta)
     o.cuda_stream = _stream_handle(stream)
+    o.jacobian = JACOBIAN[jacobian] if isinstance(jacobian, str) else int(jacobian)
     h = C.c_void_p()
     _check(lib.mba_problem_create(pc, nc, pp, np_, po, pci, ppi, n, C.byref(o), C.byref(h)))
     return h
@@ -351,9 +354,9 @@ class Problem:
     """Owning wrapper over one mba_problem handle."""
 
     def __init__(self, cameras, points, observations, cam_idx, pt_idx, precision="fp64", loss="none",
-                 huber_delta=0.0, stream=None):
+                 huber_delta=0.0, stream=None, jacobian="analytic"):
         self.handle = mba_problem_create(cameras, points, observations, cam_idx, pt_idx, precision, loss,
-                                         huber_delta, stream)
+                                         huber_delta, stream, jacobian)
         self.info = mba_problem_info(self.handle)
 
     def close(self):
@@ -412,7 +415,7 @@ def _vp(a):
 
 
 def mba_batch_create(cam_offsets, pt_offsets, obs_offsets, cameras, points, observations, cam_idx, pt_idx,
-                     precision="fp32", loss="none", huber_delta=0.0, stream=None) -> C.c_void_p:
+                     precision="fp32", loss="none", huber_delta=0.0, stream=None, jacobian="analytic") -> C.c_void_p:
     """Concatenated windows (offset arrays of n_windows + 1 entries; cam_idx / pt_idx local to the window)."""
     co = np.ascontiguousarray(cam_offsets, dtype=np.int64)
     po = np.ascontiguousarray(pt_offsets, dtype=np.int64)
@@ -432,6 +435,7 @@ def mba_batch_create(cam_offsets, pt_offsets, obs_offsets, cameras, points, obse
     o.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
     o.huber_delta = float(huber_delta)
     o.cuda_stream = _stream_handle(stream)
+    o.jacobian = JACOBIAN[jacobian] if isinstance(jacobian, str) else int(jacobian)
     h = C.c_void_p()
     _check(load().mba_batch_create(nw, _vp(co), _vp(po), _vp(oo), _vp(cams), _vp(pts), _vp(obs), _vp(ci), _vp(pi),
                                    C.byref(o), C.byref(h)))
