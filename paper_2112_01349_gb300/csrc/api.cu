@@ -214,7 +214,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.p2 = c.take<double>((size_t)nc * kVec);
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
-        P.cm2pm = c.take<int32_t>(n);
+        P.pm2cm = c.take<int32_t>(n);
         // camera-major copies for the PCG camera pass: the stored Jacobian (FP64, or
         // FP32-mixed with dual numbers), else the point and sqrt(W) (analytic FP32)
         const bool f32_chain = P.fp32 && !P.autodiff;
@@ -286,9 +286,9 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     CKC(stable_sort_by_key(pr->orig_cam, n, nc, P.cm_orig, P.cam_ptr, tmp, sort_tmp, s));
     CKC(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, s));
     CKC(gather_layout(P, obs_d, pr->orig_cam, pr->orig_pt, nullptr, flags, s));
-    // camera-major position -> point-major position, via the inverse of the
-    // point-major permutation (set-up scratch)
-    CKC(build_cm_map(P, (int32_t *)tmp, s));
+    // point-major position -> camera-major position, via the inverse of the
+    // camera-major permutation (set-up scratch): the point pass writes s there
+    CKC(build_pm2cm(P, (int32_t *)tmp, s));
     // keep the observations in input order too (for mba_evaluate)
     {
         // interleaved copy obs_d (n x 2) -> orig_uv (double2): same bytes

@@ -79,7 +79,7 @@ struct Prob {
     int32_t *cm_pt, *cm_orig;
     double2 *cm_uv;
     int32_t *cam_ptr;              // nc + 1
-    int32_t *cm2pm;                // per camera-major position: its point-major position
+    int32_t *pm2cm;                // per point-major position: its camera-major position
     // chunk tables
     int32_t *pchunk;               // n_pchunks + 1 point indices
     int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
@@ -113,7 +113,7 @@ struct Prob {
     // PCG vectors, [nc][kVec] FP64
     double *x, *r, *z, *p, *p2, *q, *g;  // p, p2: search directions of alternate iterations
     void *pT;       // [nc][kVec] search direction in T (point pass gathers when not in shared memory)
-    void *sbuf;     // [npad] per observation s = Jp~ b (2 x T), point-major, written by the point pass
+    void *sbuf;     // [npad] per observation s = Jp~ b (2 x T) in camera-major order, scattered by the point pass
     double *dp;     // [np][3] point step
     double *red;    // reduction partials: per-CTA p.q, r.z and r.r of the persistent kernel
     int32_t red_len;
@@ -397,7 +397,7 @@ cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, i
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
                           int32_t *tmp_i, cudaStream_t s);
 cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s);
-cudaError_t build_cm_map(Prob &P, int32_t *tmp_n, cudaStream_t s);
+cudaError_t build_pm2cm(Prob &P, int32_t *tmp_n, cudaStream_t s);
 
 // linearize.cu
 cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin, cudaStream_t s);

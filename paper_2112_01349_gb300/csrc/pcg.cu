@@ -362,6 +362,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
             const bool act = lane < m;
             const int64_t o = (int64_t)o0 + (act ? lane : 0);
             const int2 pc = act ? P.pm_pc[o] : make_int2(-1 - lane, 0);
+            const int so = act ? __ldcs(P.pm2cm + o) : 0;  // where the camera pass reads s
             const int pt = pc.x, cam = pc.y;
             T Jc[18], Jp[6], ci[6];
 #pragma unroll
@@ -411,7 +412,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
                 b[1] = __shfl_sync(full, bt[1], src);
                 b[2] = __shfl_sync(full, bt[2], src);
             }
-            if (act) store_s<T>(sbuf, o, Jp, b);
+            if (act) store_s<T>(sbuf, so, Jp, b);
         } else {
             // one point with a long track: two sweeps over 32-observation slices
             const int pt = c0.x;
@@ -447,7 +448,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
                     T Jp[6];
 #pragma unroll
                     for (int q = 0; q < 6; ++q) Jp[q] = __ldcs(J + (18 + q) * npad + o);
-                    store_s<T>(sbuf, o, Jp, b);
+                    store_s<T>(sbuf, __ldcs(P.pm2cm + o), Jp, b);
                 }
             }
         }
@@ -549,27 +550,25 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
         for (int s0 = b0; s0 < b1; s0 += 32 * U) {
-            // all streamed loads of the batch first, then the dependent s gathers
-            int pm[U];
+            // s arrives in camera-major order (the point pass scattered it), so
+            // every load of the batch is a coalesced stream
+            bool in[U];
             float4 X[U];
             float sw[U];
+            T2 sv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int s = s0 + u * 32 + lane;
-                const bool in = s < b1;
-                pm[u] = in ? __ldcs(P.cm2pm + s) : -1;
+                in[u] = s < b1;
+                if (in[u]) sv[u] = ldcg(sbuf + s);
                 if (sizeof(T) == 4 && !JS) {
-                    X[u] = in ? __ldcs((const float4 *)P.Xcm + s) : make_float4(0.f, 0.f, -1.f, 0.f);
-                    sw[u] = (in && P.loss != MBA_LOSS_NONE) ? __ldcs((const float *)P.swc + s) : 1.f;
+                    X[u] = in[u] ? __ldcs((const float4 *)P.Xcm + s) : make_float4(0.f, 0.f, -1.f, 0.f);
+                    sw[u] = (in[u] && P.loss != MBA_LOSS_NONE) ? __ldcs((const float *)P.swc + s) : 1.f;
                 }
             }
-            T2 sv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (pm[u] >= 0) sv[u] = ldcg(sbuf + pm[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (pm[u] >= 0) {
+                if (in[u]) {
                     if (sizeof(T) == 4 && !JS) {
                         float y[9];
                         camera_y_x((const float *)ct, X[u], (float)sv[u].x * sw[u], (float)sv[u].y * sw[u], y);

@@ -337,16 +337,16 @@ __global__ void invert_perm_kernel(const int32_t *perm, int64_t n, int32_t *inv)
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
         inv[perm[o]] = (int32_t)o;
 }
-__global__ void cm_map_kernel(const int32_t *cm_orig, const int32_t *inv, int64_t n, int32_t *cm2pm) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
-        cm2pm[s] = inv[cm_orig[s]];
+__global__ void pm2cm_kernel(const int32_t *pm_orig, const int32_t *inv, int64_t n, int32_t *pm2cm) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+        pm2cm[o] = inv[pm_orig[o]];
 }
 }  // namespace
 
-// cm2pm[s] = point-major position of the observation at camera-major position s
-cudaError_t build_cm_map(Prob &P, int32_t *tmp_n, cudaStream_t s) {
-    invert_perm_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_orig, P.n, tmp_n);
-    cm_map_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_orig, tmp_n, P.n, P.cm2pm);
+// pm2cm[o] = camera-major position of the observation at point-major position o
+cudaError_t build_pm2cm(Prob &P, int32_t *tmp_n, cudaStream_t s) {
+    invert_perm_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_orig, P.n, tmp_n);
+    pm2cm_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_orig, tmp_n, P.n, P.pm2cm);
     return cudaGetLastError();
 }
 
