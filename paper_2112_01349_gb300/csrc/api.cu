@@ -177,7 +177,6 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.pm_cam = c.take<int32_t>(n + 64);  // slack for 16-byte-rounded bulk copies
         P.pm_pt = c.take<int32_t>(n);
         P.pm_orig = c.take<int32_t>(n);
-        P.pm_pc = c.take<int2>(n);
         P.pm_uv = c.take<double2>(n);
         P.pt_ptr = c.take<int32_t>((size_t)np + 1);
         P.cm_pt = c.take<int32_t>(n);

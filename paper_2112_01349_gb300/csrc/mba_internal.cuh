@@ -72,7 +72,6 @@ struct Prob {
 
     // observations, point-major order (stable by point, then input index)
     int32_t *pm_cam, *pm_pt, *pm_orig;
-    int2 *pm_pc;                   // (point, camera) per observation
     double2 *pm_uv;
     int32_t *pt_ptr;               // np + 1
     // observations, camera-major order

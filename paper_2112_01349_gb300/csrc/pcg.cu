@@ -361,9 +361,13 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
         if (m <= 32) {
             const bool act = lane < m;
             const int64_t o = (int64_t)o0 + (act ? lane : 0);
-            const int2 pc = act ? P.pm_pc[o] : make_int2(-1 - lane, 0);
+            // point of each lane from the chunk's point starts (whole points, <= 32 observations)
+            const int npts = c1.x - c0.x;
+            const int rs = lane < npts ? __ldg(P.pt_ptr + c0.x + lane) - o0 : 32;
+            const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+            const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+            const int cam = act ? __ldcs(P.pm_cam + o) : 0;
             const int so = act ? __ldcs(P.pm2cm + o) : 0;  // where the camera pass reads s
-            const int pt = pc.x, cam = pc.y;
             T Jc[18], Jp[6], ci[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) Jp[q] = ci[q] = T(0);
@@ -427,7 +431,7 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
                         const int64_t o = (int64_t)o0 + base + lane;
                         T Jc[18], Jp[6], pa[9], u[3];
                         load_jac_stream(J, npad, o, Jc, Jp);
-                        gather_p(ps, pT, P.pm_pc[o].y, pa);
+                        gather_p(ps, pT, __ldcs(P.pm_cam + o), pa);
                         et_p(Jc, Jp, pa, u);
                         a[0] += u[0];
                         a[1] += u[1];

@@ -281,12 +281,11 @@ cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, i
 // ---------------------------------------------------------------------------
 namespace {
 __global__ void gather_kernel(const int32_t *perm, int64_t n, const double *obs, const int32_t *ci,
-                              const int32_t *pi, int32_t *o_cam, int32_t *o_pt, double2 *o_uv, int2 *o_pc) {
+                              const int32_t *pi, int32_t *o_cam, int32_t *o_pt, double2 *o_uv) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = perm[s];
         if (o_cam) o_cam[s] = ci[k];
         if (o_pt) o_pt[s] = pi[k];
-        if (o_pc) o_pc[s] = make_int2(pi[k], ci[k]);
         o_uv[s] = make_double2(obs[2 * (int64_t)k], obs[2 * (int64_t)k + 1]);
     }
 }
@@ -324,8 +323,8 @@ __global__ void point_chunk_kernel(const int32_t *pt_ptr, int32_t np, int64_t n,
 
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
                           int32_t *flags, cudaStream_t s) {
-    gather_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_orig, P.n, obs_in, ci, pi, P.pm_cam, P.pm_pt, P.pm_uv, P.pm_pc);
-    gather_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_orig, P.n, obs_in, ci, pi, nullptr, P.cm_pt, P.cm_uv, nullptr);
+    gather_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_orig, P.n, obs_in, ci, pi, P.pm_cam, P.pm_pt, P.pm_uv);
+    gather_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_orig, P.n, obs_in, ci, pi, nullptr, P.cm_pt, P.cm_uv);
     segment_stats_kernel<<<grid_for(P.np), kBlock, 0, s>>>(P.pt_ptr, P.np, flags);
     segment_stats_kernel<<<grid_for(P.nc), kBlock, 0, s>>>(P.cam_ptr, P.nc, flags + 2);
     (void)max_track;
