@@ -214,13 +214,15 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
         P.pm2cm = c.take<int32_t>(n);
-        // camera-major copies for the PCG camera pass: the stored Jacobian (FP64, or
-        // FP32-mixed with dual numbers), else the point and sqrt(W) (analytic FP32)
-        const bool f32_chain = P.fp32 && !P.autodiff;
-        P.Xcm = f32_chain ? c.take<float4>((size_t)P.npad) : nullptr;
+        // copies for the PCG: the camera-major stored Jacobian (FP64, or FP32-mixed
+        // with dual numbers), else the factored form's per-observation data
+        const bool fact = P.fp32 && !P.autodiff;
+        P.fact = fact ? 1 : 0;
+        P.PXpm = fact ? c.take<float>(3 * (size_t)P.npad) : nullptr;
+        P.Jph = fact ? c.take<float>(6 * (size_t)P.npad) : nullptr;
+        P.PXcm = fact ? c.take<float>(3 * (size_t)P.npad) : nullptr;
         P.zT = P.fp32 ? c.take<float>((size_t)nc * kVec) : nullptr;
         P.pT2 = c.take<char>((size_t)nc * kVec * w);
-        P.swc = (f32_chain && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
         P.Jcm = P.fp32 ? nullptr : c.take<double>(18 * (size_t)P.npad);
         P.JcmT = P.fp32 ? (P.autodiff ? (void *)c.take<float>(18 * (size_t)P.npad) : nullptr) : (void *)P.Jcm;
         P.dp = c.take<double>(3 * (size_t)np);

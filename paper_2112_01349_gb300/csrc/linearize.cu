@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
             const int64_t o = (int64_t)o0 + k;
             const int cam = P.pm_cam[o], pt = P.pm_pt[o];
             const double2 uv = P.pm_uv[o];
-            T e[2], Jc[18], Jp[6];
+            T e[2], Jc[18], Jp[6], pz[3];
             edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
                              (T)P.pts[3 * (int64_t)pt + 1], (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc,
-                             Jp);
+                             Jp, (sizeof(T) == 4 && !AD) ? pz : nullptr);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);
@@ -76,6 +76,12 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
             for (int q = 0; q < 6; ++q) {
                 Jp[q] *= sw;
                 J[(18 + q) * np_ + o] = Jp[q];
+            }
+            if (sizeof(T) == 4 && !AD && P.fact) {  // factored form: (px, py, 1/Pz) and W Jp
+#pragma unroll
+                for (int q = 0; q < 3; ++q) P.PXpm[q * np_ + o] = (float)pz[q];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) P.Jph[q * np_ + o] = (float)(sw * Jp[q]);
             }
             e[0] *= sw;
             e[1] *= sw;
@@ -130,9 +136,10 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
         for (int s = b0 + threadIdx.x; s < b1; s += kBlock) {
             const int pt = P.cm_pt[s];
             const double2 uv = P.cm_uv[s];
-            T e[2], Jc[18], Jp[6];
+            T e[2], Jc[18], Jp[6], pz[3];
             edge_eval<T, AD, true, false>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
-                                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+                                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp,
+                                          (sizeof(T) == 4 && !AD) ? pz : nullptr);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);
@@ -140,17 +147,17 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             for (int q = 0; q < 18; ++q) Jc[q] *= sw;
             e[0] *= sw;
             e[1] *= sw;
-            // copies the PCG camera pass reads in camera-major order: the stored
-            // Jacobian (FP64, or any dual-number Jacobian), else the point and
-            // sqrt(W) from which the FP32 pass re-derives Jc~^T s
+            // what the PCG camera pass reads in camera-major order: the stored
+            // Jacobian (FP64, or any dual-number Jacobian), else the factored
+            // form's (px, py, 1/Pz)
             if ((sizeof(T) == 8 || AD) && P.JcmT) {
 #pragma unroll
                 for (int q = 0; q < 18; ++q) ((T *)P.JcmT)[(int64_t)q * P.npad + s] = Jc[q];
             }
-            if (sizeof(T) == 4 && !AD && P.swc) ((float *)P.swc)[s] = (float)sw;
-            if (sizeof(T) == 4 && !AD && P.Xcm)
-                ((float4 *)P.Xcm)[s] = make_float4((float)P.pts[3 * (int64_t)pt], (float)P.pts[3 * (int64_t)pt + 1],
-                                                   (float)P.pts[3 * (int64_t)pt + 2], 0.f);
+            if (sizeof(T) == 4 && !AD && P.fact) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) P.PXcm[(int64_t)q * P.npad + s] = (float)pz[q];
+            }
             int idx = 0;
 #pragma unroll
             for (int a = 0; a < 9; ++a)

@@ -97,11 +97,16 @@ struct Prob {
     double *Hll;    // [np][6] packed upper triangle of C
     double *w;      // [np][3]
     double *cpart;  // [n_cchunks][54] camera-chunk partial sums (the PCG reuses [n_cchunks][9])
-    void *Xcm;      // FP32-mixed: [npad] float4 point of each observation, camera-major
     void *zT;       // FP32-mixed: [nc][kVec] float copy of z
     void *pT2;      // FP32-mixed: second float search-direction buffer (alternate iterations)
-    void *swc;      // FP32-mixed with a loss: [npad] sqrt(W) in camera-major order
     double *Jcm;    // FP64: [18][npad] sqrt(W)-scaled camera Jacobian, camera-major
+    // FP32-mixed analytic (factored) form: per observation the normalised point
+    // and 1 / P_z, from which the PCG re-derives Jc p and Jc^T s with per-camera
+    // constants, and the W-scaled point Jacobian
+    float *PXpm;    // [3][npad] (px, py, 1/Pz), point-major
+    float *Jph;     // [6][npad] W Jp, point-major
+    float *PXcm;    // [3][npad] (px, py, 1/Pz), camera-major
+    int32_t fact;   // 1: the PCG runs the factored form (FP32-mixed, analytic Jacobian)
     void *JcmT;     // [18][npad] sqrt(W)-scaled camera Jacobian in T, camera-major, that the PCG
                     // camera pass reads: Jcm in FP64; FP32-mixed with autodiff only (else null)
     int32_t autodiff;  // 1: every Jacobian comes from the edge functor on dual numbers
@@ -188,9 +193,10 @@ __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
 // Residual e = pi(c, X) - u and, if JAC, the analytic Jacobians Jc (2x9, row
 // major: w, t, f, k1, k2) and Jp (2x3) by the chain rule, in precision T.
+// pz (optional): the normalised point p = (px, py) and 1 / P_z.
 template <typename T, bool JAC>
 __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T X2, T u0, T u1, T *e, T *Jc,
-                                        T *Jp) {
+                                        T *Jp, T *pz = nullptr) {
     const T R0 = ct[0], R1 = ct[1], R2 = ct[2], R3 = ct[3], R4 = ct[4], R5 = ct[5], R6 = ct[6], R7 = ct[7],
             R8 = ct[8];
     const T P0 = R0 * X0 + R1 * X1 + R2 * X2 + ct[18];
@@ -203,6 +209,11 @@ __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T 
     const T d = T(1) + k1 * r2 + k2 * r2 * r2;
     e[0] = f * d * px - u0;
     e[1] = f * d * py - u1;
+    if (pz) {
+        pz[0] = px;
+        pz[1] = py;
+        pz[2] = iz;
+    }
     if (!JAC) return;
     const T dd = T(2) * k1 + T(4) * k2 * r2;
     // A = d(pixel)/dp = f (d I + dd p p^T); D = A dp/dP
@@ -246,9 +257,9 @@ __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T 
 constexpr int kJetK = 12;
 template <typename T, bool AD, bool CAM = true, bool PT = true>
 __device__ __forceinline__ void edge_eval(const T *__restrict__ ct, T X0, T X1, T X2, T u0, T u1, T *e, T *Jc,
-                                          T *Jp) {
+                                          T *Jp, T *pz = nullptr) {
     if (!AD) {
-        project<T, true>(ct, X0, X1, X2, u0, u1, e, Jc, Jp);
+        project<T, true>(ct, X0, X1, X2, u0, u1, e, Jc, Jp, pz);
         return;
     }
     const T cam[9] = {ct[25], ct[26], ct[27], ct[18], ct[19], ct[20], ct[21], ct[22], ct[23]};

@@ -461,44 +461,249 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
     }
 }
 
-// y = Jc~^T s for one camera-major observation of the analytic FP32 form, from
-// the camera table and the observation's point by the transposed chain rule,
-// without forming Jc: v = D^T s is the translation block (D = d(pixel)/dP),
-// y_w = M^T (X x (R^T v)) (X x v in the first-order branch), y_f = d (p.s),
-// y_k1 = f |p|^2 (p.s), y_k2 = f |p|^4 (p.s); s arrives scaled by sqrt(W).
-__device__ __forceinline__ void camera_y_x(const float *ct, float4 X, float s0, float s1, float *y) {
-    const float P0 = ct[0] * X.x + ct[1] * X.y + ct[2] * X.z + ct[18];
-    const float P1 = ct[3] * X.x + ct[4] * X.y + ct[5] * X.z + ct[19];
-    const float P2 = ct[6] * X.x + ct[7] * X.y + ct[8] * X.z + ct[20];
-    const float iz = __frcp_rn(P2);
-    const float px = -P0 * iz, py = -P1 * iz;
-    const float f = ct[21], k1 = ct[22], k2 = ct[23];
+
+// ---------------------------------------------------------------------------
+// Factored FP32 form (analytic Jacobian).  With P = R X + t the camera-frame
+// point, p = -(P_x, P_y) / P_z, r2 = |p|^2, d = 1 + k1 r2 + k2 r2^2 and
+// A = f (d I + (2 k1 + 4 k2 r2) p p^T), the BAL Jacobian of one observation is
+//   D = d(pixel)/dP = -(1/P_z) A [I | p],   Jp = D R,   Jc = [-D R [X]x M | D | p (d, f r2, f r2^2)]
+// (M: the rotation factor of the camera table).  Two identities make every
+// per-observation product depend only on (px, py, 1/P_z), the stored W Jp and
+// per-camera constants:
+//   Jc v = D (n x (P - t) + v_t) + p (d v_f + f r2 v_k1 + f r2^2 v_k2),  n = R M v_w,
+//   sum_k Jc_k^T s_k = [ (R M)^T sum_k (P_k - t) x D_k^T s_k ; sum_k D_k^T s_k ; ... ],
+// with P - t = P_z (-px, -py, 1).  The point pass streams 36 bytes per
+// observation instead of the 96-byte Jacobian; the camera pass reads 12 bytes
+// and applies (R M)^T once per chunk.  (In the first-order rotation branch,
+// |w|^2 <= 2.2e-16, this applies R = I + [w]x where the Jacobian has I: a
+// relative difference of at most |w|, below FP32 rounding.)
+//
+// Per-camera row of 12 floats for a vector v = (v_w, v_t, v_f, v_k1, v_k2):
+//   n = R M v_w, h = v_t - n x t, e = (v_f, f v_k1, f v_k2), then (f, k1, k2)
+//   (consts) or zeros.  The row is linear in v apart from the constants, so
+//   row(z) + beta row(p) with the constants carried by row(z) alone is the row
+//   of z + beta p.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fact_row(const float *__restrict__ ct, const float *v, bool consts, float *r) {
+    const float m0 = ct[9] * v[0] + ct[10] * v[1] + ct[11] * v[2];
+    const float m1 = ct[12] * v[0] + ct[13] * v[1] + ct[14] * v[2];
+    const float m2 = ct[15] * v[0] + ct[16] * v[1] + ct[17] * v[2];
+    const float n0 = ct[0] * m0 + ct[1] * m1 + ct[2] * m2;
+    const float n1 = ct[3] * m0 + ct[4] * m1 + ct[5] * m2;
+    const float n2 = ct[6] * m0 + ct[7] * m1 + ct[8] * m2;
+    const float t0 = ct[18], t1 = ct[19], t2 = ct[20], f = ct[21];
+    r[0] = n0;
+    r[1] = n1;
+    r[2] = n2;
+    r[3] = v[3] - (n1 * t2 - n2 * t1);
+    r[4] = v[4] - (n2 * t0 - n0 * t2);
+    r[5] = v[5] - (n0 * t1 - n1 * t0);
+    r[6] = v[6];
+    r[7] = f * v[7];
+    r[8] = f * v[8];
+    r[9] = consts ? f : 0.f;
+    r[10] = consts ? ct[22] : 0.f;
+    r[11] = consts ? ct[23] : 0.f;
+}
+
+// Warp-collective (all 32 lanes call it): lanes 9s..9s+8 hold the nine
+// components of camera `cam` (lane s of the three-camera group); each active
+// lane writes its element of the camera's row to dst[cam][12] (lanes of rows
+// 0..2 also the pad elements 9..11).
+__device__ __forceinline__ void fact_row_store(const Prob &P, float *dst, int cam, bool act, double val, int sub,
+                                               int row, bool consts) {
+    const float fv = (float)val;
+    float v[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v[j] = __shfl_sync(0xffffffffu, fv, (9 * sub + j) & 31);
+    if (!act) return;
+    float r[12];
+    fact_row((const float *)P.camtab + (int64_t)cam * kCamTab, v, consts, r);
+    float mine = r[0], pad = r[9];
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+        if (row == j) mine = r[j];
+    if (row == 1) pad = r[10];
+    if (row == 2) pad = r[11];
+    stcg(dst + (int64_t)cam * kVec + row, mine);
+    if (row < 3) stcg(dst + (int64_t)cam * kVec + 9 + row, pad);
+}
+
+// The camera's row: shared memory (ps, [nc][12]) or the global copy.
+__device__ __forceinline__ void gather_row(const float *ps, const float *pT, int cam, float *r) {
+    float4 a, b, c;
+    if (ps) {
+        const float4 *src = (const float4 *)(ps + cam * 12);
+        a = src[0];
+        b = src[1];
+        c = src[2];
+    } else {
+        const float4 *src = (const float4 *)(pT + (int64_t)cam * kVec);
+        a = __ldcg(src);
+        b = __ldcg(src + 1);
+        c = __ldcg(src + 2);
+    }
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+}
+
+// t = Jc v (unscaled) for one observation from (px, py, 1/Pz) and the camera's row.
+__device__ __forceinline__ void fact_jc_v(float px, float py, float iz, const float *r, float *t) {
+    const float f = r[9], k1 = r[10], k2 = r[11];
     const float r2 = px * px + py * py;
     const float d = 1.f + k1 * r2 + k2 * r2 * r2;
     const float dd = 2.f * k1 + 4.f * k2 * r2;
     const float a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
-    // v = D^T s with D = A dp/dP, A = [[a00, a01], [a01, a11]]
-    const float g0 = -(a00 * s0 + a01 * s1) * iz, g1 = -(a01 * s0 + a11 * s1) * iz;  // (A s) scaled
-    const float v0 = g0, v1 = g1, v2 = g0 * px + g1 * py;
-    y[3] = v0;
-    y[4] = v1;
-    y[5] = v2;
-    float w0 = v0, w1 = v1, w2 = v2;
-    const bool small = ct[24] != 0.f;
-    if (!small) {
-        w0 = ct[0] * v0 + ct[3] * v1 + ct[6] * v2;
-        w1 = ct[1] * v0 + ct[4] * v1 + ct[7] * v2;
-        w2 = ct[2] * v0 + ct[5] * v1 + ct[8] * v2;
-    }
-    const float u0 = X.y * w2 - X.z * w1, u1 = X.z * w0 - X.x * w2, u2 = X.x * w1 - X.y * w0;
-    y[0] = ct[9] * u0 + ct[12] * u1 + ct[15] * u2;
-    y[1] = ct[10] * u0 + ct[13] * u1 + ct[16] * u2;
-    y[2] = ct[11] * u0 + ct[14] * u1 + ct[17] * u2;
-    const float pss = px * s0 + py * s1;
-    y[6] = d * pss;
-    y[7] = f * r2 * pss;
-    y[8] = f * r2 * r2 * pss;
+    // (n x (P - t) + v_t) / P_z with P - t = P_z (-px, -py, 1)
+    const float w0 = r[1] + r[2] * py + iz * r[3];
+    const float w1 = -r[0] - r[2] * px + iz * r[4];
+    const float w2 = r[1] * px - r[0] * py + iz * r[5];
+    const float z0 = w0 + px * w2, z1 = w1 + py * w2;
+    const float ei = r[6] * d + r2 * (r[7] + r2 * r[8]);
+    t[0] = -(a00 * z0 + a01 * z1) + px * ei;
+    t[1] = -(a01 * z0 + a11 * z1) + py * ei;
 }
+
+// Point pass of the factored form: as point_pass, with u = (W Jp)^T (Jc p)
+// and s = (W Jp) b, so the camera pass forms sum Jc^T s with unscaled Jc.
+template <bool RHS>
+__device__ void point_pass_fact(const Prob &P, const float *ps, const float *pT, float2 *sbuf) {
+    const float *__restrict__ Jh = P.Jph;
+    const float *__restrict__ PX = P.PXpm;
+    const float *__restrict__ Cinv = (const float *)P.Cinv;
+    const int64_t npad = P.npad;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
+    const int gstride = gridDim.x * nwarp;
+    int w = blockIdx.x * nwarp + (threadIdx.x >> 5);
+    int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
+    if (w < P.n_wchunks) {
+        c0 = P.wchunk[w];
+        c1 = P.wchunk[w + 1];
+    }
+    for (; w < P.n_wchunks; w += gstride) {
+        const int wn = w + gstride;
+        int2 n0 = c0, n1 = c1;
+        if (wn < P.n_wchunks) {
+            n0 = P.wchunk[wn];
+            n1 = P.wchunk[wn + 1];
+        }
+        const int o0 = c0.y, m = c1.y - c0.y;
+        if (m <= 32) {
+            const bool act = lane < m;
+            const int64_t o = (int64_t)o0 + (act ? lane : 0);
+            // point of each lane from the chunk's point starts (whole points, <= 32 observations)
+            const int npts = c1.x - c0.x;
+            const int rs = lane < npts ? __ldg(P.pt_ptr + c0.x + lane) - o0 : 32;
+            const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+            const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+            const int cam = act ? __ldcs(P.pm_cam + o) : 0;
+            const int so = act ? __ldcs(P.pm2cm + o) : 0;  // where the camera pass reads s
+            float jh[6], ci[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) jh[q] = ci[q] = 0.f;
+            float px = 0.f, py = 0.f, iz = 0.f;
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) jh[q] = __ldcs(Jh + q * npad + o);
+                if (!RHS) {
+                    px = __ldcs(PX + o);
+                    py = __ldcs(PX + npad + o);
+                    iz = __ldcs(PX + 2 * npad + o);
+                }
+                load_sym3(Cinv + 6 * (int64_t)pt, ci);
+            }
+            float b[3] = {0.f, 0.f, 0.f};
+            if (RHS) {
+                if (act)
+                    apply_sym3(ci, (float)P.w[3 * (int64_t)pt], (float)P.w[3 * (int64_t)pt + 1],
+                               (float)P.w[3 * (int64_t)pt + 2], b);
+            } else {
+                float u[3] = {0.f, 0.f, 0.f};
+                if (act) {
+                    float r[12], t[2];
+                    gather_row(ps, pT, cam, r);
+                    fact_jc_v(px, py, iz, r, t);
+                    u[0] = jh[0] * t[0] + jh[3] * t[1];
+                    u[1] = jh[1] * t[0] + jh[4] * t[1];
+                    u[2] = jh[2] * t[0] + jh[5] * t[1];
+                }
+                // inclusive segmented scan keyed by point (segments are contiguous)
+#pragma unroll
+                for (int dl = 1; dl < 32; dl <<= 1) {
+                    const int kp = __shfl_up_sync(full, pt, dl);
+                    const float v0 = __shfl_up_sync(full, u[0], dl), v1 = __shfl_up_sync(full, u[1], dl),
+                                v2 = __shfl_up_sync(full, u[2], dl);
+                    if (lane >= dl && kp == pt) {
+                        u[0] += v0;
+                        u[1] += v1;
+                        u[2] += v2;
+                    }
+                }
+                const int nxt = __shfl_down_sync(full, pt, 1);
+                const bool tail = act && (lane == 31 || lane == m - 1 || nxt != pt);
+                const unsigned tails = __ballot_sync(full, tail);
+                float bt[3];
+                apply_sym3(ci, u[0], u[1], u[2], bt);
+                const unsigned mine = tails & (0xffffffffu << lane);
+                const int src = mine ? __ffs(mine) - 1 : lane;
+                b[0] = __shfl_sync(full, bt[0], src);
+                b[1] = __shfl_sync(full, bt[1], src);
+                b[2] = __shfl_sync(full, bt[2], src);
+            }
+            if (act) store_s<float>(sbuf, so, jh, b);
+        } else {
+            // one point with a long track: two sweeps over 32-observation slices
+            const int pt = c0.x;
+            float ci[6], b[3];
+            load_sym3(Cinv + 6 * (int64_t)pt, ci);
+            if (RHS) {
+                apply_sym3(ci, (float)P.w[3 * (int64_t)pt], (float)P.w[3 * (int64_t)pt + 1],
+                           (float)P.w[3 * (int64_t)pt + 2], b);
+            } else {
+                float a[3] = {0.f, 0.f, 0.f};
+                for (int base = 0; base < m; base += 32) {
+                    if (base + lane < m) {
+                        const int64_t o = (int64_t)o0 + base + lane;
+                        float r[12], t[2];
+                        gather_row(ps, pT, __ldcs(P.pm_cam + o), r);
+                        fact_jc_v(__ldcs(PX + o), __ldcs(PX + npad + o), __ldcs(PX + 2 * npad + o), r, t);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            a[q] += __ldcs(Jh + q * npad + o) * t[0] + __ldcs(Jh + (3 + q) * npad + o) * t[1];
+                    }
+                }
+#pragma unroll
+                for (int dl = 16; dl > 0; dl >>= 1) {
+                    a[0] += __shfl_xor_sync(full, a[0], dl);
+                    a[1] += __shfl_xor_sync(full, a[1], dl);
+                    a[2] += __shfl_xor_sync(full, a[2], dl);
+                }
+                apply_sym3(ci, a[0], a[1], a[2], b);
+            }
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    const int64_t o = (int64_t)o0 + base + lane;
+                    float jh[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) jh[q] = __ldcs(Jh + q * npad + o);
+                    store_s<float>(sbuf, __ldcs(P.pm2cm + o), jh, b);
+                }
+            }
+        }
+        c0 = n0;
+        c1 = n1;
+    }
+}
+
+template <typename T, bool RHS, bool FACT>
+__device__ __forceinline__ void point_pass_any(const Prob &P, const T *ps, const T *pT, typename V2<T>::type *sbuf) {
+    if constexpr (FACT) point_pass_fact<RHS>(P, (const float *)ps, (const float *)pT, (float2 *)sbuf);
+    else point_pass<T, RHS>(P, ps, pT, sbuf);
+}
+
 // Stored form (FP64, and FP32-mixed with dual-number Jacobians): acc += Jc~^T s
 // as 18 fused multiply-adds on the stored camera-major Jc~ (sqrt(W) included).
 template <typename T>
@@ -527,6 +732,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                                T *pT_cur, double beta, bool first, double *cslot, double *sb) {
     using T2 = typename V2<T>::type;
     constexpr int U = 4;
+    constexpr bool FACT = sizeof(T) == 4 && !JS;
     __shared__ T cts[32][kCamTab];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
@@ -553,31 +759,53 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         T acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
+        // factored form: the camera's f, k1, k2 for every observation of the chunk
+        float cf = 0.f, ck1 = 0.f, ck2 = 0.f;
+        if (FACT) {
+            cf = (float)ct[21];
+            ck1 = (float)ct[22];
+            ck2 = (float)ct[23];
+        }
         for (int s0 = b0; s0 < b1; s0 += 32 * U) {
             // s arrives in camera-major order (the point pass scattered it), so
             // every load of the batch is a coalesced stream
             bool in[U];
-            float4 X[U];
-            float sw[U];
+            float px[U], py[U], iz[U];
             T2 sv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int s = s0 + u * 32 + lane;
                 in[u] = s < b1;
                 if (in[u]) sv[u] = ldcg(sbuf + s);
-                if (sizeof(T) == 4 && !JS) {
-                    X[u] = in[u] ? __ldcs((const float4 *)P.Xcm + s) : make_float4(0.f, 0.f, -1.f, 0.f);
-                    sw[u] = (in[u] && P.loss != MBA_LOSS_NONE) ? __ldcs((const float *)P.swc + s) : 1.f;
+                if (FACT) {
+                    px[u] = in[u] ? __ldcs(P.PXcm + s) : 0.f;
+                    py[u] = in[u] ? __ldcs(P.PXcm + P.npad + s) : 0.f;
+                    iz[u] = in[u] ? __ldcs(P.PXcm + 2 * P.npad + s) : 0.f;
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (in[u]) {
-                    if (sizeof(T) == 4 && !JS) {
-                        float y[9];
-                        camera_y_x((const float *)ct, X[u], (float)sv[u].x * sw[u], (float)sv[u].y * sw[u], y);
-#pragma unroll
-                        for (int a = 0; a < 9; ++a) acc[a] += (T)y[a];
+                    if (FACT) {
+                        // g = A s, D^T s = -(1/Pz) (g0, g1, p.g); accumulate D^T s,
+                        // q x (g0, g1, p.g) with q = (-px, -py, 1), and p.s (d, r2, r2^2)
+                        const float x = px[u], y = py[u], s0v = (float)sv[u].x, s1v = (float)sv[u].y;
+                        const float r2 = x * x + y * y;
+                        const float d = 1.f + ck1 * r2 + ck2 * r2 * r2;
+                        const float dd = 2.f * ck1 + 4.f * ck2 * r2;
+                        const float a00 = cf * (d + dd * x * x), a01 = cf * dd * x * y, a11 = cf * (d + dd * y * y);
+                        const float g0 = a00 * s0v + a01 * s1v, g1 = a01 * s0v + a11 * s1v, g2 = x * g0 + y * g1;
+                        const float mz = -iz[u];
+                        acc[0] += (T)(mz * g0);
+                        acc[1] += (T)(mz * g1);
+                        acc[2] += (T)(mz * g2);
+                        acc[3] += (T)(-y * g2 - g1);
+                        acc[4] += (T)(g0 + x * g2);
+                        acc[5] += (T)(y * g0 - x * g1);
+                        const float pss = x * s0v + y * s1v;
+                        acc[6] += (T)(d * pss);
+                        acc[7] += (T)(r2 * pss);
+                        acc[8] += (T)(r2 * r2 * pss);
                     } else {
                         camera_acc_stored<T>(P, s0 + u * 32 + lane, (T)sv[u].x, (T)sv[u].y, acc);
                     }
@@ -590,7 +818,30 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
             T v = acc[a];
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(full, v, d);
-            if (lane == a) mine = v;
+            if (FACT) acc[a] = v;  // every lane holds every sum
+            else if (lane == a) mine = v;
+        }
+        if (FACT) {
+            // Jc^T s of the chunk: rotation (R M)^T (-Cq - t x Yt), translation Yt,
+            // intrinsics (Yi0, f Yi1, f Yi2)
+            const float t0 = (float)ct[18], t1 = (float)ct[19], t2 = (float)ct[20];
+            const float Y0 = (float)acc[0], Y1 = (float)acc[1], Y2 = (float)acc[2];
+            const float c0 = -(float)acc[3] - (t1 * Y2 - t2 * Y1);
+            const float c1 = -(float)acc[4] - (t2 * Y0 - t0 * Y2);
+            const float c2 = -(float)acc[5] - (t0 * Y1 - t1 * Y0);
+            const float q0 = ct[0] * c0 + ct[3] * c1 + ct[6] * c2;  // R^T c
+            const float q1 = ct[1] * c0 + ct[4] * c1 + ct[7] * c2;
+            const float q2 = ct[2] * c0 + ct[5] * c1 + ct[8] * c2;
+            const int a = lane < 3 ? lane : 0;
+            const float yr = ct[9 + a] * q0 + ct[12 + a] * q1 + ct[15 + a] * q2;  // (M^T q)_a
+            float mv = yr;
+            if (lane == 3) mv = Y0;
+            if (lane == 4) mv = Y1;
+            if (lane == 5) mv = Y2;
+            if (lane == 6) mv = (float)acc[6];
+            if (lane == 7) mv = cf * (float)acc[7];
+            if (lane == 8) mv = cf * (float)acc[8];
+            mine = (T)mv;
         }
         if (lane < 9) cslot[(k - k0) * 9 + lane] = (double)mine;  // one conversion per lane
         int nk = 0;
@@ -625,10 +876,11 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 stcg(P.x + vo, 0.0);
                 stcg(P.r + vo, g);
                 stcg(P.z + vo, z);
-                if (sizeof(T) == 4) stcg((float *)P.zT + vo, (float)z);
+                if (sizeof(T) == 4 && !FACT) stcg((float *)P.zT + vo, (float)z);
                 v1 = g * g;
                 v2 = g * z;
             }
+            if (FACT) fact_row_store(P, (float *)P.zT, cm, act, z, sub, row, true);
         } else {
             double p = 0.0;
             if (act) {
@@ -646,10 +898,11 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 stcg(P.q + vo, q);
                 if (MODE == CAM_ITER) {
                     stcg(p_cur + vo, p);
-                    if (pT_cur) stcg(pT_cur + vo, (T)p);
+                    if (pT_cur && !FACT) stcg(pT_cur + vo, (T)p);
                 }
                 v1 = p * q;
             }
+            if (FACT && MODE == CAM_ITER && pT_cur) fact_row_store(P, (float *)pT_cur, cm, act, p, sub, row, false);
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
@@ -668,9 +921,41 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 // (p = z on the first iteration), or the given FP64 p (src_given).  The FP32
 // form builds it from float copies of z and p_prev with float4 loads; the FP64
 // form from the FP64 vectors, as the camera pass does.
-template <typename T>
+// Factored form: the camera rows (12 floats, [nc][12]) instead: row(z) + beta
+// row(p_prev) from the float row copies, or the rows of the given FP64 p.
+template <typename T, bool FACT>
 __device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_prev, double beta, bool first,
                         const double *src_given) {
+    if constexpr (FACT) {
+        float4 *dst = (float4 *)ps;
+        if (!src_given) {
+            const float4 *z4 = (const float4 *)P.zT, *p4 = (const float4 *)pT_prev;
+            const float fb = (float)beta;
+            const int nq = P.nc * 3;  // three float4 per camera row
+            for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+                const float4 zv = __ldcg(z4 + e);
+                float4 v = zv;
+                if (!first) {
+                    const float4 pv = __ldcg(p4 + e);
+                    v = make_float4(fmaf(fb, pv.x, zv.x), fmaf(fb, pv.y, zv.y), fmaf(fb, pv.z, zv.z),
+                                    fmaf(fb, pv.w, zv.w));
+                }
+                dst[e] = v;
+            }
+        } else {
+            for (int cam = threadIdx.x; cam < P.nc; cam += blockDim.x) {
+                float v[9], r[12];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) v[j] = (float)src_given[(int64_t)cam * kVec + j];
+                fact_row((const float *)P.camtab + (int64_t)cam * kCamTab, v, true, r);
+                dst[3 * cam] = make_float4(r[0], r[1], r[2], r[3]);
+                dst[3 * cam + 1] = make_float4(r[4], r[5], r[6], r[7]);
+                dst[3 * cam + 2] = make_float4(r[8], r[9], r[10], r[11]);
+            }
+        }
+        __syncthreads();
+        return;
+    }
     const int total = P.nc * 9;
     if (sizeof(T) == 4 && !src_given) {
         const float4 *z4 = (const float4 *)P.zT, *p4 = (const float4 *)pT_prev;
@@ -779,6 +1064,7 @@ template <typename T, bool JS>
 __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin, int forcing) {
     using T2 = typename V2<T>::type;
+    constexpr bool FACT = sizeof(T) == 4 && !JS;  // FP32-mixed, analytic Jacobian: the factored form
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double sb[64];
     DevState *st = P.st;
@@ -802,36 +1088,39 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     double *cslot = (double *)(smem_raw + P.pcg_ps_bytes);
     bool ok = true;
     auto barrier = [&]() -> bool { return grid_barrier(st, epoch, spin); };
-    // owner phase: p = z + beta p_prev written in FP64 and as T for the gathers
+    // owner phase: p = z + beta p_prev written in FP64 and, for the gathers, as
+    // T (or, in the factored form, as the camera's row)
     auto phase_p = [&](const double *p_prev, double *p_cur, double beta, bool first, const double *given) {
         for (int w = blockIdx.x * nwarp + wid; w < ncw; w += G * nwarp) {
             const int cam = w * 3 + my_sub;
-            if (lane < 27 && cam < P.nc) {
+            const bool act = lane < 27 && cam < P.nc;
+            double pn = 0.0;
+            if (act) {
                 const int64_t vo = (int64_t)cam * kVec + row;
-                const double pn = given ? given[vo]
-                                        : (first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo)));
+                pn = given ? given[vo] : (first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo)));
                 if (!given) stcg(p_cur + vo, pn);
-                stcg(pT + vo, (T)pn);
+                if (!FACT) stcg(pT + vo, (T)pn);
             }
+            if (FACT) fact_row_store(P, (float *)pT, act ? cam : 0, act, pn, my_sub, row, true);
         }
     };
 
     if (mode == PCG_MATVEC) {
         // p given in P.p (FP64): q = B~ p - E C~^-1 E^T p
         if (ps) {
-            stage_p<T>(P, ps, nullptr, nullptr, 0.0, true, P.p);
+            stage_p<T, FACT>(P, ps, nullptr, nullptr, 0.0, true, P.p);
         } else {
             phase_p(nullptr, nullptr, 0.0, true, P.p);
             if (!(ok = barrier())) return;
         }
-        point_pass<T, false>(P, ps, pT, sbuf);
+        point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
         if (!barrier()) return;
         camera_pass<T, CAM_MATVEC, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         return;
     }
 
     // ---- right-hand side g = v - E C~^-1 w (Eq. 3), x = 0, r = g, z = B~^-1 g ----
-    point_pass<T, true>(P, nullptr, nullptr, sbuf);
+    point_pass_any<T, true, FACT>(P, nullptr, nullptr, sbuf);
     ok = barrier();
     if (ok) {
         const double2 d = camera_pass<T, CAM_RHS, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
@@ -879,15 +1168,16 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             T *pT_cur = (n & 1) ? (T *)P.pT2 : pT;
             const T *pT_prev = (n & 1) ? pT : (T *)P.pT2;
             if (ps) {
-                stage_p<T>(P, ps, p_prev, pT_prev, beta, n == 0, nullptr);
+                stage_p<T, FACT>(P, ps, p_prev, pT_prev, beta, n == 0, nullptr);
             } else {
                 phase_p(p_prev, p_cur, beta, n == 0, nullptr);
                 if (!(ok = barrier())) break;
             }
-            point_pass<T, false>(P, ps, pT, sbuf);
+            point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
             if (!(ok = barrier())) break;
             {
-                const double2 d = camera_pass<T, CAM_ITER, JS>(P, sbuf, p_prev, p_cur, sizeof(T) == 4 ? pT_cur : nullptr,
+                const double2 d = camera_pass<T, CAM_ITER, JS>(P, sbuf, p_prev, p_cur,
+                                                               (sizeof(T) == 4 && ps) ? pT_cur : nullptr,
                                                            beta, n == 0, cslot, sb);
                 if (threadIdx.x == 0) stcg(part_pq + blockIdx.x, d.x);
             }
@@ -922,9 +1212,10 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                         const double rc = __shfl_sync(full, rv, my_sub * 9 + c);
                         if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c), rc, z);
                     }
+                    if (FACT) fact_row_store(P, (float *)P.zT, act ? cam : c0, act, z, my_sub, row, true);
                     if (act) {
                         stcg(P.z + vo, z);
-                        if (sizeof(T) == 4) stcg((float *)P.zT + vo, (float)z);
+                        if (sizeof(T) == 4 && !FACT) stcg((float *)P.zT + vo, (float)z);
                         rr += rv * rv;
                         rz += rv * z;
                     }
@@ -1093,9 +1384,10 @@ cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *
 // gathers p from global memory and an extra barrier is needed.
 void plan_pcg_smem(Prob &P) {
     const int w = P.fp32 ? 4 : 8;
+    const int per_cam = P.fact ? 12 : 9;  // the factored form stages a 12-float row per camera
     const int64_t budget = 227 * 1024 - 12 * 1024;
     const int64_t slots = (int64_t)P.pcg_max_cta_chunks * 9 * 8;
-    const int64_t psb = (((int64_t)P.nc * 9 * w) + 127) & ~(int64_t)127;
+    const int64_t psb = (((int64_t)P.nc * per_cam * w) + 127) & ~(int64_t)127;
     P.pcg_use_ps = (psb + slots <= budget) ? 1 : 0;
     P.pcg_ps_bytes = P.pcg_use_ps ? (int)psb : 0;
     P.pcg_smem = (int)(P.pcg_ps_bytes + slots);
