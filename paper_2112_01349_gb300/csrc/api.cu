@@ -209,7 +209,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.p = c.take<double>((size_t)nc * kVec);
         P.q = c.take<double>((size_t)nc * kVec);
         P.g = c.take<double>((size_t)nc * kVec);
-        P.pT = c.take<char>((size_t)nc * kVec * w);
+        P.pT = c.take<char>((size_t)nc * ((P.fp32 && !P.autodiff) ? kRow * 4 : kVec * w));
         P.p2 = c.take<double>((size_t)nc * kVec);
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
@@ -220,9 +220,10 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.fact = fact ? 1 : 0;
         P.PXpm = fact ? c.take<float>(3 * (size_t)P.npad) : nullptr;
         P.Jph = fact ? c.take<float>(6 * (size_t)P.npad) : nullptr;
-        P.PXcm = fact ? c.take<float>(3 * (size_t)P.npad) : nullptr;
-        P.zT = P.fp32 ? c.take<float>((size_t)nc * kVec) : nullptr;
-        P.pT2 = c.take<char>((size_t)nc * kVec * w);
+        P.RXcm = fact ? c.take<float>(4 * (size_t)P.npad) : nullptr;
+        // float copies of z and p (the factored form: their camera rows, kRow floats)
+        P.zT = P.fp32 ? c.take<float>((size_t)nc * (fact ? kRow : kVec)) : nullptr;
+        P.pT2 = c.take<char>((size_t)nc * (fact ? kRow * 4 : kVec * w));
         P.Jcm = P.fp32 ? nullptr : c.take<double>(18 * (size_t)P.npad);
         P.JcmT = P.fp32 ? (P.autodiff ? (void *)c.take<float>(18 * (size_t)P.npad) : nullptr) : (void *)P.Jcm;
         P.dp = c.take<double>(3 * (size_t)np);

@@ -149,14 +149,17 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             e[1] *= sw;
             // what the PCG camera pass reads in camera-major order: the stored
             // Jacobian (FP64, or any dual-number Jacobian), else the factored
-            // form's (px, py, 1/Pz)
+            // form's R X
             if ((sizeof(T) == 8 || AD) && P.JcmT) {
 #pragma unroll
                 for (int q = 0; q < 18; ++q) ((T *)P.JcmT)[(int64_t)q * P.npad + s] = Jc[q];
             }
             if (sizeof(T) == 4 && !AD && P.fact) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) P.PXcm[(int64_t)q * P.npad + s] = (float)pz[q];
+                const T X0 = (T)P.pts[3 * (int64_t)pt], X1 = (T)P.pts[3 * (int64_t)pt + 1],
+                        X2 = (T)P.pts[3 * (int64_t)pt + 2];
+                ((float4 *)P.RXcm)[s] = make_float4((float)(ctab[0] * X0 + ctab[1] * X1 + ctab[2] * X2),
+                                                    (float)(ctab[3] * X0 + ctab[4] * X1 + ctab[5] * X2),
+                                                    (float)(ctab[6] * X0 + ctab[7] * X1 + ctab[8] * X2), (float)pz[2]);
             }
             int idx = 0;
 #pragma unroll

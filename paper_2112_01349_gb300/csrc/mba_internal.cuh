@@ -17,6 +17,7 @@ constexpr int kBlock = 256;          // threads per CTA for every kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kCamTab = 28;          // values per camera in the camera table
 constexpr int kVec = 12;             // padded stride of 9-vectors per camera (16-B aligned rows)
+constexpr int kRow = 12;             // floats per camera row of the factored FP32 Schur product
 constexpr int kCamChunk = 256;       // observations per camera-major chunk (at least)
 constexpr int kMaxTrack = 1024;      // longest supported point track
 
@@ -101,11 +102,12 @@ struct Prob {
     void *pT2;      // FP32-mixed: second float search-direction buffer (alternate iterations)
     double *Jcm;    // FP64: [18][npad] sqrt(W)-scaled camera Jacobian, camera-major
     // FP32-mixed analytic (factored) form: per observation the normalised point
-    // and 1 / P_z, from which the PCG re-derives Jc p and Jc^T s with per-camera
-    // constants, and the W-scaled point Jacobian
+    // and 1 / P_z (point-major), the point rotated into the camera frame, R X,
+    // with 1 / P_z (camera-major), and the W-scaled point Jacobian, from which
+    // the PCG re-derives Jc p and Jc^T s with per-camera constants
     float *PXpm;    // [3][npad] (px, py, 1/Pz), point-major
     float *Jph;     // [6][npad] W Jp, point-major
-    float *PXcm;    // [3][npad] (px, py, 1/Pz), camera-major
+    float *RXcm;    // [npad] float4 (R X, 1/Pz), camera-major
     int32_t fact;   // 1: the PCG runs the factored form (FP32-mixed, analytic Jacobian)
     void *JcmT;     // [18][npad] sqrt(W)-scaled camera Jacobian in T, camera-major, that the PCG
                     // camera pass reads: Jcm in FP64; FP32-mixed with autodiff only (else null)

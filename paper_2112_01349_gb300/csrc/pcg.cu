@@ -467,18 +467,25 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
 // point, p = -(P_x, P_y) / P_z, r2 = |p|^2, d = 1 + k1 r2 + k2 r2^2 and
 // A = f (d I + (2 k1 + 4 k2 r2) p p^T), the BAL Jacobian of one observation is
 //   D = d(pixel)/dP = -(1/P_z) A [I | p],   Jp = D R,   Jc = [-D R [X]x M | D | p (d, f r2, f r2^2)]
-// (M: the rotation factor of the camera table).  Two identities make every
-// per-observation product depend only on (px, py, 1/P_z), the stored W Jp and
+// (M: the rotation factor of the camera table).  Because R (a x b) = R a x R b,
+// the two products the PCG needs reduce to per-observation data and
 // per-camera constants:
-//   Jc v = D (n x (P - t) + v_t) + p (d v_f + f r2 v_k1 + f r2^2 v_k2),  n = R M v_w,
-//   sum_k Jc_k^T s_k = [ (R M)^T sum_k (P_k - t) x D_k^T s_k ; sum_k D_k^T s_k ; ... ],
-// with P - t = P_z (-px, -py, 1).  The point pass streams 36 bytes per
-// observation instead of the 96-byte Jacobian; the camera pass reads 12 bytes
-// and applies (R M)^T once per chunk.  (In the first-order rotation branch,
-// |w|^2 <= 2.2e-16, this applies R = I + [w]x where the Jacobian has I: a
-// relative difference of at most |w|, below FP32 rounding.)
+//   Jc v = D (n x (P - t) + v_t) + p (d v_f + f r2 v_k1 + f r2^2 v_k2),   n = R M v_w,
+//   sum_k Jc_k^T s_k = [ (R M)^T sum_k RX_k x D_k^T s_k ; sum_k D_k^T s_k ;
+//                        (sum_k d p.s, f sum_k r2 p.s, f sum_k r2^2 p.s) ],
+// RX = R X = P - t.  The point pass streams (px, py, 1/P_z) and W Jp, 36 bytes
+// per observation instead of the 96-byte Jacobian, and forms
+// (n x (P - t) + v_t) / P_z = n x (-px, -py, 1) + h / P_z with the camera
+// constant h = v_t - n x t: one cancellation of order |t| / |RX| per
+// observation.  The camera pass reads (RX, 1/P_z) as one float4 and recomputes
+// p from P = RX + t, so its cross products, summed over a chunk of hundreds of
+// observations, use RX itself: forming them as P_z q - t instead would cancel
+// after the sum, and that loss broke the PCG near mu ~ 1e-7.
+// (In the first-order rotation branch, |w|^2 <= 2.2e-16, both apply
+// R = I + [w]x where the Jacobian has I: a relative difference of at most |w|,
+// below FP32 rounding.)
 //
-// Per-camera row of 12 floats for a vector v = (v_w, v_t, v_f, v_k1, v_k2):
+// Per-camera row of kRow = 12 floats for a vector v = (v_w, v_t, v_f, v_k1, v_k2):
 //   n = R M v_w, h = v_t - n x t, e = (v_f, f v_k1, f v_k2), then (f, k1, k2)
 //   (consts) or zeros.  The row is linear in v apart from the constants, so
 //   row(z) + beta row(p) with the constants carried by row(z) alone is the row
@@ -508,8 +515,8 @@ __device__ __forceinline__ void fact_row(const float *__restrict__ ct, const flo
 
 // Warp-collective (all 32 lanes call it): lanes 9s..9s+8 hold the nine
 // components of camera `cam` (lane s of the three-camera group); each active
-// lane writes its element of the camera's row to dst[cam][12] (lanes of rows
-// 0..2 also the pad elements 9..11).
+// lane writes its element of the camera's row to dst[cam][kRow] (lanes of rows
+// 0..2 also the elements 9..11).
 __device__ __forceinline__ void fact_row_store(const Prob &P, float *dst, int cam, bool act, double val, int sub,
                                                int row, bool consts) {
     const float fv = (float)val;
@@ -517,7 +524,7 @@ __device__ __forceinline__ void fact_row_store(const Prob &P, float *dst, int ca
 #pragma unroll
     for (int j = 0; j < 9; ++j) v[j] = __shfl_sync(0xffffffffu, fv, (9 * sub + j) & 31);
     if (!act) return;
-    float r[12];
+    float r[kRow];
     fact_row((const float *)P.camtab + (int64_t)cam * kCamTab, v, consts, r);
     float mine = r[0], pad = r[9];
 #pragma unroll
@@ -525,27 +532,29 @@ __device__ __forceinline__ void fact_row_store(const Prob &P, float *dst, int ca
         if (row == j) mine = r[j];
     if (row == 1) pad = r[10];
     if (row == 2) pad = r[11];
-    stcg(dst + (int64_t)cam * kVec + row, mine);
-    if (row < 3) stcg(dst + (int64_t)cam * kVec + 9 + row, pad);
+    stcg(dst + (int64_t)cam * kRow + row, mine);
+    if (row < 3) stcg(dst + (int64_t)cam * kRow + 9 + row, pad);
 }
 
-// The camera's row: shared memory (ps, [nc][12]) or the global copy.
+// The camera's row: shared memory (ps, [nc][kRow]) or the global copy.
 __device__ __forceinline__ void gather_row(const float *ps, const float *pT, int cam, float *r) {
-    float4 a, b, c;
+    float4 q[kRow / 4];
     if (ps) {
-        const float4 *src = (const float4 *)(ps + cam * 12);
-        a = src[0];
-        b = src[1];
-        c = src[2];
+        const float4 *src = (const float4 *)(ps + cam * kRow);
+#pragma unroll
+        for (int i = 0; i < kRow / 4; ++i) q[i] = src[i];
     } else {
-        const float4 *src = (const float4 *)(pT + (int64_t)cam * kVec);
-        a = __ldcg(src);
-        b = __ldcg(src + 1);
-        c = __ldcg(src + 2);
+        const float4 *src = (const float4 *)(pT + (int64_t)cam * kRow);
+#pragma unroll
+        for (int i = 0; i < kRow / 4; ++i) q[i] = __ldcg(src + i);
     }
-    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
-    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
-    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+#pragma unroll
+    for (int i = 0; i < kRow / 4; ++i) {
+        r[4 * i] = q[i].x;
+        r[4 * i + 1] = q[i].y;
+        r[4 * i + 2] = q[i].z;
+        r[4 * i + 3] = q[i].w;
+    }
 }
 
 // t = Jc v (unscaled) for one observation from (px, py, 1/Pz) and the camera's row.
@@ -555,7 +564,7 @@ __device__ __forceinline__ void fact_jc_v(float px, float py, float iz, const fl
     const float d = 1.f + k1 * r2 + k2 * r2 * r2;
     const float dd = 2.f * k1 + 4.f * k2 * r2;
     const float a00 = f * (d + dd * px * px), a01 = f * dd * px * py, a11 = f * (d + dd * py * py);
-    // (n x (P - t) + v_t) / P_z with P - t = P_z (-px, -py, 1)
+    // (n x (P - t) + v_t) / P_z = n x (-px, -py, 1) + h / P_z
     const float w0 = r[1] + r[2] * py + iz * r[3];
     const float w1 = -r[0] - r[2] * px + iz * r[4];
     const float w2 = r[1] * px - r[0] * py + iz * r[5];
@@ -623,7 +632,7 @@ __device__ void point_pass_fact(const Prob &P, const float *ps, const float *pT,
             } else {
                 float u[3] = {0.f, 0.f, 0.f};
                 if (act) {
-                    float r[12], t[2];
+                    float r[kRow], t[2];
                     gather_row(ps, pT, cam, r);
                     fact_jc_v(px, py, iz, r, t);
                     u[0] = jh[0] * t[0] + jh[3] * t[1];
@@ -667,7 +676,7 @@ __device__ void point_pass_fact(const Prob &P, const float *ps, const float *pT,
                 for (int base = 0; base < m; base += 32) {
                     if (base + lane < m) {
                         const int64_t o = (int64_t)o0 + base + lane;
-                        float r[12], t[2];
+                        float r[kRow], t[2];
                         gather_row(ps, pT, __ldcs(P.pm_cam + o), r);
                         fact_jc_v(__ldcs(PX + o), __ldcs(PX + npad + o), __ldcs(PX + 2 * npad + o), r, t);
 #pragma unroll
@@ -759,9 +768,11 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         T acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
-        // factored form: the camera's f, k1, k2 for every observation of the chunk
-        float cf = 0.f, ck1 = 0.f, ck2 = 0.f;
+        // factored form: the camera's t_x, t_y, f, k1, k2 for every observation of the chunk
+        float ct0 = 0.f, ct1 = 0.f, cf = 0.f, ck1 = 0.f, ck2 = 0.f;
         if (FACT) {
+            ct0 = (float)ct[18];
+            ct1 = (float)ct[19];
             cf = (float)ct[21];
             ck1 = (float)ct[22];
             ck2 = (float)ct[23];
@@ -770,7 +781,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
             // s arrives in camera-major order (the point pass scattered it), so
             // every load of the batch is a coalesced stream
             bool in[U];
-            float px[U], py[U], iz[U];
+            float rx0[U], rx1[U], rx2[U], rz[U];  // R X and 1 / P_z
             T2 sv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -778,30 +789,35 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 in[u] = s < b1;
                 if (in[u]) sv[u] = ldcg(sbuf + s);
                 if (FACT) {
-                    px[u] = in[u] ? __ldcs(P.PXcm + s) : 0.f;
-                    py[u] = in[u] ? __ldcs(P.PXcm + P.npad + s) : 0.f;
-                    iz[u] = in[u] ? __ldcs(P.PXcm + 2 * P.npad + s) : 0.f;
+                    const float4 v = in[u] ? __ldcs((const float4 *)P.RXcm + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    rx0[u] = v.x;
+                    rx1[u] = v.y;
+                    rx2[u] = v.z;
+                    rz[u] = v.w;
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (in[u]) {
                     if (FACT) {
-                        // g = A s, D^T s = -(1/Pz) (g0, g1, p.g); accumulate D^T s,
-                        // q x (g0, g1, p.g) with q = (-px, -py, 1), and p.s (d, r2, r2^2)
-                        const float x = px[u], y = py[u], s0v = (float)sv[u].x, s1v = (float)sv[u].y;
+                        // y_t = D^T s = -(1/Pz) (g0, g1, p.g) with g = A s; accumulate
+                        // y_t, RX x y_t, and p.s (d, r2, r2^2)
+                        const float X0 = rx0[u], X1 = rx1[u], X2 = rx2[u];
+                        const float s0v = (float)sv[u].x, s1v = (float)sv[u].y;
+                        const float iz = rz[u];
+                        const float x = -(X0 + ct0) * iz, y = -(X1 + ct1) * iz;
                         const float r2 = x * x + y * y;
                         const float d = 1.f + ck1 * r2 + ck2 * r2 * r2;
                         const float dd = 2.f * ck1 + 4.f * ck2 * r2;
                         const float a00 = cf * (d + dd * x * x), a01 = cf * dd * x * y, a11 = cf * (d + dd * y * y);
-                        const float g0 = a00 * s0v + a01 * s1v, g1 = a01 * s0v + a11 * s1v, g2 = x * g0 + y * g1;
-                        const float mz = -iz[u];
-                        acc[0] += (T)(mz * g0);
-                        acc[1] += (T)(mz * g1);
-                        acc[2] += (T)(mz * g2);
-                        acc[3] += (T)(-y * g2 - g1);
-                        acc[4] += (T)(g0 + x * g2);
-                        acc[5] += (T)(y * g0 - x * g1);
+                        const float g0 = a00 * s0v + a01 * s1v, g1 = a01 * s0v + a11 * s1v;
+                        const float y0 = -iz * g0, y1 = -iz * g1, y2 = x * y0 + y * y1;
+                        acc[0] += (T)y0;
+                        acc[1] += (T)y1;
+                        acc[2] += (T)y2;
+                        acc[3] += (T)(X1 * y2 - X2 * y1);
+                        acc[4] += (T)(X2 * y0 - X0 * y2);
+                        acc[5] += (T)(X0 * y1 - X1 * y0);
                         const float pss = x * s0v + y * s1v;
                         acc[6] += (T)(d * pss);
                         acc[7] += (T)(r2 * pss);
@@ -822,13 +838,10 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
             else if (lane == a) mine = v;
         }
         if (FACT) {
-            // Jc^T s of the chunk: rotation (R M)^T (-Cq - t x Yt), translation Yt,
-            // intrinsics (Yi0, f Yi1, f Yi2)
-            const float t0 = (float)ct[18], t1 = (float)ct[19], t2 = (float)ct[20];
+            // Jc^T s of the chunk: rotation (R M)^T sum RX x y_t, translation
+            // sum y_t, intrinsics (sum d p.s, f sum r2 p.s, f sum r2^2 p.s)
             const float Y0 = (float)acc[0], Y1 = (float)acc[1], Y2 = (float)acc[2];
-            const float c0 = -(float)acc[3] - (t1 * Y2 - t2 * Y1);
-            const float c1 = -(float)acc[4] - (t2 * Y0 - t0 * Y2);
-            const float c2 = -(float)acc[5] - (t0 * Y1 - t1 * Y0);
+            const float c0 = (float)acc[3], c1 = (float)acc[4], c2 = (float)acc[5];
             const float q0 = ct[0] * c0 + ct[3] * c1 + ct[6] * c2;  // R^T c
             const float q1 = ct[1] * c0 + ct[4] * c1 + ct[7] * c2;
             const float q2 = ct[2] * c0 + ct[5] * c1 + ct[8] * c2;
@@ -921,7 +934,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 // (p = z on the first iteration), or the given FP64 p (src_given).  The FP32
 // form builds it from float copies of z and p_prev with float4 loads; the FP64
 // form from the FP64 vectors, as the camera pass does.
-// Factored form: the camera rows (12 floats, [nc][12]) instead: row(z) + beta
+// Factored form: the camera rows ([nc][kRow] floats) instead: row(z) + beta
 // row(p_prev) from the float row copies, or the rows of the given FP64 p.
 template <typename T, bool FACT>
 __device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_prev, double beta, bool first,
@@ -931,7 +944,7 @@ __device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_
         if (!src_given) {
             const float4 *z4 = (const float4 *)P.zT, *p4 = (const float4 *)pT_prev;
             const float fb = (float)beta;
-            const int nq = P.nc * 3;  // three float4 per camera row
+            const int nq = P.nc * (kRow / 4);  // float4 per camera row
             for (int e = threadIdx.x; e < nq; e += blockDim.x) {
                 const float4 zv = __ldcg(z4 + e);
                 float4 v = zv;
@@ -944,13 +957,13 @@ __device__ void stage_p(const Prob &P, T *ps, const double *p_prev, const T *pT_
             }
         } else {
             for (int cam = threadIdx.x; cam < P.nc; cam += blockDim.x) {
-                float v[9], r[12];
+                float v[9], r[kRow];
 #pragma unroll
                 for (int j = 0; j < 9; ++j) v[j] = (float)src_given[(int64_t)cam * kVec + j];
                 fact_row((const float *)P.camtab + (int64_t)cam * kCamTab, v, true, r);
-                dst[3 * cam] = make_float4(r[0], r[1], r[2], r[3]);
-                dst[3 * cam + 1] = make_float4(r[4], r[5], r[6], r[7]);
-                dst[3 * cam + 2] = make_float4(r[8], r[9], r[10], r[11]);
+#pragma unroll
+                for (int i = 0; i < kRow / 4; ++i)
+                    dst[(kRow / 4) * cam + i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
             }
         }
         __syncthreads();
@@ -1384,7 +1397,7 @@ cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *
 // gathers p from global memory and an extra barrier is needed.
 void plan_pcg_smem(Prob &P) {
     const int w = P.fp32 ? 4 : 8;
-    const int per_cam = P.fact ? 12 : 9;  // the factored form stages a 12-float row per camera
+    const int per_cam = P.fact ? kRow : 9;  // the factored form stages a kRow-float row per camera
     const int64_t budget = 227 * 1024 - 12 * 1024;
     const int64_t slots = (int64_t)P.pcg_max_cta_chunks * 9 * 8;
     const int64_t psb = (((int64_t)P.nc * per_cam * w) + 127) & ~(int64_t)127;
