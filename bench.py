@@ -98,7 +98,10 @@ def batch_flops(ws, summaries, schur: str) -> float:
 # written over 31 passes of 1,501,396 observations; FP64: 16.32 GB + 52.1 MB).
 # Traffic grows with the observation count, so a full launch moves this many
 # bytes per observation per pass.
-PCG_TRAFFIC_B_PER_OBS_PASS = {4: (5.317e9 + 32.1e6) / 31 / 1501396, 8: (16.32e9 + 52.1e6) / 31 / 1501396}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one PCG launch (30 iterations
+# plus the right-hand-side pass) on the full Venice-shaped problem, per observation
+# per pass (profiles/pcg_kernel_fp32_venice.md, profiles/pcg_kernel_fp64_venice.md)
+PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9384019200 + 100877568) / 31 / 5004484, 8: (63971187456 + 3471845376) / 31 / 5004484}
 
 
 def pcg_flops_per_iter(sc) -> float:
@@ -342,6 +345,7 @@ def main():
         return dict(value=value, ms_per_step=ms / args.steps, pcg_ms=pcg_ms, pcg_iters=pcg_iters,
                     pcg_launches=launches, gbs=alg_bytes / (pcg_ms / 1e3) / 1e9,
                     traffic_per_launch=PCG_TRAFFIC_B_PER_OBS_PASS[w] * sc.n * (pcg_iters + launches) / launches,
+                    dram_gbs=PCG_TRAFFIC_B_PER_OBS_PASS[w] * sc.n * (pcg_iters + launches) / (pcg_ms / 1e3) / 1e9,
                     alg_bytes_per_launch=alg_bytes / launches,
                     tflops=alg_flops / (pcg_ms / 1e3) / 1e12,
                     us_per_pcg_iter=1e3 * pcg_ms / max(1, pcg_iters + launches),
@@ -558,9 +562,12 @@ def main():
         "roofline": {"kernel": "pcg_kernel (persistent PCG, implicit Schur product)", "bound": "hbm",
                      "achieved": a32["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": a32["gbs"] / hbm_peak,
                      "peak_kind": peak_kind, "traffic": a32["traffic_per_launch"],
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write per observation per pass on the "
-                                     "0.3-scale case, scaled by observations and passes; profiles/)",
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write per observation per pass of a "
+                                     "full-size launch, times this run's observations and passes; profiles/)",
                      "algorithmic_bytes_per_launch": a32["alg_bytes_per_launch"],
+                     "algorithmic": "stored-Jacobian count: 100 B per observation per pass plus per-point and "
+                                    "per-camera terms; the factored FP32 product streams fewer bytes than that",
+                     "dram_gbs": a32["dram_gbs"], "dram_frac": a32["dram_gbs"] / hbm_peak,
                      "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"]},
         "fp64": {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms_per_step"],
                  "final_cost": a64["final_cost"],
