@@ -557,7 +557,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": a32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64 (FP32-mixed)", "data": "synthetic",
         "config": {"workload": workload_desc(sc), "precision": "fp32-mixed",
-                   "l2": "inputs larger than L2 (Jacobian stream 0.48 GB FP32 / 0.96 GB FP64 per pass)",
+                   "l2": "inputs larger than L2 (per PCG pass: 0.26 GB streamed FP32, 1.7 GB FP64)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"kernel": "pcg_kernel (persistent PCG, implicit Schur product)", "bound": "hbm",
                      "achieved": a32["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": a32["gbs"] / hbm_peak,
