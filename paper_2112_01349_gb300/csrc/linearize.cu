@@ -116,24 +116,27 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
     }
 }
 
+// One warp per camera chunk: each lane accumulates the 54 block terms of its
+// observations, then one shuffle tree per chunk (a CTA-wide reduction per
+// chunk of a few hundred observations cost as much as the Jacobians).
 template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
-    __shared__ T ctab[kCamTab];
-    __shared__ double red[kWarps][54];
+    __shared__ T ctabs[kWarps][kCamTab];
     const T *__restrict__ camtab = (const T *)P.camtab;
     const T delta = (T)P.delta;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int c = blockIdx.x; c < P.n_cchunks; c += gridDim.x) {
+    T *ctab = ctabs[wid];
+    for (int c = blockIdx.x * kWarps + wid; c < P.n_cchunks; c += gridDim.x * kWarps) {
         const int cam = P.cchunk_cam[c];
         const int b0 = P.cchunk_beg[c], b1 = P.cchunk_beg[c + 1];
-        __syncthreads();
-        if (threadIdx.x < kCamTab) ctab[threadIdx.x] = camtab[(int64_t)cam * kCamTab + threadIdx.x];
-        __syncthreads();
+        __syncwarp();
+        if (lane < kCamTab) ctab[lane] = camtab[(int64_t)cam * kCamTab + lane];
+        __syncwarp();
         T acc[54];
 #pragma unroll
         for (int q = 0; q < 54; ++q) acc[q] = T(0);
-        for (int s = b0 + threadIdx.x; s < b1; s += kBlock) {
+        for (int s = b0 + lane; s < b1; s += 32) {
             const int pt = P.cm_pt[s];
             const double2 uv = P.cm_uv[s];
             T e[2], Jc[18], Jp[6], pz[3];
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             e[1] *= sw;
             // what the PCG camera pass reads in camera-major order: the stored
             // Jacobian (FP64, or any dual-number Jacobian), else the factored
-            // form's R X
+            // form's (R X, 1/Pz)
             if ((sizeof(T) == 8 || AD) && P.JcmT) {
 #pragma unroll
                 for (int q = 0; q < 18; ++q) ((T *)P.JcmT)[(int64_t)q * P.npad + s] = Jc[q];
@@ -169,19 +172,20 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[45 + a] -= Jc[a] * e[0] + Jc[9 + a] * e[1];
         }
+        // lane q (and q - 32) ends with sum q
+        double mine0 = 0.0, mine1 = 0.0;
 #pragma unroll
         for (int q = 0; q < 54; ++q) {
             T v = acc[q];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[wid][q] = (double)v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (q & 31)) {
+                if (q < 32) mine0 = (double)v;
+                else mine1 = (double)v;
+            }
         }
-        __syncthreads();
-        if (threadIdx.x < 54) {
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-            P.cpart[54 * (int64_t)c + threadIdx.x] = s;
-        }
+        P.cpart[54 * (int64_t)c + lane] = mine0;
+        if (lane < 22) P.cpart[54 * (int64_t)c + 32 + lane] = mine1;
     }
 }
 
@@ -290,7 +294,9 @@ static void launch_lin_pair(const Prob &P, int force, cudaStream_t s) {
         attr_done = true;
     }
     lin_point_kernel<T, AD><<<nb, kBlock, sm, s>>>(P, force);
-    lin_camera_kernel<T, AD><<<nb, kBlock, 0, s>>>(P, force);
+    int nbc = (P.n_cchunks + kWarps - 1) / kWarps;
+    if (nbc > 152 * 16) nbc = 152 * 16;
+    lin_camera_kernel<T, AD><<<nbc < 1 ? 1 : nbc, kBlock, 0, s>>>(P, force);
 }
 
 cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s) {

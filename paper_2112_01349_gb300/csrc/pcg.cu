@@ -31,53 +31,89 @@ __device__ __forceinline__ double current_mu(const DevState *st) {
     return st->mu_override >= 0.0 ? st->mu_override : 1.0 / st->radius;
 }
 
-__global__ void damp_cameras_kernel(Prob P, int damping) {
+// Warp-collective inverse of a symmetric positive definite 9x9 matrix in FP64.
+// A (shared memory, 81 doubles, both triangles set) is overwritten by its
+// lower Cholesky factor (right-looking: lane-parallel column scaling and
+// trailing update), Y (shared, 81) receives L^-1 by forward substitution, one
+// column per lane, and inv (global, row-major) = L^-T L^-1.  Returns false on
+// every lane, writing nothing, if a pivot is not positive.  The chains are
+// short (about 9 steps per column) where one thread per matrix would run
+// hundreds of dependent FP64 operations.
+__device__ bool warp_spd_inverse9(double *A, double *Y, double *il, double *inv) {
+    const int lane = threadIdx.x & 31;
+    // this lane's lower-triangle entries (r >= c) of the trailing updates
+    int e_r[2], e_c[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        int r = 0;
+        while (r < 9 && (r + 1) * (r + 2) / 2 <= e) ++r;
+        e_r[h] = r;
+        e_c[h] = e - r * (r + 1) / 2;
+    }
+    for (int j = 0; j < 9; ++j) {
+        __syncwarp();
+        const double d = A[j * 9 + j];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        const double l = sqrt(d), ilj = 1.0 / l;
+        __syncwarp();
+        if (lane == 0) {
+            A[j * 9 + j] = l;
+            il[j] = ilj;
+        }
+        if (lane > j && lane < 9) A[lane * 9 + j] *= ilj;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = e_r[h], c = e_c[h];
+            if (lane + 32 * h < 45 && c > j) A[r * 9 + c] -= A[r * 9 + j] * A[c * 9 + j];
+        }
+    }
+    __syncwarp();
+    if (lane < 9) {  // column `lane` of L^-1 (rows >= lane)
+        const int c = lane;
+        for (int r = 0; r < 9; ++r) {
+            if (r < c) {
+                Y[r * 9 + c] = 0.0;
+                continue;
+            }
+            double s = r == c ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) s -= A[r * 9 + k] * Y[k * 9 + c];
+            Y[r * 9 + c] = s * il[r];
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < 81; e += 32) {
+        const int r = e / 9, c = e - 9 * (e / 9), k0 = r > c ? r : c;
+        double s = 0.0;
+        for (int k = k0; k < 9; ++k) s += Y[k * 9 + r] * Y[k * 9 + c];
+        inv[e] = s;
+    }
+    return true;
+}
+
+// One warp per camera: B~ (full, stored for the PCG's B~ p) and its inverse.
+constexpr int kDampWarps = 4;
+__global__ void __launch_bounds__(32 * kDampWarps) damp_cameras_kernel(Prob P, int damping) {
+    __shared__ double sA[kDampWarps][81], sY[kDampWarps][81], sil[kDampWarps][9];
     DevState *st = P.st;
     if (st->done) return;
     const double mu = current_mu(st);
     if (blockIdx.x == 0 && threadIdx.x == 0) st->mu = mu;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nc; i += gridDim.x * blockDim.x) {
-        double A[81];
-#pragma unroll
-        for (int a = 0; a < 9; ++a)
-#pragma unroll
-            for (int b = 0; b < 9; ++b) A[a * 9 + b] = P.Hpp[45 * (int64_t)i + sym9(a, b)];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) A[a * 10] += mu * damp_term(damping, A[a * 10]);
-        for (int q = 0; q < 81; ++q) P.Bd[81 * (int64_t)i + q] = A[q];
-        // lower Cholesky in place
-        bool ok = true;
-        for (int j = 0; j < 9; ++j) {
-            double s = A[j * 9 + j];
-            for (int k = 0; k < j; ++k) s -= A[j * 9 + k] * A[j * 9 + k];
-            if (!(s > 0.0)) { ok = false; break; }
-            const double l = sqrt(s);
-            A[j * 9 + j] = l;
-            for (int r = j + 1; r < 9; ++r) {
-                double t = A[r * 9 + j];
-                for (int k = 0; k < j; ++k) t -= A[r * 9 + k] * A[j * 9 + k];
-                A[r * 9 + j] = t / l;
-            }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = blockIdx.x * kDampWarps + wid; i < P.nc; i += gridDim.x * kDampWarps) {
+        double *A = sA[wid];
+        __syncwarp();
+        for (int e = lane; e < 81; e += 32) {
+            const int a = e / 9, b = e - 9 * (e / 9);
+            double v = P.Hpp[45 * (int64_t)i + sym9(a, b)];
+            if (a == b) v += mu * damp_term(damping, v);
+            A[e] = v;
+            P.Bd[81 * (int64_t)i + e] = v;
         }
-        if (!ok) {
+        __syncwarp();
+        if (!warp_spd_inverse9(A, sY[wid], sil[wid], P.Binv + 81 * (int64_t)i) && lane == 0)
             atomicCAS(&st->err, 0, (int)MBA_ERR_NONFINITE);
-            continue;
-        }
-        // inverse = L^-T L^-1, column by column
-        for (int col = 0; col < 9; ++col) {
-            double y[9];
-            for (int r = 0; r < 9; ++r) {
-                double s = (r == col) ? 1.0 : 0.0;
-                for (int k = 0; k < r; ++k) s -= A[r * 9 + k] * y[k];
-                y[r] = s / A[r * 9 + r];
-            }
-            for (int r = 8; r >= 0; --r) {
-                double s = y[r];
-                for (int k = r + 1; k < 9; ++k) s -= A[k * 9 + r] * y[k];
-                y[r] = s / A[r * 9 + r];
-            }
-            for (int r = 0; r < 9; ++r) P.Binv[81 * (int64_t)i + r * 9 + col] = y[r];
-        }
     }
 }
 
@@ -185,51 +221,21 @@ __global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
     }
 }
 
-__global__ void sj_finalize_kernel(Prob P, const int32_t *__restrict__ cfirst) {
+__global__ void __launch_bounds__(32 * kDampWarps) sj_finalize_kernel(Prob P, const int32_t *__restrict__ cfirst) {
+    __shared__ double sA[kDampWarps][81], sY[kDampWarps][81], sil[kDampWarps][9];
     if (P.st->done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nc; i += gridDim.x * blockDim.x) {
-        double A[81];
-        for (int q = 0; q < 81; ++q) A[q] = P.Bd[81 * (int64_t)i + q];
-        for (int a = 0; a < 9; ++a)
-            for (int b = a; b < 9; ++b) {
-                double s = 0.0;
-                for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) s += P.cpart[54 * (int64_t)c + sym9(a, b)];
-                A[a * 9 + b] -= s;
-                if (b != a) A[b * 9 + a] -= s;
-            }
-        bool ok = true;
-        double il[9];
-        for (int j = 0; j < 9 && ok; ++j) {
-            double s = A[j * 9 + j];
-            for (int k = 0; k < j; ++k) s -= A[j * 9 + k] * A[j * 9 + k];
-            if (!(s > 0.0) || !isfinite(s)) {
-                ok = false;
-                break;
-            }
-            const double l = sqrt(s);
-            il[j] = 1.0 / l;
-            A[j * 9 + j] = l;
-            for (int r = j + 1; r < 9; ++r) {
-                double t = A[r * 9 + j];
-                for (int k = 0; k < j; ++k) t -= A[r * 9 + k] * A[j * 9 + k];
-                A[r * 9 + j] = t * il[j];
-            }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = blockIdx.x * kDampWarps + wid; i < P.nc; i += gridDim.x * kDampWarps) {
+        double *A = sA[wid];
+        __syncwarp();
+        for (int e = lane; e < 81; e += 32) {
+            const int a = e / 9, b = e - 9 * (e / 9);
+            double sum = 0.0;
+            for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) sum += P.cpart[54 * (int64_t)c + sym9(a, b)];
+            A[e] = P.Bd[81 * (int64_t)i + e] - sum;
         }
-        if (!ok) continue;  // keep B~_i^-1
-        for (int col = 0; col < 9; ++col) {
-            double y[9];
-            for (int r = 0; r < 9; ++r) {
-                double s = (r == col) ? 1.0 : 0.0;
-                for (int k = 0; k < r; ++k) s -= A[r * 9 + k] * y[k];
-                y[r] = s * il[r];
-            }
-            for (int r = 8; r >= 0; --r) {
-                double s = y[r];
-                for (int k = r + 1; k < 9; ++k) s -= A[k * 9 + r] * y[k];
-                y[r] = s * il[r];
-            }
-            for (int r = 0; r < 9; ++r) P.Binv[81 * (int64_t)i + r * 9 + col] = y[r];
-        }
+        __syncwarp();
+        warp_spd_inverse9(A, sY[wid], sil[wid], P.Binv + 81 * (int64_t)i);  // not PD: B~_i^-1 stays
     }
 }
 
@@ -1373,7 +1379,7 @@ bool g_pcg_attr[2] = {false, false};
 }  // namespace
 
 cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *cfirst, cudaStream_t s) {
-    damp_cameras_kernel<<<(P.nc + 127) / 128, 128, 0, s>>>(P, damping);
+    damp_cameras_kernel<<<(P.nc + kDampWarps - 1) / kDampWarps, 32 * kDampWarps, 0, s>>>(P, damping);
     const int64_t nb = (P.np + kBlock - 1) / kBlock;
     const unsigned g = (unsigned)(nb > 152 * 16 ? 152 * 16 : nb);
     if (P.fp32) damp_points_kernel<float><<<g, kBlock, 0, s>>>(P, damping);
@@ -1387,7 +1393,7 @@ cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *
             if (P.autodiff) sj_camera_kernel<double, true><<<gc, kBlock, 0, s>>>(P);
             else sj_camera_kernel<double, false><<<gc, kBlock, 0, s>>>(P);
         }
-        sj_finalize_kernel<<<(P.nc + 63) / 64, 64, 0, s>>>(P, cfirst);
+        sj_finalize_kernel<<<(P.nc + kDampWarps - 1) / kDampWarps, 32 * kDampWarps, 0, s>>>(P, cfirst);
     }
     return cudaGetLastError();
 }
