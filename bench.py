@@ -568,7 +568,8 @@ def main():
                      "algorithmic": "stored-Jacobian count: 100 B per observation per pass plus per-point and "
                                     "per-camera terms; the factored FP32 product streams fewer bytes than that",
                      "dram_gbs": a32["dram_gbs"], "dram_frac": a32["dram_gbs"] / hbm_peak,
-                     "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"]},
+                     "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"],
+                     "pcg_iters_per_solve": a32["pcg_iters"] / max(1, len(s32))},
         "fp64": {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms_per_step"],
                  "final_cost": a64["final_cost"],
                  "roofline": {"kernel": "pcg_kernel<double>", "bound": "alu", "achieved": a64["tflops"],

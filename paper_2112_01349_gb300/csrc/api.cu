@@ -150,6 +150,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     P.loss = o.loss;
     P.delta = o.huber_delta;
     P.autodiff = o.jacobian == MBA_JACOBIAN_AUTODIFF;
+    P.fact = (P.fp32 && !P.autodiff) ? 1 : 0;  // FP32-mixed analytic: the factored Schur product
     const size_t w = P.fp32 ? 4 : 8;
     const int64_t pbound = (n + 512) / 513 + 2;                 // point chunks (stride >= 513)
     const int64_t cbound = n / kCamChunk + (int64_t)nc + 2;     // camera chunks
@@ -191,7 +192,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         pr->orig_cam = c.take<int32_t>(n);
         pr->orig_pt = c.take<int32_t>(n);
         pr->orig_uv = c.take<double2>(n);
-        P.J = c.take<char>(24 * (size_t)P.npad * w);
+        P.J = P.fact ? nullptr : c.take<char>(24 * (size_t)P.npad * w);
         P.res = c.take<char>(2 * (size_t)P.npad * w);
         P.camtab = c.take<char>((size_t)nc * kCamTab * w);
         P.camtab64 = c.take<double>((size_t)nc * kCamTab);
@@ -216,11 +217,11 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.pm2cm = c.take<int32_t>(n);
         // copies for the PCG: the camera-major stored Jacobian (FP64, or FP32-mixed
         // with dual numbers), else the factored form's per-observation data
-        const bool fact = P.fp32 && !P.autodiff;
-        P.fact = fact ? 1 : 0;
+        const bool fact = P.fact != 0;
         P.PXpm = fact ? c.take<float>(3 * (size_t)P.npad) : nullptr;
         P.Jph = fact ? c.take<float>(6 * (size_t)P.npad) : nullptr;
         P.RXcm = fact ? c.take<float>(4 * (size_t)P.npad) : nullptr;
+        P.swpm = (fact && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
         // float copies of z and p (the factored form: their camera rows, kRow floats)
         P.zT = P.fp32 ? c.take<float>((size_t)nc * (fact ? kRow : kVec)) : nullptr;
         P.pT2 = c.take<char>((size_t)nc * (fact ? kRow * 4 : kVec * w));
@@ -390,7 +391,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     CKC(cudaMemcpyAsync(P.cams0, P.cams, sizeof(double) * 9 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
     CKC(cudaMemcpyAsync(P.pts0, P.pts, sizeof(double) * 3 * (size_t)np, cudaMemcpyDeviceToDevice, s));
     CKC(cudaMemsetAsync(P.st, 0, sizeof(DevState), s));
-    CKC(cudaMemsetAsync(P.J, 0, 24 * (size_t)P.npad * w, s));
+    if (P.J) CKC(cudaMemsetAsync(P.J, 0, 24 * (size_t)P.npad * w, s));
     CKC(cudaMemsetAsync(P.res, 0, 2 * (size_t)P.npad * w, s));
     CKC(cudaStreamSynchronize(s));
     cudaFree(tmp);

@@ -43,6 +43,7 @@ __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc,
 
 template <typename T, bool AD>
 __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
+    constexpr bool FACT = sizeof(T) == 4 && !AD;  // FP32-mixed analytic: no stored Jacobian
     if (!force && (P.st->done || !P.st->relin)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *slot = reinterpret_cast<T *>(smem_raw);  // [9][cap]
@@ -63,25 +64,25 @@ __global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
             T e[2], Jc[18], Jp[6], pz[3];
             edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
                              (T)P.pts[3 * (int64_t)pt + 1], (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc,
-                             Jp, (sizeof(T) == 4 && !AD) ? pz : nullptr);
+                             Jp, FACT ? pz : nullptr);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);
 #pragma unroll
-            for (int q = 0; q < 18; ++q) {
-                Jc[q] *= sw;
-                J[q * np_ + o] = Jc[q];
-            }
+            for (int q = 0; q < 18; ++q) Jc[q] *= sw;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                Jp[q] *= sw;
-                J[(18 + q) * np_ + o] = Jp[q];
-            }
-            if (sizeof(T) == 4 && !AD && P.fact) {  // factored form: (px, py, 1/Pz) and W Jp
+            for (int q = 0; q < 6; ++q) Jp[q] *= sw;
+            if (FACT) {  // factored form: (px, py, 1/Pz), W Jp and, with a loss, sqrt(W)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) P.PXpm[q * np_ + o] = (float)pz[q];
 #pragma unroll
                 for (int q = 0; q < 6; ++q) P.Jph[q * np_ + o] = (float)(sw * Jp[q]);
+                if (P.swpm) P.swpm[o] = (float)sw;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) J[q * np_ + o] = Jc[q];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) J[(18 + q) * np_ + o] = Jp[q];
             }
             e[0] *= sw;
             e[1] *= sw;

@@ -89,7 +89,7 @@ struct Prob {
     int32_t pcg_ps_bytes;          // shared-memory bytes of the search-direction copy
 
     // per-linearisation data (T = float in FP32-mixed, double otherwise)
-    void *J;        // [24][npad] sqrt(W)-scaled Jacobian, point-major
+    void *J;        // [24][npad] sqrt(W)-scaled Jacobian, point-major (null in the factored form)
     void *res;      // [2][npad]  sqrt(W)-scaled residual
     void *camtab;   // [nc][kCamTab] camera table in T (lin kernels)
     double *camtab64;  // [nc][kCamTab] FP64 camera table (cost evaluation)
@@ -108,6 +108,7 @@ struct Prob {
     float *PXpm;    // [3][npad] (px, py, 1/Pz), point-major
     float *Jph;     // [6][npad] W Jp, point-major
     float *RXcm;    // [npad] float4 (R X, 1/Pz), camera-major
+    float *swpm;    // [npad] sqrt(W), point-major (factored form with a robust loss; else null)
     int32_t fact;   // 1: the PCG runs the factored form (FP32-mixed, analytic Jacobian)
     void *JcmT;     // [18][npad] sqrt(W)-scaled camera Jacobian in T, camera-major, that the PCG
                     // camera pass reads: Jcm in FP64; FP32-mixed with autodiff only (else null)
@@ -362,8 +363,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
 }
 
 // Bounded grid barrier for cooperative (co-resident) launches.  Arrivals
-// increment a monotone counter; the k-th barrier completes when it reaches
-// k * gridDim.x.  A CTA that polls more than `limit` times, or sees the error
+// increment a monotone counter (release); the k-th barrier completes when an
+// acquire load sees k * gridDim.x.  A CTA that polls more than `limit` times, or sees the error
 // flag raised, records MBA_ERR_TIMEOUT and returns false; the caller must
 // then leave the kernel.  Returns true when every CTA has arrived.
 __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long long limit) {
@@ -372,9 +373,11 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long
     epoch += 1;
     if (threadIdx.x == 0) {
         const uint32_t target = epoch * gridDim.x;
-        __threadfence();
         unsigned int *ctr = reinterpret_cast<unsigned int *>(&st->barrier);
-        atomicAdd(ctr, 1u);
+        // release: the CTA's writes (ordered before this thread by the block
+        // barrier above) become visible to every CTA whose acquire load below
+        // sees this arrival
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
         int ok = 1;
         long long polls = 0;
         for (;;) {
@@ -388,9 +391,8 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(16);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

@@ -1274,13 +1274,19 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
 // candidate points, and the model decrease sum_k (-e~_k.d_k - |d_k|^2/2)
 // with d_k = Jc~_k dc + Jp~_k dp.
 // ---------------------------------------------------------------------------
-template <typename T>
+// FACT (FP32-mixed analytic): t = Jc dc from the camera rows of dc (formed by
+// fact_rows_kernel into the free search-direction buffer) and (px, py, 1/Pz),
+// Jp~^T Jc~ dc = (W Jp)^T t, and d~ = sqrt(W) t + (W Jp) dp / sqrt(W).
+template <typename T, bool FACT>
 __global__ void __launch_bounds__(kBlock) backsub_kernel(Prob P, double *partial) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sl = reinterpret_cast<T *>(smem_raw);
     __shared__ double sb[kWarps];
     if (P.st->done) return;
     const T *__restrict__ J = (const T *)P.J;
+    const float *__restrict__ rowsx = (const float *)P.pT;
+    const float *__restrict__ PX = P.PXpm;
+    const float *__restrict__ Jh = P.Jph;
     const T *__restrict__ res = (const T *)P.res;
     const T *__restrict__ Cinv = (const T *)P.Cinv;
     const int cap = P.cap;
@@ -1293,19 +1299,30 @@ __global__ void __launch_bounds__(kBlock) backsub_kernel(Prob P, double *partial
         for (int k = threadIdx.x; k < m; k += kBlock) {
             const int64_t o = (int64_t)o0 + k;
             const int cam = P.pm_cam[o];
-            T Jc[18], Jp[6];
-            load_jac(J, npad, o, Jc, Jp);
-            const double *xc = P.x + (int64_t)cam * kVec;
-            T t0 = T(0), t1 = T(0);
+            if constexpr (FACT) {
+                float r[kRow], t[2], jh[6];
+                gather_row(nullptr, rowsx, cam, r);
+                fact_jc_v(__ldg(PX + o), __ldg(PX + npad + o), __ldg(PX + 2 * npad + o), r, t);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const T xa = (T)xc[a];
-                t0 += Jc[a] * xa;
-                t1 += Jc[9 + a] * xa;
+                for (int q = 0; q < 6; ++q) jh[q] = __ldg(Jh + q * npad + o);
+                sl[0 * cap + k] = jh[0] * t[0] + jh[3] * t[1];
+                sl[1 * cap + k] = jh[1] * t[0] + jh[4] * t[1];
+                sl[2 * cap + k] = jh[2] * t[0] + jh[5] * t[1];
+            } else {
+                T Jc[18], Jp[6];
+                load_jac(J, npad, o, Jc, Jp);
+                const double *xc = P.x + (int64_t)cam * kVec;
+                T t0 = T(0), t1 = T(0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const T xa = (T)xc[a];
+                    t0 += Jc[a] * xa;
+                    t1 += Jc[9 + a] * xa;
+                }
+                sl[0 * cap + k] = Jp[0] * t0 + Jp[3] * t1;
+                sl[1 * cap + k] = Jp[1] * t0 + Jp[4] * t1;
+                sl[2 * cap + k] = Jp[2] * t0 + Jp[5] * t1;
             }
-            sl[0 * cap + k] = Jp[0] * t0 + Jp[3] * t1;
-            sl[1 * cap + k] = Jp[1] * t0 + Jp[4] * t1;
-            sl[2 * cap + k] = Jp[2] * t0 + Jp[5] * t1;
         }
         __syncthreads();
         for (int j = j0 + threadIdx.x; j < j1; j += kBlock) {
@@ -1335,16 +1352,28 @@ __global__ void __launch_bounds__(kBlock) backsub_kernel(Prob P, double *partial
         for (int k = threadIdx.x; k < m; k += kBlock) {
             const int64_t o = (int64_t)o0 + k;
             const int cam = P.pm_cam[o];
-            T Jc[18], Jp[6];
-            load_jac(J, npad, o, Jc, Jp);
-            const double *xc = P.x + (int64_t)cam * kVec;
-            T d0 = Jp[0] * sl[k] + Jp[1] * sl[cap + k] + Jp[2] * sl[2 * cap + k];
-            T d1 = Jp[3] * sl[k] + Jp[4] * sl[cap + k] + Jp[5] * sl[2 * cap + k];
+            T d0, d1;
+            if constexpr (FACT) {
+                float r[kRow], t[2], jh[6];
+                gather_row(nullptr, rowsx, cam, r);
+                fact_jc_v(__ldg(PX + o), __ldg(PX + npad + o), __ldg(PX + 2 * npad + o), r, t);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const T xa = (T)xc[a];
-                d0 += Jc[a] * xa;
-                d1 += Jc[9 + a] * xa;
+                for (int q = 0; q < 6; ++q) jh[q] = __ldg(Jh + q * npad + o);
+                const float sw = P.swpm ? __ldg(P.swpm + o) : 1.f, isw = 1.f / sw;
+                d0 = sw * t[0] + isw * (jh[0] * sl[k] + jh[1] * sl[cap + k] + jh[2] * sl[2 * cap + k]);
+                d1 = sw * t[1] + isw * (jh[3] * sl[k] + jh[4] * sl[cap + k] + jh[5] * sl[2 * cap + k]);
+            } else {
+                T Jc[18], Jp[6];
+                load_jac(J, npad, o, Jc, Jp);
+                const double *xc = P.x + (int64_t)cam * kVec;
+                d0 = Jp[0] * sl[k] + Jp[1] * sl[cap + k] + Jp[2] * sl[2 * cap + k];
+                d1 = Jp[3] * sl[k] + Jp[4] * sl[cap + k] + Jp[5] * sl[2 * cap + k];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const T xa = (T)xc[a];
+                    d0 += Jc[a] * xa;
+                    d1 += Jc[9 + a] * xa;
+                }
             }
             const double e0 = (double)res[o], e1 = (double)res[npad + o];
             const double dd0 = (double)d0, dd1 = (double)d1;
@@ -1354,6 +1383,21 @@ __global__ void __launch_bounds__(kBlock) backsub_kernel(Prob P, double *partial
     }
     const double s = block_sum(ldec, sb);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Camera rows (with the constants) of the PCG solution dc, for the factored
+// back-substitution; one thread per camera.
+__global__ void fact_rows_kernel(Prob P, const double *__restrict__ x, float *__restrict__ rows) {
+    if (P.st->done) return;
+    for (int cam = blockIdx.x * blockDim.x + threadIdx.x; cam < P.nc; cam += gridDim.x * blockDim.x) {
+        float v[9], r[kRow];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) v[j] = (float)x[(int64_t)cam * kVec + j];
+        fact_row((const float *)P.camtab + (int64_t)cam * kCamTab, v, true, r);
+        float4 *dst = (float4 *)(rows + (int64_t)cam * kRow);
+#pragma unroll
+        for (int i = 0; i < kRow / 4; ++i) dst[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+    }
 }
 
 __global__ void cams_new_kernel(Prob P) {
@@ -1448,16 +1492,24 @@ cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t 
     const size_t smem = (P.fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)P.cap;
     if (P.fp32) {
         if (!g_pcg_attr[0]) {
-            cudaFuncSetAttribute(backsub_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4 * 2048);
+            cudaFuncSetAttribute(backsub_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4 * 2048);
+            cudaFuncSetAttribute(backsub_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 3 * 4 * 2048);
             g_pcg_attr[0] = true;
         }
-        backsub_kernel<float><<<nb, kBlock, smem, s>>>(P, partial);
+        if (P.fact) {
+            fact_rows_kernel<<<(P.nc + 127) / 128, 128, 0, s>>>(P, P.x, (float *)P.pT);
+            backsub_kernel<float, true><<<nb, kBlock, smem, s>>>(P, partial);
+        } else {
+            backsub_kernel<float, false><<<nb, kBlock, smem, s>>>(P, partial);
+        }
     } else {
         if (!g_pcg_attr[1]) {
-            cudaFuncSetAttribute(backsub_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 8 * 2048);
+            cudaFuncSetAttribute(backsub_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 3 * 8 * 2048);
             g_pcg_attr[1] = true;
         }
-        backsub_kernel<double><<<nb, kBlock, smem, s>>>(P, partial);
+        backsub_kernel<double, false><<<nb, kBlock, smem, s>>>(P, partial);
     }
     ldec_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, P.st);
     cams_new_kernel<<<(P.nc * 9 + kBlock - 1) / kBlock, kBlock, 0, s>>>(P);

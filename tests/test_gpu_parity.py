@@ -139,6 +139,23 @@ def test_step_fp64(mba, kind):
     assert st["model_dec"] == pytest.approx(ref["model_dec"], rel=1e-6)
 
 
+@pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber")])
+def test_step_fp32_mixed(mba, kind, loss):
+    """One damped step in FP32-mixed (the factored Schur product and
+    back-substitution) against the FP64 oracle: camera and point steps and the
+    model decrease at 1e-4, with 10 fixed PCG iterations on both sides."""
+    sc = _scene(kind)
+    mu = 1e-2
+    with _problem(mba, sc, "fp32", loss=loss, delta=2.0) as pr:
+        st = pr.step(mu, pcg_max_iter=10, pcg_rel_tol=0.0)
+    ref = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, pcg_max=10, pcg_tol=0.0,
+                      loss=loss, delta=2.0)
+    assert st["pcg_iters"] == ref["pcg_iters"] == 10
+    rel_close(st["dc"], ref["dc"], 1e-4, "dc")
+    rel_close(st["dp"], ref["dp"], 1e-4, "dp")
+    assert st["model_dec"] == pytest.approx(ref["model_dec"], rel=1e-4)
+
+
 @pytest.mark.parametrize("kind,loss,iters,pcg", [("cfg1", "none", 10, 50), ("ragged", "none", 6, 40),
                                                  ("huber", "huber", 6, 40), ("longtrack", "none", 5, 30)])
 def test_solve_fp64_final_cost(mba, kind, loss, iters, pcg):
