@@ -250,6 +250,30 @@ mba_status mba_cost_noalloc(const double *d_cameras, int32_t nc, const double *d
                             int64_t n, int32_t loss, double huber_delta, double *d_cost, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Bundle-Adjustment-in-the-Large text files (the problem format of the paper's
+ * BAL experiments, Sec. 6): header "nc np n", then n lines "camera point x y",
+ * then nc x 9 camera values (angle-axis w, t, f, k1, k2) and np x 3 point
+ * values, all whitespace separated.  This is the library's own camera model,
+ * so a file's arrays go to mba_problem_create unchanged.  Host only: no GPU.
+ *
+ * mba_bal_read: parses `path` and returns the sizes; if every array pointer
+ * is non-NULL it also fills cameras (nc x 9), points (np x 3), observations
+ * (n x 2), cam_idx[n] and pt_idx[n], all owned by the caller (call once with
+ * NULL arrays to size them).  Errors: MBA_ERR_INVALID_ARG for an unreadable
+ * file, a malformed or truncated file, sizes out of the range
+ * mba_problem_create accepts, or an index out of range; MBA_ERR_NONFINITE for
+ * a NaN/Inf value.
+ * mba_bal_write: writes the same layout, every double with 17 significant
+ * digits, so that reading it back returns the same bits.  Errors:
+ * MBA_ERR_INVALID_ARG for NULL arguments, sizes < 1 or a failed write.
+ * ------------------------------------------------------------------------ */
+mba_status mba_bal_read(const char *path, int32_t *nc, int32_t *np, int64_t *n, double *cameras, double *points,
+                        double *observations, int32_t *cam_idx, int32_t *pt_idx);
+mba_status mba_bal_write(const char *path, int32_t nc, int32_t np, int64_t n, const double *cameras,
+                         const double *points, const double *observations, const int32_t *cam_idx,
+                         const int32_t *pt_idx);
+
+/* ------------------------------------------------------------------------
  * Batched local bundle adjustment: many small independent problems
  * ("windows", e.g. the sliding windows of a visual SLAM back end) solved in
  * ONE persistent kernel launch, captured once as a CUDA graph.  Each window

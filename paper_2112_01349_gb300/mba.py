@@ -125,6 +125,8 @@ def load():
             "mba_batch_set_parameters": (C.c_int, [P, P, P]),
             "mba_batch_reset": (C.c_int, [P]),
             "mba_batch_get_gradients": (C.c_int, [P, P, P, P]),
+            "mba_bal_read": (C.c_int, [C.c_char_p, P, P, P, P, P, P, P, P]),
+            "mba_bal_write": (C.c_int, [C.c_char_p, i32, i32, i64, P, P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
         }
@@ -530,6 +532,82 @@ def mba_batch_get_gradients(h):
     go, gc, gp = np.zeros((info["n"], 2)), np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
     _check(load().mba_batch_get_gradients(h, _vp(go), _vp(gc), _vp(gp)))
     return dict(grad_obs=go, grad_init_cam=gc, grad_init_pt=gp)
+
+
+def mba_bal_read(path):
+    """(cameras (nc, 9), points (np, 3), observations (n, 2), cam_idx (n,), pt_idx (n,)) of a BAL text file."""
+    lib = load()
+    bpath = os.fsencode(path)
+    nc, np_, n = C.c_int32(), C.c_int32(), C.c_int64()
+    _check(lib.mba_bal_read(bpath, C.byref(nc), C.byref(np_), C.byref(n), None, None, None, None, None))
+    cams, pts = np.zeros((nc.value, 9)), np.zeros((np_.value, 3))
+    obs = np.zeros((n.value, 2))
+    ci, pi = np.zeros(n.value, np.int32), np.zeros(n.value, np.int32)
+    _check(lib.mba_bal_read(bpath, C.byref(nc), C.byref(np_), C.byref(n), _vp(cams), _vp(pts), _vp(obs), _vp(ci),
+                            _vp(pi)))
+    return cams, pts, obs, ci, pi
+
+
+def mba_bal_write(path, cameras, points, observations, cam_idx, pt_idx):
+    """Write a BAL text file (every double to 17 significant digits: it reads back bit for bit)."""
+    cams = np.ascontiguousarray(cameras, dtype=np.float64).reshape(-1, 9)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    obs = np.ascontiguousarray(observations, dtype=np.float64).reshape(-1, 2)
+    ci, pi = np.ascontiguousarray(cam_idx, dtype=np.int32), np.ascontiguousarray(pt_idx, dtype=np.int32)
+    if len(ci) != len(obs) or len(pi) != len(obs):
+        raise ValueError("cam_idx and pt_idx must have one entry per observation")
+    _check(load().mba_bal_write(os.fsencode(path), len(cams), len(pts), len(obs), _vp(cams), _vp(pts), _vp(obs),
+                                _vp(ci), _vp(pi)))
+
+
+class Graph:
+    """Graph-style declaration of a BA problem, after the g2o / Ceres convention
+    the paper's API follows (Sec. 5.3): camera and point nodes, observation
+    edges (the BAL reprojection edge), then one solver call.  Node ids are the
+    return values of add_camera / add_point; the graph turns into the flat
+    arrays of mba_problem_create."""
+
+    def __init__(self):
+        self._cams, self._pts, self._obs, self._ci, self._pi = [], [], [], [], []
+
+    def add_camera(self, params) -> int:
+        """9 parameters: angle-axis w (3), t (3), f, k1, k2."""
+        p = np.asarray(params, dtype=np.float64).reshape(9)
+        self._cams.append(p)
+        return len(self._cams) - 1
+
+    def add_point(self, xyz) -> int:
+        self._pts.append(np.asarray(xyz, dtype=np.float64).reshape(3))
+        return len(self._pts) - 1
+
+    def add_edge(self, camera: int, point: int, uv) -> int:
+        """Observation uv of point `point` in camera `camera` (residual pi(c, X) - uv)."""
+        if not (0 <= camera < len(self._cams)) or not (0 <= point < len(self._pts)):
+            raise IndexError("add the camera and point nodes before the edge")
+        self._obs.append(np.asarray(uv, dtype=np.float64).reshape(2))
+        self._ci.append(camera)
+        self._pi.append(point)
+        return len(self._obs) - 1
+
+    def arrays(self):
+        """(cameras, points, observations, cam_idx, pt_idx) in node and edge order."""
+        return (np.array(self._cams).reshape(-1, 9), np.array(self._pts).reshape(-1, 3),
+                np.array(self._obs).reshape(-1, 2), np.array(self._ci, np.int32), np.array(self._pi, np.int32))
+
+    def problem(self, **opts) -> "Problem":
+        """A device problem (mba_problem_create) of this graph; opts as Problem's."""
+        return Problem(*self.arrays(), **opts)
+
+    @classmethod
+    def from_bal(cls, path) -> "Graph":
+        g = cls()
+        cams, pts, obs, ci, pi = mba_bal_read(path)
+        g._cams, g._pts, g._obs = list(cams), list(pts), list(obs)
+        g._ci, g._pi = [int(i) for i in ci], [int(i) for i in pi]
+        return g
+
+    def to_bal(self, path):
+        mba_bal_write(path, *self.arrays())
 
 
 def concat_windows(windows):
