@@ -41,79 +41,120 @@ __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc,
     }
 }
 
+// Per observation of a point-major warp chunk: residual and Jacobians, the
+// stored per-observation data, and the nine point-block terms q (packed
+// Jp~^T Jp~, then -Jp~^T e~).
 template <typename T, bool AD>
-__global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
+__device__ __forceinline__ void lin_point_obs(const Prob &P, int64_t o, int cam, int pt, T *q) {
     constexpr bool FACT = sizeof(T) == 4 && !AD;  // FP32-mixed analytic: no stored Jacobian
-    if (!force && (P.st->done || !P.st->relin)) return;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *slot = reinterpret_cast<T *>(smem_raw);  // [9][cap]
     const T *__restrict__ camtab = (const T *)P.camtab;
     T *__restrict__ J = (T *)P.J;
     T *__restrict__ res = (T *)P.res;
     const int64_t np_ = P.npad;
-    const int cap = P.cap;
-    const T delta = (T)P.delta;
-    for (int c = blockIdx.x; c < P.n_pchunks; c += gridDim.x) {
-        const int j0 = P.pchunk[c], j1 = P.pchunk[c + 1];
-        if (j0 == j1) continue;
-        const int o0 = P.pt_ptr[j0], m = P.pt_ptr[j1] - o0;
-        for (int k = threadIdx.x; k < m; k += kBlock) {
-            const int64_t o = (int64_t)o0 + k;
-            const int cam = P.pm_cam[o], pt = P.pm_pt[o];
-            const double2 uv = P.pm_uv[o];
-            T e[2], Jc[18], Jp[6], pz[3];
-            edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt],
-                             (T)P.pts[3 * (int64_t)pt + 1], (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc,
-                             Jp, FACT ? pz : nullptr);
-            T rho, W;
-            loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
-            const T sw = sqrt(W);
+    const double2 uv = __ldg(P.pm_uv + o);
+    T e[2], Jc[18], Jp[6], pz[3];
+    edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)__ldg(P.pts + 3 * (int64_t)pt),
+                     (T)__ldg(P.pts + 3 * (int64_t)pt + 1), (T)__ldg(P.pts + 3 * (int64_t)pt + 2), (T)uv.x, (T)uv.y, e,
+                     Jc, Jp, FACT ? pz : nullptr);
+    T rho, W;
+    loss_weight<T>(P.loss, (T)P.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
+    const T sw = sqrt(W);
 #pragma unroll
-            for (int q = 0; q < 18; ++q) Jc[q] *= sw;
+    for (int k = 0; k < 18; ++k) Jc[k] *= sw;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) Jp[q] *= sw;
-            if (FACT) {  // factored form: (px, py, 1/Pz), W Jp and, with a loss, sqrt(W)
+    for (int k = 0; k < 6; ++k) Jp[k] *= sw;
+    if (FACT) {  // factored form: (px, py, 1/Pz), W Jp and, with a loss, sqrt(W)
 #pragma unroll
-                for (int q = 0; q < 3; ++q) P.PXpm[q * np_ + o] = (float)pz[q];
+        for (int k = 0; k < 3; ++k) P.PXpm[k * np_ + o] = (float)pz[k];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) P.Jph[q * np_ + o] = (float)(sw * Jp[q]);
-                if (P.swpm) P.swpm[o] = (float)sw;
-            } else {
+        for (int k = 0; k < 6; ++k) P.Jph[k * np_ + o] = (float)(sw * Jp[k]);
+        if (P.swpm) P.swpm[o] = (float)sw;
+    } else {
 #pragma unroll
-                for (int q = 0; q < 18; ++q) J[q * np_ + o] = Jc[q];
+        for (int k = 0; k < 18; ++k) J[k * np_ + o] = Jc[k];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) J[(18 + q) * np_ + o] = Jp[q];
+        for (int k = 0; k < 6; ++k) J[(18 + k) * np_ + o] = Jp[k];
+    }
+    e[0] *= sw;
+    e[1] *= sw;
+    res[o] = e[0];
+    res[np_ + o] = e[1];
+    q[0] = Jp[0] * Jp[0] + Jp[3] * Jp[3];
+    q[1] = Jp[0] * Jp[1] + Jp[3] * Jp[4];
+    q[2] = Jp[0] * Jp[2] + Jp[3] * Jp[5];
+    q[3] = Jp[1] * Jp[1] + Jp[4] * Jp[4];
+    q[4] = Jp[1] * Jp[2] + Jp[4] * Jp[5];
+    q[5] = Jp[2] * Jp[2] + Jp[5] * Jp[5];
+    q[6] = -(Jp[0] * e[0] + Jp[3] * e[1]);
+    q[7] = -(Jp[1] * e[0] + Jp[4] * e[1]);
+    q[8] = -(Jp[2] * e[0] + Jp[5] * e[1]);
+}
+
+// Point-major linearisation over warp chunks (whole points, <= 32 observations,
+// one per lane; or one point with a longer track): every observation's data,
+// and per point C = sum Jp~^T Jp~ and w = -sum Jp~^T e~ by a segmented shuffle
+// scan in a fixed order, with no shared memory or CTA barrier.
+template <typename T, bool AD>
+__global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
+    if (!force && (P.st->done || !P.st->relin)) return;
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
+    for (int w = blockIdx.x * nwarp + (threadIdx.x >> 5); w < P.n_wchunks; w += gridDim.x * nwarp) {
+        const int2 c0 = P.wchunk[w], c1 = P.wchunk[w + 1];
+        const int o0 = c0.y, m = c1.y - c0.y;
+        T q[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) q[k] = T(0);
+        if (m <= 32) {
+            const bool act = lane < m;
+            const int64_t o = (int64_t)o0 + (act ? lane : 0);
+            const int npts = c1.x - c0.x;
+            const int rs = lane < npts ? __ldg(P.pt_ptr + c0.x + lane) - o0 : 32;
+            const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+            const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+            if (act) lin_point_obs<T, AD>(P, o, __ldg(P.pm_cam + o), pt, q);
+            // inclusive segmented scan keyed by point; the last lane of each point writes
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int kp = __shfl_up_sync(full, pt, d);
+                T v[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = __shfl_up_sync(full, q[k], d);
+                if (lane >= d && kp == pt) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) q[k] += v[k];
+                }
             }
-            e[0] *= sw;
-            e[1] *= sw;
-            res[o] = e[0];
-            res[np_ + o] = e[1];
-            // C terms (packed upper 3x3) and w terms
-            slot[0 * cap + k] = Jp[0] * Jp[0] + Jp[3] * Jp[3];
-            slot[1 * cap + k] = Jp[0] * Jp[1] + Jp[3] * Jp[4];
-            slot[2 * cap + k] = Jp[0] * Jp[2] + Jp[3] * Jp[5];
-            slot[3 * cap + k] = Jp[1] * Jp[1] + Jp[4] * Jp[4];
-            slot[4 * cap + k] = Jp[1] * Jp[2] + Jp[4] * Jp[5];
-            slot[5 * cap + k] = Jp[2] * Jp[2] + Jp[5] * Jp[5];
-            slot[6 * cap + k] = -(Jp[0] * e[0] + Jp[3] * e[1]);
-            slot[7 * cap + k] = -(Jp[1] * e[0] + Jp[4] * e[1]);
-            slot[8 * cap + k] = -(Jp[2] * e[0] + Jp[5] * e[1]);
+            const int nxt = __shfl_down_sync(full, pt, 1);
+            if (act && (lane == m - 1 || nxt != pt)) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) P.Hll[6 * (int64_t)pt + k] = (double)q[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) P.w[3 * (int64_t)pt + k] = (double)q[6 + k];
+            }
+        } else {
+            // one point with a long track: 32-observation slices, then a tree
+            const int pt = c0.x;
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    const int64_t o = (int64_t)o0 + base + lane;
+                    T qq[9];
+                    lin_point_obs<T, AD>(P, o, __ldg(P.pm_cam + o), pt, qq);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) q[k] += qq[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) q[k] += __shfl_xor_sync(full, q[k], d);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) P.Hll[6 * (int64_t)pt + k] = (double)q[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) P.w[3 * (int64_t)pt + k] = (double)q[6 + k];
+            }
         }
-        __syncthreads();
-        for (int j = j0 + threadIdx.x; j < j1; j += kBlock) {
-            const int b = P.pt_ptr[j] - o0, e_ = P.pt_ptr[j + 1] - o0;
-            T acc[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) acc[q] = T(0);
-            for (int s = b; s < e_; ++s)
-#pragma unroll
-                for (int q = 0; q < 9; ++q) acc[q] += slot[q * cap + s];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) P.Hll[6 * (int64_t)j + q] = (double)acc[q];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) P.w[3 * (int64_t)j + q] = (double)acc[6 + q];
-        }
-        __syncthreads();
     }
 }
 
@@ -286,15 +327,9 @@ cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaS
 
 template <typename T, bool AD>
 static void launch_lin_pair(const Prob &P, int force, cudaStream_t s) {
-    static bool attr_done = false;
-    const int nb = 152 * 4;
-    const size_t sm = sizeof(T) * 9 * (size_t)P.cap;
-    if (!attr_done) {
-        cudaFuncSetAttribute(lin_point_kernel<T, AD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(9 * sizeof(T) * 2048));
-        attr_done = true;
-    }
-    lin_point_kernel<T, AD><<<nb, kBlock, sm, s>>>(P, force);
+    int nbp = (P.n_wchunks + kWarps - 1) / kWarps;
+    if (nbp > 152 * 16) nbp = 152 * 16;
+    lin_point_kernel<T, AD><<<nbp < 1 ? 1 : nbp, kBlock, 0, s>>>(P, force);
     int nbc = (P.n_cchunks + kWarps - 1) / kWarps;
     if (nbc > 152 * 16) nbc = 152 * 16;
     lin_camera_kernel<T, AD><<<nbc < 1 ? 1 : nbc, kBlock, 0, s>>>(P, force);

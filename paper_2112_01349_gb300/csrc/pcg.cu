@@ -1274,112 +1274,149 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
 // candidate points, and the model decrease sum_k (-e~_k.d_k - |d_k|^2/2)
 // with d_k = Jc~_k dc + Jp~_k dp.
 // ---------------------------------------------------------------------------
-// FACT (FP32-mixed analytic): t = Jc dc from the camera rows of dc (formed by
-// fact_rows_kernel into the free search-direction buffer) and (px, py, 1/Pz),
-// Jp~^T Jc~ dc = (W Jp)^T t, and d~ = sqrt(W) t + (W Jp) dp / sqrt(W).
+// Per observation: t = Jc dc (sqrt(W)-scaled in the stored form, unscaled in
+// FACT) and the point-side Jacobian (Jp~, or W Jp in FACT), so that
+// u = jp^T t is this observation's term of Jp~^T Jc~ dc.
+template <typename T, bool FACT>
+__device__ __forceinline__ void backsub_obs(const Prob &P, int64_t o, int cam, T *t, T *jp) {
+    const int64_t npad = P.npad;
+    if constexpr (FACT) {
+        float r[kRow];
+        gather_row(nullptr, (const float *)P.pT, cam, r);
+        fact_jc_v(__ldcs(P.PXpm + o), __ldcs(P.PXpm + npad + o), __ldcs(P.PXpm + 2 * npad + o), r, t);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) jp[k] = __ldcs(P.Jph + k * npad + o);
+    } else {
+        T Jc[18];
+        load_jac_stream((const T *)P.J, npad, o, Jc, jp);
+        const double *xc = P.x + (int64_t)cam * kVec;
+        t[0] = t[1] = T(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const T xa = (T)xc[a];
+            t[0] += Jc[a] * xa;
+            t[1] += Jc[9 + a] * xa;
+        }
+    }
+}
+// Model-decrease term of one observation given its point step: d~ = J~_k (dc, dp),
+// -e~.d~ - |d~|^2 / 2 (FACT: d~ = sqrt(W) t + (W Jp) dp / sqrt(W)).
+template <typename T, bool FACT>
+__device__ __forceinline__ double backsub_dec(const Prob &P, int64_t o, const T *t, const T *jp, const T *dp) {
+    T d0 = jp[0] * dp[0] + jp[1] * dp[1] + jp[2] * dp[2];
+    T d1 = jp[3] * dp[0] + jp[4] * dp[1] + jp[5] * dp[2];
+    if constexpr (FACT) {
+        const float sw = P.swpm ? __ldg(P.swpm + o) : 1.f, isw = 1.f / sw;
+        d0 = sw * t[0] + isw * d0;
+        d1 = sw * t[1] + isw * d1;
+    } else {
+        d0 += t[0];
+        d1 += t[1];
+    }
+    const T *res = (const T *)P.res;
+    const double e0 = (double)__ldcs(res + o), e1 = (double)__ldcs(res + P.npad + o);
+    const double dd0 = (double)d0, dd1 = (double)d1;
+    return -(e0 * dd0 + e1 * dd1) - 0.5 * (dd0 * dd0 + dd1 * dd1);
+}
+// The point step dp_j = C~_j^-1 (w_j - a), its FP64 copy and the candidate point.
+template <typename T>
+__device__ __forceinline__ void backsub_point(const Prob &P, int pt, const T *a, T *dp) {
+    const T t0 = (T)P.w[3 * (int64_t)pt] - a[0], t1 = (T)P.w[3 * (int64_t)pt + 1] - a[1],
+            t2 = (T)P.w[3 * (int64_t)pt + 2] - a[2];
+    sym3_apply((const T *)P.Cinv + 6 * (int64_t)pt, t0, t1, t2, dp);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        P.dp[3 * (int64_t)pt + k] = (double)dp[k];
+        P.pts_new[3 * (int64_t)pt + k] = P.pts[3 * (int64_t)pt + k] + (double)dp[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// back-substitution dp_j = C~_j^-1 (w_j - sum_k Jp~_k^T Jc~_k dc_i(k)) (Eq. 4),
+// candidate points, and the model decrease sum_k (-e~_k.d_k - |d_k|^2/2)
+// with d_k = Jc~_k dc + Jp~_k dp, in one sweep over point-major warp chunks:
+// a segmented scan gives each point's sum, its last lane forms dp and the
+// point's lanes take it by a shuffle.  FACT (FP32-mixed analytic): t = Jc dc
+// from the camera rows of dc (fact_rows_kernel, into the free search-direction
+// buffer) and (px, py, 1/Pz).
+// ---------------------------------------------------------------------------
 template <typename T, bool FACT>
 __global__ void __launch_bounds__(kBlock) backsub_kernel(Prob P, double *partial) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sl = reinterpret_cast<T *>(smem_raw);
     __shared__ double sb[kWarps];
     if (P.st->done) return;
-    const T *__restrict__ J = (const T *)P.J;
-    const float *__restrict__ rowsx = (const float *)P.pT;
-    const float *__restrict__ PX = P.PXpm;
-    const float *__restrict__ Jh = P.Jph;
-    const T *__restrict__ res = (const T *)P.res;
-    const T *__restrict__ Cinv = (const T *)P.Cinv;
-    const int cap = P.cap;
-    const int64_t npad = P.npad;
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
     double ldec = 0.0;
-    for (int c = blockIdx.x; c < P.n_pchunks; c += gridDim.x) {
-        const int j0 = P.pchunk[c], j1 = P.pchunk[c + 1];
-        if (j0 == j1) continue;
-        const int o0 = P.pt_ptr[j0], m = P.pt_ptr[j1] - o0;
-        for (int k = threadIdx.x; k < m; k += kBlock) {
-            const int64_t o = (int64_t)o0 + k;
-            const int cam = P.pm_cam[o];
-            if constexpr (FACT) {
-                float r[kRow], t[2], jh[6];
-                gather_row(nullptr, rowsx, cam, r);
-                fact_jc_v(__ldg(PX + o), __ldg(PX + npad + o), __ldg(PX + 2 * npad + o), r, t);
+    for (int w = blockIdx.x * nwarp + (threadIdx.x >> 5); w < P.n_wchunks; w += gridDim.x * nwarp) {
+        const int2 c0 = P.wchunk[w], c1 = P.wchunk[w + 1];
+        const int o0 = c0.y, m = c1.y - c0.y;
+        if (m <= 32) {
+            const bool act = lane < m;
+            const int64_t o = (int64_t)o0 + (act ? lane : 0);
+            const int npts = c1.x - c0.x;
+            const int rs = lane < npts ? __ldg(P.pt_ptr + c0.x + lane) - o0 : 32;
+            const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+            const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+            T t[2] = {T(0), T(0)}, jp[6], u[3];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) jh[q] = __ldg(Jh + q * npad + o);
-                sl[0 * cap + k] = jh[0] * t[0] + jh[3] * t[1];
-                sl[1 * cap + k] = jh[1] * t[0] + jh[4] * t[1];
-                sl[2 * cap + k] = jh[2] * t[0] + jh[5] * t[1];
-            } else {
-                T Jc[18], Jp[6];
-                load_jac(J, npad, o, Jc, Jp);
-                const double *xc = P.x + (int64_t)cam * kVec;
-                T t0 = T(0), t1 = T(0);
+            for (int k = 0; k < 6; ++k) jp[k] = T(0);
+            if (act) backsub_obs<T, FACT>(P, o, __ldg(P.pm_cam + o), t, jp);
+            u[0] = jp[0] * t[0] + jp[3] * t[1];
+            u[1] = jp[1] * t[0] + jp[4] * t[1];
+            u[2] = jp[2] * t[0] + jp[5] * t[1];
 #pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    const T xa = (T)xc[a];
-                    t0 += Jc[a] * xa;
-                    t1 += Jc[9 + a] * xa;
-                }
-                sl[0 * cap + k] = Jp[0] * t0 + Jp[3] * t1;
-                sl[1 * cap + k] = Jp[1] * t0 + Jp[4] * t1;
-                sl[2 * cap + k] = Jp[2] * t0 + Jp[5] * t1;
-            }
-        }
-        __syncthreads();
-        for (int j = j0 + threadIdx.x; j < j1; j += kBlock) {
-            const int b = P.pt_ptr[j] - o0, e = P.pt_ptr[j + 1] - o0;
-            T a0 = T(0), a1 = T(0), a2 = T(0);
-            for (int s = b; s < e; ++s) {
-                a0 += sl[s];
-                a1 += sl[cap + s];
-                a2 += sl[2 * cap + s];
-            }
-            const T t0 = (T)P.w[3 * (int64_t)j] - a0, t1 = (T)P.w[3 * (int64_t)j + 1] - a1,
-                    t2 = (T)P.w[3 * (int64_t)j + 2] - a2;
-            T d[3];
-            sym3_apply(Cinv + 6 * (int64_t)j, t0, t1, t2, d);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                P.dp[3 * (int64_t)j + q] = (double)d[q];
-                P.pts_new[3 * (int64_t)j + q] = P.pts[3 * (int64_t)j + q] + (double)d[q];
-            }
-            for (int s = b; s < e; ++s) {
-                sl[s] = d[0];
-                sl[cap + s] = d[1];
-                sl[2 * cap + s] = d[2];
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < m; k += kBlock) {
-            const int64_t o = (int64_t)o0 + k;
-            const int cam = P.pm_cam[o];
-            T d0, d1;
-            if constexpr (FACT) {
-                float r[kRow], t[2], jh[6];
-                gather_row(nullptr, rowsx, cam, r);
-                fact_jc_v(__ldg(PX + o), __ldg(PX + npad + o), __ldg(PX + 2 * npad + o), r, t);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) jh[q] = __ldg(Jh + q * npad + o);
-                const float sw = P.swpm ? __ldg(P.swpm + o) : 1.f, isw = 1.f / sw;
-                d0 = sw * t[0] + isw * (jh[0] * sl[k] + jh[1] * sl[cap + k] + jh[2] * sl[2 * cap + k]);
-                d1 = sw * t[1] + isw * (jh[3] * sl[k] + jh[4] * sl[cap + k] + jh[5] * sl[2 * cap + k]);
-            } else {
-                T Jc[18], Jp[6];
-                load_jac(J, npad, o, Jc, Jp);
-                const double *xc = P.x + (int64_t)cam * kVec;
-                d0 = Jp[0] * sl[k] + Jp[1] * sl[cap + k] + Jp[2] * sl[2 * cap + k];
-                d1 = Jp[3] * sl[k] + Jp[4] * sl[cap + k] + Jp[5] * sl[2 * cap + k];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    const T xa = (T)xc[a];
-                    d0 += Jc[a] * xa;
-                    d1 += Jc[9 + a] * xa;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int kp = __shfl_up_sync(full, pt, d);
+                const T v0 = __shfl_up_sync(full, u[0], d), v1 = __shfl_up_sync(full, u[1], d),
+                        v2 = __shfl_up_sync(full, u[2], d);
+                if (lane >= d && kp == pt) {
+                    u[0] += v0;
+                    u[1] += v1;
+                    u[2] += v2;
                 }
             }
-            const double e0 = (double)res[o], e1 = (double)res[npad + o];
-            const double dd0 = (double)d0, dd1 = (double)d1;
-            ldec += -(e0 * dd0 + e1 * dd1) - 0.5 * (dd0 * dd0 + dd1 * dd1);
+            const int nxt = __shfl_down_sync(full, pt, 1);
+            const bool tail = act && (lane == m - 1 || nxt != pt);
+            T dp[3] = {T(0), T(0), T(0)};
+            if (tail) backsub_point<T>(P, pt, u, dp);
+            const unsigned tails = __ballot_sync(full, tail);
+            const unsigned mine = tails & (0xffffffffu << lane);
+            const int src = mine ? __ffs(mine) - 1 : lane;
+            T dq[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dq[k] = __shfl_sync(full, dp[k], src);
+            if (act) ldec += backsub_dec<T, FACT>(P, o, t, jp, dq);
+        } else {
+            // one point with a long track: the sum over 32-observation slices, then
+            // a second sweep for the model decrease
+            const int pt = c0.x;
+            T a[3] = {T(0), T(0), T(0)};
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    const int64_t o = (int64_t)o0 + base + lane;
+                    T t[2], jp[6];
+                    backsub_obs<T, FACT>(P, o, __ldg(P.pm_cam + o), t, jp);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) a[k] += jp[k] * t[0] + jp[3 + k] * t[1];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) a[k] += __shfl_xor_sync(full, a[k], d);
+            T dp[3] = {T(0), T(0), T(0)};
+            if (lane == 0) backsub_point<T>(P, pt, a, dp);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dp[k] = __shfl_sync(full, dp[k], 0);
+            for (int base = 0; base < m; base += 32) {
+                if (base + lane < m) {
+                    const int64_t o = (int64_t)o0 + base + lane;
+                    T t[2], jp[6];
+                    backsub_obs<T, FACT>(P, o, __ldg(P.pm_cam + o), t, jp);
+                    ldec += backsub_dec<T, FACT>(P, o, t, jp, dp);
+                }
+            }
         }
-        __syncthreads();
     }
     const double s = block_sum(ldec, sb);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -1418,7 +1455,6 @@ __global__ void ldec_final_kernel(const double *partial, int nb, DevState *st) {
     if (threadIdx.x == 0) st->model_dec = s;
 }
 
-bool g_pcg_attr[2] = {false, false};
 
 }  // namespace
 
@@ -1489,27 +1525,13 @@ cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long l
 }
 
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s) {
-    const size_t smem = (P.fp32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)P.cap;
-    if (P.fp32) {
-        if (!g_pcg_attr[0]) {
-            cudaFuncSetAttribute(backsub_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4 * 2048);
-            cudaFuncSetAttribute(backsub_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 3 * 4 * 2048);
-            g_pcg_attr[0] = true;
-        }
-        if (P.fact) {
-            fact_rows_kernel<<<(P.nc + 127) / 128, 128, 0, s>>>(P, P.x, (float *)P.pT);
-            backsub_kernel<float, true><<<nb, kBlock, smem, s>>>(P, partial);
-        } else {
-            backsub_kernel<float, false><<<nb, kBlock, smem, s>>>(P, partial);
-        }
+    if (P.fact) {
+        fact_rows_kernel<<<(P.nc + 127) / 128, 128, 0, s>>>(P, P.x, (float *)P.pT);
+        backsub_kernel<float, true><<<nb, kBlock, 0, s>>>(P, partial);
+    } else if (P.fp32) {
+        backsub_kernel<float, false><<<nb, kBlock, 0, s>>>(P, partial);
     } else {
-        if (!g_pcg_attr[1]) {
-            cudaFuncSetAttribute(backsub_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 3 * 8 * 2048);
-            g_pcg_attr[1] = true;
-        }
-        backsub_kernel<double, false><<<nb, kBlock, smem, s>>>(P, partial);
+        backsub_kernel<double, false><<<nb, kBlock, 0, s>>>(P, partial);
     }
     ldec_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, P.st);
     cams_new_kernel<<<(P.nc * 9 + kBlock - 1) / kBlock, kBlock, 0, s>>>(P);
