@@ -868,7 +868,8 @@ int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const dou
 /* on rejection radius /= factor and factor *= 2 (Nielsen's rule); radius is  */
 /* clamped to [1e-32, 1e16].  A rejected iteration counts and reuses the     */
 /* linearisation.  With function_tol > 0 the loop stops after an accepted     */
-/* step whose |F - F'|/F < function_tol.                                      */
+/* step whose |F - F'|/F < function_tol.  An iteration whose damped blocks */
+/* are not all positive definite has no step and counts as rejected.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double cost, cost_new, model_dec, mu, gain;
@@ -899,6 +900,19 @@ int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, c
         double rel_res = 0.0;
         rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, &pcg_iters, &rel_res, precond,
                          forcing ? &g0n : NULL);
+        if (rc == ORC_ERR_NOT_SPD) {
+            /* a damped block that is not positive definite gives no step: the
+               iteration counts as rejected (mu grows, the linearisation is kept) */
+            rc = ORC_OK;
+            if (trace) {
+                trace[it].cost = F; trace[it].cost_new = NAN; trace[it].model_dec = 0.0; trace[it].mu = mu;
+                trace[it].gain = NAN; trace[it].accepted = 0; trace[it].pcg_iters = 0; trace[it].pcg_rel_res = 0.0;
+            }
+            radius = radius / factor;
+            factor *= 2.0;
+            if (radius < 1e-32) radius = 1e-32;
+            continue;
+        }
         if (rc) goto done;
         double ldec = model_decrease(&L, dc, dp, scr);
         for (int64_t t = 0; t < 9 * (int64_t)nc; ++t) cand_c[t] = cams[t] + dc[t];

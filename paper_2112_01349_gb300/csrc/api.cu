@@ -222,6 +222,9 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.Jph = fact ? c.take<float>(6 * (size_t)P.npad) : nullptr;
         P.RXcm = fact ? c.take<float>(4 * (size_t)P.npad) : nullptr;
         P.swpm = (fact && o.loss != MBA_LOSS_NONE) ? c.take<float>((size_t)P.npad) : nullptr;
+        P.camff = fact ? c.take<float2>(16 * (size_t)nc) : nullptr;
+        P.uvff = fact ? c.take<float4>((size_t)n) : nullptr;
+        P.ptsff = fact ? c.take<float2>(3 * (size_t)np) : nullptr;
         // float copies of z and p (the factored form: their camera rows, kRow floats)
         P.zT = P.fp32 ? c.take<float>((size_t)nc * (fact ? kRow : kVec)) : nullptr;
         P.pT2 = c.take<char>((size_t)nc * (fact ? kRow * 4 : kVec * w));
@@ -292,6 +295,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     // point-major position -> camera-major position, via the inverse of the
     // camera-major permutation (set-up scratch): the point pass writes s there
     CKC(build_pm2cm(P, (int32_t *)tmp, s));
+    CKC(launch_split_observations(P, s));  // float-float pixels for the FP32-mixed solve's cost
     // keep the observations in input order too (for mba_evaluate)
     {
         // interleaved copy obs_d (n x 2) -> orig_uv (double2): same bytes
@@ -429,7 +433,8 @@ mba_status check_device_state(mba_problem *pr, DevState *hs) {
     CK(cudaMemcpyAsync(hs, pr->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, pr->stream));
     CK(cudaStreamSynchronize(pr->stream));
     if (hs->err == MBA_ERR_TIMEOUT) return fail(MBA_ERR_TIMEOUT, "a grid barrier of the persistent PCG kernel timed out");
-    if (hs->err == MBA_ERR_NONFINITE) return fail(MBA_ERR_NONFINITE, "a damped block is not positive definite");
+    if (hs->err == MBA_ERR_NONFINITE || hs->blockfail)
+        return fail(MBA_ERR_NONFINITE, "a damped block is not positive definite");
     if (hs->err != 0) return fail((mba_status)hs->err, "device error");
     return MBA_OK;
 }
@@ -638,7 +643,7 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
     CK(rec(0));
     CK(launch_state_init(P, o.initial_radius, -1.0, 0, s));
     CK(launch_camera_tables(P, P.cams, false, s));
-    CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s));
+    CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s, P.fact != 0));
     for (int it = 0; it < o.max_iter; ++it) {
         CK(rec(1 + 4 * it));
         CK(launch_camera_tables(P, P.cams, true, s));
@@ -650,15 +655,19 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         CK(rec(4 + 4 * it));
         CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
         CK(launch_camera_tables(P, P.cams_new, false, s));
-        CK(launch_cost_impl(P, P.pts_new, pr->part_b, &P.st->cost_new, nullptr, 1, s));
+        CK(launch_cost_impl(P, P.pts_new, pr->part_b, &P.st->cost_new, nullptr, 1, s, P.fact != 0));
         CK(launch_lm_update(P, o, s));
         CK(launch_accept(P, s));
     }
     CK(rec(ne > 0 ? ne - 1 : 0));
     // state_init, camera table, 2 cost kernels; per iteration: camera table, 3
     // linearisation, 2 damping, PCG, 3 back-substitution, camera table, 2 cost,
-    // LM update, accept
-    const int launches = 4 + (15 + (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI ? 2 : 0)) * o.max_iter;
+    // LM update, accept; the factored form adds the camera rows of dc and the
+    // float-float point copy before each cost, the Schur-Jacobi preconditioner
+    // two damping kernels
+    const int fact = P.fact ? 1 : 0;
+    const int launches =
+        4 + fact + (15 + 2 * fact + (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI ? 2 : 0)) * o.max_iter;
     DevState hs;
     mba_status st = check_device_state(pr, &hs);
     if (summary) {

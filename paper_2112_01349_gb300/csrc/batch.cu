@@ -163,7 +163,8 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
 struct WinState {
     double radius, factor, mu, F, F0, Fn, ldec, mu_acc;
     double g0;  // norm of the window's first reduced right-hand side (forcing sequence)
-    int32_t win, relin, done, iter, acc_total, pcg_total, status, accept, adj_iters, pad;
+    int32_t win, relin, done, iter, acc_total, pcg_total, status, accept, adj_iters;
+    int32_t blockfail;  // a damped block was not positive definite (this iteration)
 };
 
 __device__ __forceinline__ double damp_term_b(int damping, double d) {
@@ -948,7 +949,7 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
             }
         }
         if (!ok) {
-            S.status = MBA_ERR_NONFINITE;
+            S.blockfail = 1;
             continue;
         }
         for (int col = 0; col < 9; ++col) {
@@ -976,7 +977,7 @@ __device__ void damp(const BatchArgs &A, const WinMem<T> &M, WinState &S, const 
         const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
         const double det = a00 * c00 + a01 * c01 + a02 * c02;
         if (!(det > 0.0) || !isfinite(det)) {
-            S.status = MBA_ERR_NONFINITE;
+            S.blockfail = 1;
             continue;
         }
         const double id = 1.0 / det;
@@ -1329,6 +1330,7 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
         S.status = MBA_OK;
         S.accept = 0;
         S.adj_iters = 0;
+        S.blockfail = 0;
         S.g0 = 0.0;
     }
     __syncthreads();
@@ -1361,6 +1363,19 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
         const double mu = 1.0 / S.radius;
         damp<T, NT>(A, M, S, d, mu, O.damping);
         __syncthreads();
+        if (S.blockfail) {  // no step: the iteration counts as rejected (the rule of lm.cu)
+            __syncthreads();
+            if (tid == 0) {
+                S.radius = fmax(S.radius / S.factor, 1e-32);
+                S.factor *= 2.0;
+                S.mu = mu;
+                S.accept = 0;
+                S.iter = it + 1;
+                S.blockfail = 0;
+            }
+            __syncthreads();
+            continue;
+        }
         if (S.status != MBA_OK) break;
         if (O.explicit_schur) {
             s_build<T, NT>(A, M, d, mu, O.damping);
@@ -1426,6 +1441,8 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
             }
             const double mu = O.adj_mu >= 0.0 ? O.adj_mu : S.mu_acc;
             damp<T, NT>(A, M, S, d, mu, O.damping);
+            __syncthreads();
+            if (tid == 0 && S.blockfail) S.status = MBA_ERR_NONFINITE;
             __syncthreads();
             if (S.status == MBA_OK) {
                 if (O.explicit_schur) {

@@ -12,6 +12,7 @@
 //   v = -sum Jc~^T e~ per chunk; cam_finalize sums the chunks of each camera
 //   in order.
 // * cost kernels: F = 1/2 sum rho(|e|^2) in FP64 for accept/reject.
+#include "ff.cuh"
 #include "mba_internal.cuh"
 
 namespace mba {
@@ -26,7 +27,8 @@ inline unsigned grid_for(int64_t n, int per = kBlock) {
 
 template <typename T>
 __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc, T *__restrict__ tab,
-                                    double *__restrict__ tab64, const DevState *st, int gate) {
+                                    double *__restrict__ tab64, float2 *__restrict__ tabff, const DevState *st,
+                                    int gate) {
     if (gate == 1 && (st->done || !st->relin)) return;
     if (gate == 2 && st->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
@@ -38,7 +40,86 @@ __global__ void camera_table_kernel(const double *__restrict__ cams, int32_t nc,
         if (tab64)
 #pragma unroll
             for (int q = 0; q < kCamTab; ++q) tab64[(int64_t)i * kCamTab + q] = row[q];
+        if (tabff) {  // R, t, f, k1, k2 as float-float
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const ff v = ff_from(row[q]);
+                tabff[16 * (int64_t)i + q] = make_float2(v.hi, v.lo);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const ff v = ff_from(row[18 + q]);
+                tabff[16 * (int64_t)i + 9 + q] = make_float2(v.hi, v.lo);
+            }
+        }
     }
+}
+
+__global__ void split_points_kernel(const double *__restrict__ pts, int64_t m, float2 *__restrict__ out,
+                                    const DevState *st, int gate) {
+    if (gate && st->done) return;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const ff v = ff_from(pts[k]);
+        out[k] = make_float2(v.hi, v.lo);
+    }
+}
+
+__global__ void split_uv_kernel(const double2 *__restrict__ uv, int64_t n, float4 *__restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const ff u = ff_from(uv[k].x), v = ff_from(uv[k].y);
+        out[k] = make_float4(u.hi, u.lo, v.hi, v.lo);
+    }
+}
+
+// F = 1/2 sum rho(|e|^2) in float-float (ff.cuh): the BAL projection of each
+// observation from the float-float camera table, point and pixel, the loss in
+// FP64 where Huber's square root is needed, per-thread sums in float-float.
+__global__ void __launch_bounds__(kBlock) cost_partial_ff_kernel(Prob P, double *__restrict__ partial, int gate) {
+    __shared__ double sred[kWarps];
+    if (gate && P.st->done) return;
+    const double d2 = P.delta * P.delta;
+    ff acc = ff_from(0.f);
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < P.n; o += (int64_t)gridDim.x * blockDim.x) {
+        const int cam = P.pm_cam[o], pt = P.pm_pt[o];
+        const float2 *c = P.camff + 16 * (int64_t)cam;
+        const float2 *xp = P.ptsff + 3 * (int64_t)pt;
+        ff R[9], t[3], X[3];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float2 v = __ldg(c + q);
+            R[q] = {v.x, v.y};
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float2 v = __ldg(c + 9 + q), x = __ldg(xp + q);
+            t[q] = {v.x, v.y};
+            X[q] = {x.x, x.y};
+        }
+        ff Pc[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            Pc[r] = ff_add(ff_add(ff_mul(R[3 * r], X[0]), ff_mul(R[3 * r + 1], X[1])),
+                           ff_add(ff_mul(R[3 * r + 2], X[2]), t[r]));
+        const ff iz = ff_rcp(Pc[2]);
+        const ff px = ff_neg(ff_mul(Pc[0], iz)), py = ff_neg(ff_mul(Pc[1], iz));
+        const float2 fv = __ldg(c + 12), k1v = __ldg(c + 13), k2v = __ldg(c + 14);
+        const ff f = {fv.x, fv.y}, k1 = {k1v.x, k1v.y}, k2 = {k2v.x, k2v.y};
+        const ff r2 = ff_add(ff_mul(px, px), ff_mul(py, py));
+        const ff d = ff_add(ff_from(1.f), ff_mul(r2, ff_add(k1, ff_mul(k2, r2))));
+        const ff fd = ff_mul(f, d);
+        const float4 uv = __ldg(P.uvff + o);
+        const ff e0 = ff_sub(ff_mul(fd, px), ff{uv.x, uv.y});
+        const ff e1 = ff_sub(ff_mul(fd, py), ff{uv.z, uv.w});
+        const ff sq = ff_add(ff_mul(e0, e0), ff_mul(e1, e1));
+        if (P.loss == MBA_LOSS_HUBER && ff_to_double(sq) > d2) {
+            const double r = sqrt(ff_to_double(sq));
+            acc = ff_add(acc, ff_from(2.0 * P.delta * r - d2));
+        } else {
+            acc = ff_add(acc, sq);
+        }
+    }
+    const double s = block_sum(ff_to_double(acc), sred);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 // Per observation of a point-major warp chunk: residual and Jacobians, the
@@ -307,11 +388,11 @@ cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin
     const unsigned g = grid_for(P.nc, 128);
     if (for_lin) {
         if (P.fp32)
-            camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, nullptr, P.st, 1);
+            camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, nullptr, nullptr, P.st, 1);
         else
-            camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, nullptr, P.st, 1);
+            camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, nullptr, nullptr, P.st, 1);
     } else {
-        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, nullptr, P.camtab64, P.st, 2);
+        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, nullptr, P.camtab64, P.camff, P.st, 2);
     }
     return cudaGetLastError();
 }
@@ -319,9 +400,14 @@ cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin
 cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaStream_t s) {
     const unsigned g = grid_for(P.nc, 128);
     if (P.fp32)
-        camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, P.camtab64, P.st, 0);
+        camera_table_kernel<float><<<g, 128, 0, s>>>(cams, P.nc, (float *)P.camtab, P.camtab64, P.camff, P.st, 0);
     else
-        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, P.camtab64, P.st, 0);
+        camera_table_kernel<double><<<g, 128, 0, s>>>(cams, P.nc, (double *)P.camtab, P.camtab64, nullptr, P.st, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_observations(const Prob &P, cudaStream_t s) {
+    if (P.uvff) split_uv_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_uv, P.n, P.uvff);
     return cudaGetLastError();
 }
 
@@ -348,8 +434,14 @@ cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int forc
 }
 
 cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, double *out, double *out2, int gate,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool ff) {
     const int nb = cost_grid(P);
+    if (ff && P.camff && P.uvff && P.ptsff) {
+        split_points_kernel<<<grid_for(3 * (int64_t)P.np), kBlock, 0, s>>>(pts, 3 * (int64_t)P.np, P.ptsff, P.st, gate);
+        cost_partial_ff_kernel<<<nb, kBlock, 0, s>>>(P, partial, gate);
+        cost_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, out, out2, P.st, gate);
+        return cudaGetLastError();
+    }
     if (P.autodiff) cost_partial_kernel<true><<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
     else cost_partial_kernel<false><<<nb, kBlock, 0, s>>>(P, pts, partial, gate);
     cost_final_kernel<<<1, kBlock, 0, s>>>(partial, nb, out, out2, P.st, gate);

@@ -6,7 +6,8 @@
 // iff model_decrease > 0, F' is finite and gain > min_relative_decrease.
 // Accepted: radius /= max(1/3, 1 - (2 gain - 1)^3), decrease factor = 2.
 // Rejected: radius /= factor, factor *= 2.  radius stays in [1e-32, 1e16].
-// A rejected iteration counts and keeps the linearisation.
+// A rejected iteration counts and keeps the linearisation.  An iteration whose
+// damped blocks are not all positive definite (no step) is rejected.
 #include "mba_internal.cuh"
 
 namespace mba {
@@ -38,9 +39,19 @@ __global__ void lm_update_kernel(DevState *st, mba_iteration *trace, int trace_c
         st->accepted = 0;
         return;
     }
+    // a damped block that was not positive definite: no step this iteration,
+    // which counts as rejected (mu grows, the linearisation is kept)
+    const int blockfail = st->blockfail;
+    if (blockfail) {
+        st->cost_new = nan("");
+        st->model_dec = 0.0;
+        st->pcg_iters = 0;
+        st->pcg_rel_res = 0.0;
+        st->blockfail = 0;
+    }
     const double F = st->cost, Fn = st->cost_new, L = st->model_dec;
-    const double gain = (F - Fn) / L;
-    const int accept = (L > 0.0) && isfinite(Fn) && (gain > min_rel_dec);
+    const double gain = blockfail ? nan("") : (F - Fn) / L;
+    const int accept = !blockfail && (L > 0.0) && isfinite(Fn) && (gain > min_rel_dec);
     const int it = st->iter;
     if (trace && it < trace_cap) {
         mba_iteration t;

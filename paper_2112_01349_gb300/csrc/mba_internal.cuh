@@ -47,7 +47,7 @@ struct DevState {
     int32_t pcg_iters;
     int32_t accepted_total, pcg_total;
     uint32_t barrier;     // arrival counter of the persistent kernel's grid barrier
-    int32_t pad;
+    int32_t blockfail;    // 1: a damped block was not positive definite in this iteration
 };
 
 // Everything a kernel needs, as plain device pointers.  Sized at creation.
@@ -109,6 +109,10 @@ struct Prob {
     float *Jph;     // [6][npad] W Jp, point-major
     float *RXcm;    // [npad] float4 (R X, 1/Pz), camera-major
     float *swpm;    // [npad] sqrt(W), point-major (factored form with a robust loss; else null)
+    // float-float copies for the FP32-mixed solve's cost (ff.cuh; else null)
+    float2 *camff;  // [nc][16] R (9), t (3), f, k1, k2 of the cost's camera table
+    float4 *uvff;   // [n] observations, point-major (u hi, u lo, v hi, v lo)
+    float2 *ptsff;  // [np][3] the points being evaluated
     int32_t fact;   // 1: the PCG runs the factored form (FP32-mixed, analytic Jacobian)
     void *JcmT;     // [18][npad] sqrt(W)-scaled camera Jacobian in T, camera-major, that the PCG
                     // camera pass reads: Jcm in FP64; FP32-mixed with autodiff only (else null)
@@ -417,8 +421,10 @@ cudaError_t build_pm2cm(Prob &P, int32_t *tmp_n, cudaStream_t s);
 cudaError_t launch_camera_tables(const Prob &P, const double *cams, bool for_lin, cudaStream_t s);
 cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaStream_t s);
 cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s);
+// ff: evaluate in float-float arithmetic (FP32-mixed solves; ff.cuh)
 cudaError_t launch_cost_impl(const Prob &P, const double *pts, double *partial, double *out, double *out2, int gate,
-                             cudaStream_t s);
+                             cudaStream_t s, bool ff = false);
+cudaError_t launch_split_observations(const Prob &P, cudaStream_t s);
 int cost_grid(const Prob &P);
 cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_t *pi, const double2 *uv, int64_t m,
                                   double *e, double *jc, double *jp, cudaStream_t s);

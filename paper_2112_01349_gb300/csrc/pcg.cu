@@ -20,7 +20,9 @@ namespace {
 // ---------------------------------------------------------------------------
 // damping: B~ = B + mu D_B, C~ = C + mu D_C (D = clamp(diag, 1e-6, 1e32), or I)
 // B~ is stored full, with its inverse (Cholesky, FP64) as the block-Jacobi
-// preconditioner; C~^-1 (adjugate, FP64) is stored packed in T.
+// preconditioner; C~^-1 (adjugate, FP64) is stored packed in T.  A block that
+// is not positive definite sets DevState::blockfail: the LM loop rejects the
+// iteration (mu grows), single-step entry points report MBA_ERR_NONFINITE.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double damp_term(int damping, double d) {
     if (damping == MBA_DAMP_IDENTITY) return 1.0;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(32 * kDampWarps) damp_cameras_kernel(Prob P, i
         }
         __syncwarp();
         if (!warp_spd_inverse9(A, sY[wid], sil[wid], P.Binv + 81 * (int64_t)i) && lane == 0)
-            atomicCAS(&st->err, 0, (int)MBA_ERR_NONFINITE);
+            atomicExch(&st->blockfail, 1);
     }
 }
 
@@ -131,7 +133,7 @@ __global__ void damp_points_kernel(Prob P, int damping) {
         const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
         const double det = a00 * c00 + a01 * c01 + a02 * c02;
         if (!(det > 0.0) || !isfinite(det)) {
-            atomicCAS(&st->err, 0, (int)MBA_ERR_NONFINITE);
+            atomicExch(&st->blockfail, 1);
             continue;
         }
         const double id = 1.0 / det;
@@ -1087,7 +1089,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double sb[64];
     DevState *st = P.st;
-    if (st->done) return;
+    if (st->done || st->blockfail) return;  // a failed damping: the LM loop rejects this iteration
     // forcing sequence: the first solve's right-hand side norm as it was before
     // this launch, read before the first grid barrier (block 0 writes it after
     // the last one)

@@ -138,7 +138,8 @@ def test_venice_step_fp64_matches_oracle(mba, venice):
 
 def test_venice_fp32_mixed_equals_fp64_final_cost(mba, venice):
     """The bench's solve (20 LM iterations, PCG <= 100) in both forms: equal
-    final cost within 1e-4 relative, monotone accepted cost."""
+    final cost within 1e-4 relative, monotone accepted cost, and the same initial
+    cost to 1e-11 (float-float in FP32-mixed, FP64 in FP64)."""
     opts = dict(max_iter=20, pcg_max_iter=100, pcg_rel_tol=1e-10)
     out = {}
     for prec in ("fp64", "fp32"):
@@ -148,7 +149,10 @@ def test_venice_fp32_mixed_equals_fp64_final_cost(mba, venice):
         acc = [t["cost_new"] for t in s["trace"] if t["accepted"]]
         assert all(b < a for a, b in zip(acc, acc[1:]))
         out[prec] = s["final_cost"]
+        out[prec + "_initial"] = s["initial_cost"]
     assert abs(out["fp32"] - out["fp64"]) <= 1e-4 * out["fp64"]
+    # the FP32-mixed solve's float-float cost against the FP64 solve's cost
+    assert out["fp32_initial"] == pytest.approx(out["fp64_initial"], rel=1e-11)
 
 
 # ---------------------------------------------------------------- Final-shaped

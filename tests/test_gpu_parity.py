@@ -139,6 +139,22 @@ def test_step_fp64(mba, kind):
     assert st["model_dec"] == pytest.approx(ref["model_dec"], rel=1e-6)
 
 
+@pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber"), ("cfg1", "none")])
+def test_fp32_mixed_solve_cost_matches_fp64(mba, kind, loss):
+    """The FP32-mixed solve evaluates the cost for accept/reject in float-float
+    arithmetic: its initial and final costs equal the oracle's FP64 costs at the
+    same parameters to 1e-11 relative."""
+    sc = _scene(kind)
+    rc0 = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0,
+                          jacobians=False)[0]
+    with _problem(mba, sc, "fp32", loss=loss, delta=2.0) as pr:
+        s = pr.solve(max_iter=3, pcg_max_iter=20)
+        cams, pts = pr.parameters()
+    rc1 = oracle.evaluate(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0, jacobians=False)[0]
+    assert s["initial_cost"] == pytest.approx(rc0, rel=1e-11)
+    assert s["final_cost"] == pytest.approx(rc1, rel=1e-11)
+
+
 @pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber")])
 def test_step_fp32_mixed(mba, kind, loss):
     """One damped step in FP32-mixed (the factored Schur product and
