@@ -101,7 +101,7 @@ def batch_flops(ws, summaries, schur: str) -> float:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one PCG launch (30 iterations
 # plus the right-hand-side pass) on the full Venice-shaped problem, per observation
 # per pass (profiles/pcg_kernel_fp32_venice.md, profiles/pcg_kernel_fp64_venice.md)
-PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9384019200 + 100877568) / 31 / 5004484, 8: (63971187456 + 3471845376) / 31 / 5004484}
+PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9394786048 + 97457664) / 31 / 5004484, 8: (63629832448 + 3470636288) / 31 / 5004484}
 
 
 def pcg_flops_per_iter(sc) -> float:
