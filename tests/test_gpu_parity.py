@@ -252,3 +252,20 @@ def test_barrier_timeout_returns_status_and_context_survives(mba):
         pr.reset()
         s = pr.solve(max_iter=2, pcg_max_iter=10)
         assert s["status"] == 0 and s["iterations"] == 2
+
+
+def test_non_positive_definite_block_is_a_rejected_iteration(mba):
+    """The oracle pin's scene (a point seen by one camera, identity damping at
+    mu = 1e-16): the solve completes, and every iteration without a step (no PCG
+    iterations) is rejected with no candidate cost; the final cost is not above
+    the initial one."""
+    from tests.test_oracle_pins import _one_view_point_scene
+
+    cams, pts, obs, ci, pi = _one_view_point_scene()
+    with mba.Problem(cams, pts, obs, ci, pi) as pr:
+        s = pr.solve(trace_capacity=6, max_iter=6, pcg_max_iter=20, damping="identity", initial_radius=1e16)
+    assert s["status"] == 0 and s["iterations"] == 6
+    for t in s["trace"]:
+        if t["pcg_iters"] == 0:
+            assert not t["accepted"] and not np.isfinite(t["cost_new"])
+    assert s["final_cost"] <= s["initial_cost"]

@@ -355,3 +355,33 @@ def test_forcing_sequence_loosens_early_solves():
     costs = [t["cost_new"] for t in forced["trace"] if t["accepted"]]
     assert costs and all(b < a for a, b in zip(costs, costs[1:]))
     assert forced["final_cost"] < forced["trace"][0]["cost"]
+
+
+def _one_view_point_scene():
+    """A small scene plus one point seen by a single camera: its block J^T J has
+    rank 2, so with identity damping at mu = 1e-16 (radius 1e16) the damped 3x3
+    block is singular to FP64 rounding."""
+    sc = make_scene(3, 20, sigma=0.5, seed=0)
+    X = np.random.default_rng(0).normal(0, 0.3, 3)
+    pts = np.vstack([sc.points, X])
+    pix = oracle.residual_jacobian(sc.cameras[0], X, np.zeros(2))[0]
+    obs = np.vstack([sc.observations, pix + 0.3])
+    ci = np.concatenate([sc.cam_idx, [0]]).astype(np.int32)
+    pi = np.concatenate([sc.pt_idx, [len(pts) - 1]]).astype(np.int32)
+    return sc.cameras, pts, obs, ci, pi
+
+
+def test_non_positive_definite_block_is_a_rejected_iteration():
+    """No step exists when a damped block is not positive definite; the LM rule
+    then rejects the iteration: mu follows the rejection sequence 1e-16,
+    2e-16, 8e-16, 6.4e-15 (radius divided by 2, 4, 8), the trace records no
+    PCG iterations and no candidate cost, and the first solvable system gives
+    an accepted step that lowers the cost."""
+    cams, pts, obs, ci, pi = _one_view_point_scene()
+    r = oracle.lm_solve(cams, pts, obs, ci, pi, max_iter=4, pcg_max=20, damping="identity", initial_radius=1e16)
+    tr = r["trace"]
+    assert [t["accepted"] for t in tr] == [0, 0, 0, 1]
+    for t in tr[:3]:
+        assert math.isnan(t["cost_new"]) and t["pcg_iters"] == 0 and t["model_dec"] == 0.0
+    assert [t["mu"] for t in tr] == pytest.approx([1e-16, 2e-16, 8e-16, 6.4e-15], rel=1e-12)
+    assert tr[3]["cost_new"] < tr[3]["cost"]
