@@ -152,7 +152,6 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     P.autodiff = o.jacobian == MBA_JACOBIAN_AUTODIFF;
     P.fact = (P.fp32 && !P.autodiff) ? 1 : 0;  // FP32-mixed analytic: the factored Schur product
     const size_t w = P.fp32 ? 4 : 8;
-    const int64_t pbound = (n + 512) / 513 + 2;                 // point chunks (stride >= 513)
     const int64_t cbound = n / kCamChunk + (int64_t)nc + 2;     // camera chunks
     pr->pcg_grid = 0;
     int sms = 0;
@@ -184,7 +183,6 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.cm_orig = c.take<int32_t>(n);
         P.cm_uv = c.take<double2>(n);
         P.cam_ptr = c.take<int32_t>((size_t)nc + 1);
-        P.pchunk = c.take<int32_t>(pbound + 1);
         P.wchunk = c.take<int2>((size_t)np + 2);
         P.cchunk_cam = c.take<int32_t>(cbound);
         P.cchunk_beg = c.take<int32_t>(cbound + 1);
@@ -311,11 +309,6 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     if (max_track > kMaxTrack)
         return cleanup_fail(MBA_ERR_INVALID_ARG,
                             "a point has " + std::to_string(max_track) + " observations; at most 1024 are supported");
-    P.cap = max_track <= 512 ? 1024 : 2048;
-    const int stride = P.cap - max_track + 1;
-    P.n_pchunks = (int)((n + stride - 1) / stride);
-    if (P.n_pchunks > pbound) return cleanup_fail(MBA_ERR_INVALID_ARG, "internal: point chunk bound");
-    CKC(build_point_chunks(P, stride, s));
 
     // PCG camera partition: one group of whole cameras per CTA (one CTA per SM),
     // cut at the camera boundaries nearest to equal observation counts; then

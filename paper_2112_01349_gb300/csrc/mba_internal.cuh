@@ -57,8 +57,7 @@ struct Prob {
     int32_t fp32;          // 1: FP32-mixed
     int32_t loss;
     double delta;
-    int32_t cap;           // max observations in a point chunk (smem slots)
-    int32_t n_pchunks, n_cchunks;
+    int32_t n_cchunks;
     // warp chunks: wchunk[w] = (first point, first observation); runs of whole
     // points with <= 32 observations, or a single point with a longer track
     int32_t n_wchunks;
@@ -81,7 +80,6 @@ struct Prob {
     int32_t *cam_ptr;              // nc + 1
     int32_t *pm2cm;                // per point-major position: its camera-major position
     // chunk tables
-    int32_t *pchunk;               // n_pchunks + 1 point indices
     int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
     int32_t *cfirst;               // nc + 1: first camera chunk of each camera
     int32_t *cta_cam;              // grid + 1: cameras owned by each PCG CTA (balanced by observations)
@@ -414,7 +412,6 @@ cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, i
                             const int32_t *ci, const int32_t *pi, int64_t n, int32_t *flags, cudaStream_t s);
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
                           int32_t *tmp_i, cudaStream_t s);
-cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s);
 cudaError_t build_pm2cm(Prob &P, int32_t *tmp_n, cudaStream_t s);
 
 // linearize.cu

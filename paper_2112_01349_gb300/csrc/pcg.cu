@@ -244,13 +244,6 @@ __global__ void __launch_bounds__(32 * kDampWarps) sj_finalize_kernel(Prob P, co
 // ---------------------------------------------------------------------------
 // shared pieces of the point-major passes
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void load_jac(const T *__restrict__ J, int64_t npad, int64_t o, T *Jc, T *Jp) {
-#pragma unroll
-    for (int q = 0; q < 18; ++q) Jc[q] = __ldg(J + q * npad + o);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) Jp[q] = __ldg(J + (18 + q) * npad + o);
-}
 
 // Streaming variant: evict-first loads, so the once-per-pass Jacobian stream
 // does not push the per-observation s vectors and camera data out of L2.

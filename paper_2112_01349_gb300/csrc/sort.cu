@@ -1,7 +1,7 @@
 // sort.cu -- problem set-up on the device: input validation, the stable
 // orderings of the observations by point and by camera (the CSR layout of E
-// and E^T, Sec. 4.1), the permuted structure-of-arrays copies and the point
-// chunk table used by every point-major kernel.
+// and E^T, Sec. 4.1), the permuted structure-of-arrays copies and the map from
+// point-major to camera-major positions.
 #include "mba_internal.cuh"
 
 namespace mba {
@@ -302,23 +302,6 @@ __global__ void segment_stats_kernel(const int32_t *ptr, int32_t nseg, int32_t *
     atomicMax(flags + 1, mx);
 }
 
-__global__ void point_chunk_kernel(const int32_t *pt_ptr, int32_t np, int64_t n, int32_t stride, int32_t nch,
-                                   int32_t *pchunk) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= nch; c += (int64_t)gridDim.x * blockDim.x) {
-        if (c == nch) {
-            pchunk[c] = np;
-            continue;
-        }
-        const int64_t target = c * (int64_t)stride;
-        int32_t lo = 0, hi = np;  // first j in [0, np] with pt_ptr[j] >= target
-        while (lo < hi) {
-            const int32_t mid = lo + (hi - lo) / 2;
-            if ((int64_t)pt_ptr[mid] < target) lo = mid + 1;
-            else hi = mid;
-        }
-        pchunk[c] = lo;
-    }
-}
 }  // namespace
 
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,
@@ -349,10 +332,5 @@ cudaError_t build_pm2cm(Prob &P, int32_t *tmp_n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t build_point_chunks(Prob &P, int32_t stride, cudaStream_t s) {
-    point_chunk_kernel<<<grid_for((int64_t)P.n_pchunks + 1), kBlock, 0, s>>>(P.pt_ptr, P.np, P.n, stride,
-                                                                           P.n_pchunks, P.pchunk);
-    return cudaGetLastError();
-}
 
 }  // namespace mba
