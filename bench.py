@@ -182,6 +182,23 @@ def dist_setup(gpus: int):
     return rank, world, local, pg
 
 
+def max_over_ranks(ms: float, dist) -> float:
+    """The slowest rank's time: every rank returns the same value."""
+    if dist is None:
+        return ms
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def run_reference(args, rank, world):
     """CPU oracle on the host cores: each step is one LM iteration of the workload."""
     if rank != 0:
@@ -322,11 +339,8 @@ def main():
                 sums.append(pr.solve(**opts))
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
         if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         pr.close()
         return ms, sums, clk.summary()
@@ -335,8 +349,7 @@ def main():
     ms64, s64, clk64 = timed("fp64")
 
     def stats(ms, sums, w):
-        its = LM_ITERS * args.steps * world
-        value = its / (ms / 1e3)
+        value = whole_job_rate(LM_ITERS * args.steps, world, ms)
         pcg_ms = sum(s["ms_pcg"] for s in sums)
         pcg_iters = sum(s["pcg_iters_total"] for s in sums)
         launches = len(sums) * LM_ITERS  # one persistent PCG launch per LM iteration
@@ -372,13 +385,15 @@ def main():
 
     for _ in range(2):
         e2e_step()
+    if dist is not None:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = LM_ITERS * args.steps * world / e2e_s
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dist)
+    e2e_value = whole_job_rate(LM_ITERS * args.steps, world, e2e_ms)
 
     # solver variants beside Alg. 2 (not the headline): the same workload and
     # LM iteration count with the Schur-Jacobi preconditioner and/or the
