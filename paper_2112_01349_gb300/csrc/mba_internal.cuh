@@ -329,41 +329,6 @@ __device__ __forceinline__ double block_sum(double v, double *sbuf) {
     return s;
 }
 
-// ---------------------------------------------------------------------------
-// TMA bulk copies (global -> shared) completed on an mbarrier
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for an mbarrier phase; false after `limit` polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
-    for (long long i = 0; i <= limit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
 // Bounded grid barrier for cooperative (co-resident) launches.  Arrivals
 // increment a monotone counter (release); the k-th barrier completes when an
 // acquire load sees k * gridDim.x.  A CTA that polls more than `limit` times, or sees the error
