@@ -33,11 +33,14 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
+
+#include <sched.h>
 
 #include "mba_internal.cuh"
 
@@ -1674,12 +1677,45 @@ mba_status build_graph(mba_batch *b) {
     return MBA_OK;
 }
 
+// Threads the process may keep busy at once: the smaller of the cores it is
+// allowed to run on (affinity mask) and, where the container sets one, its
+// CFS CPU quota (cgroup v2 cpu.max, or v1 cpu.cfs_quota_us / cfs_period_us).
+// More busy threads than the quota allows get the whole process throttled
+// for the rest of each scheduling period.
+int host_threads() {
+    int n = (int)std::thread::hardware_concurrency();
+    if (n <= 0) n = 4;
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) {
+        const int c = CPU_COUNT(&set);
+        if (c > 0 && c < n) n = c;
+    }
+    long long quota = -1, period = 0;
+    if (FILE *f = std::fopen("/sys/fs/cgroup/cpu.max", "r")) {
+        char q[32] = {0};
+        if (std::fscanf(f, "%31s %lld", q, &period) == 2 && std::strcmp(q, "max") != 0) quota = std::atoll(q);
+        std::fclose(f);
+    } else {
+        FILE *fq = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_quota_us", "r");
+        FILE *fp = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_period_us", "r");
+        if (!fq || !fp || std::fscanf(fq, "%lld", &quota) != 1 || std::fscanf(fp, "%lld", &period) != 1) quota = -1;
+        if (fq) std::fclose(fq);
+        if (fp) std::fclose(fp);
+    }
+    if (quota > 0 && period > 0) {
+        const long long c = quota / period;  // whole cores within the quota
+        if (c < n) n = c > 1 ? (int)c : 1;
+    }
+    return n;
+}
+
 // Runs f(0..n-1) over the host's cores (dynamic claiming; each call of f
 // touches its own data).
 template <typename F>
 void parallel_for(int n, F &&f) {
-    unsigned hw = std::thread::hardware_concurrency();
-    int nt = (int)(hw ? hw : 4);
+    static const int hw = host_threads();
+    int nt = hw;
     if (nt > 32) nt = 32;
     if (nt > n) nt = n;
     if (nt <= 1) {
