@@ -534,8 +534,41 @@ def mba_batch_get_gradients(h):
     return dict(grad_obs=go, grad_init_cam=gc, grad_init_pt=gp)
 
 
+_COMPRESSED = {".bz2": "bz2", ".gz": "gzip", ".xz": "lzma"}
+
+
+def _codec(path):
+    """The standard-library module for a compressed BAL path (by suffix), or None."""
+    ext = os.path.splitext(os.fspath(path))[1].lower()
+    if ext not in _COMPRESSED:
+        return None
+    import importlib
+
+    return importlib.import_module(_COMPRESSED[ext])
+
+
 def mba_bal_read(path):
-    """(cameras (nc, 9), points (np, 3), observations (n, 2), cam_idx (n,), pt_idx (n,)) of a BAL text file."""
+    """(cameras (nc, 9), points (np, 3), observations (n, 2), cam_idx (n,), pt_idx (n,)) of a BAL text file.
+
+    Paths ending in .bz2, .gz or .xz (the BAL datasets are distributed
+    bz2-compressed) are decompressed to a temporary file first; the parsing is
+    always the C reader's."""
+    codec = _codec(path)
+    if codec is None:
+        return _bal_read_text(path)
+    import shutil
+    import tempfile
+
+    fd, tmp = tempfile.mkstemp(suffix=".txt")
+    try:
+        with os.fdopen(fd, "wb") as out, codec.open(os.fspath(path), "rb") as src:
+            shutil.copyfileobj(src, out, 1 << 20)
+        return _bal_read_text(tmp)
+    finally:
+        os.unlink(tmp)
+
+
+def _bal_read_text(path):
     lib = load()
     bpath = os.fsencode(path)
     nc, np_, n = C.c_int32(), C.c_int32(), C.c_int64()
@@ -549,7 +582,23 @@ def mba_bal_read(path):
 
 
 def mba_bal_write(path, cameras, points, observations, cam_idx, pt_idx):
-    """Write a BAL text file (every double to 17 significant digits: it reads back bit for bit)."""
+    """Write a BAL text file (every double to 17 significant digits: it reads back bit for bit).
+
+    Paths ending in .bz2, .gz or .xz are written through that compressor."""
+    codec = _codec(path)
+    if codec is not None:
+        import shutil
+        import tempfile
+
+        fd, tmp = tempfile.mkstemp(suffix=".txt")
+        os.close(fd)
+        try:
+            mba_bal_write(tmp, cameras, points, observations, cam_idx, pt_idx)
+            with open(tmp, "rb") as src, codec.open(os.fspath(path), "wb") as out:
+                shutil.copyfileobj(src, out, 1 << 20)
+        finally:
+            os.unlink(tmp)
+        return
     cams = np.ascontiguousarray(cameras, dtype=np.float64).reshape(-1, 9)
     pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
     obs = np.ascontiguousarray(observations, dtype=np.float64).reshape(-1, 2)

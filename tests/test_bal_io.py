@@ -86,6 +86,28 @@ def test_malformed_files_are_rejected(mba, tmp_path, text, status):
         mba.mba_bal_read(path)
 
 
+@pytest.mark.parametrize("suffix", [".bz2", ".gz", ".xz"])
+def test_compressed_files_round_trip(mba, tmp_path, suffix):
+    """The BAL datasets ship bz2-compressed: a compressed path is written
+    through, and read back from, the standard-library codec of its suffix."""
+    import bz2
+    import gzip
+    import lzma
+
+    codec = {".bz2": bz2, ".gz": gzip, ".xz": lzma}[suffix]
+    sc = make_scene(4, 120, sigma=0.5, seed=6)
+    path = tmp_path / ("scene.txt" + suffix)
+    mba.mba_bal_write(path, *_arrays(sc))
+    with codec.open(path, "rt") as f:  # really compressed, and the header is the BAL one
+        assert f.readline().split() == [str(sc.nc), str(sc.np_), str(sc.n)]
+    got = mba.mba_bal_read(path)
+    for a, b in zip(got, _arrays(sc)):
+        np.testing.assert_array_equal(a, np.asarray(b).reshape(a.shape))
+    plain = tmp_path / "plain.txt"
+    mba.mba_bal_write(plain, *_arrays(sc))
+    assert codec.decompress(path.read_bytes()) == plain.read_bytes()
+
+
 def test_missing_file_is_rejected(mba, tmp_path):
     with pytest.raises(mba.MbaError, match="INVALID_ARG"):
         mba.mba_bal_read(tmp_path / "absent.txt")
