@@ -385,3 +385,25 @@ def test_non_positive_definite_block_is_a_rejected_iteration():
         assert math.isnan(t["cost_new"]) and t["pcg_iters"] == 0 and t["model_dec"] == 0.0
     assert [t["mu"] for t in tr] == pytest.approx([1e-16, 2e-16, 8e-16, 6.4e-15], rel=1e-12)
     assert tr[3]["cost_new"] < tr[3]["cost"]
+
+
+def test_resume_from_a_checkpoint_continues_the_trajectory():
+    """Checkpoint / resume: an LM solve that stops after an accepted step and is
+    restarted from its parameters with its final trust-region radius (the
+    decrease factor is 2 after any accepted step, as at a start) continues the
+    uninterrupted solve bit for bit (Alg. 1 with the radius rule of the Ceres
+    trust region).  Tiny workload, split after the third iteration."""
+    from scenes import config_scene
+
+    sc = config_scene(1)
+    arrays = (sc.observations, sc.cam_idx, sc.pt_idx)
+    kw = dict(pcg_max=50, pcg_tol=1e-10)
+    full = oracle.lm_solve(sc.cameras, sc.points, *arrays, max_iter=10, **kw)
+    first = oracle.lm_solve(sc.cameras, sc.points, *arrays, max_iter=3, **kw)
+    assert first["trace"][-1]["accepted"] == 1
+    rest = oracle.lm_solve(first["cameras"], first["points"], *arrays, max_iter=7, initial_radius=first["radius"], **kw)
+    assert rest["final_cost"] == full["final_cost"]
+    assert [t["cost_new"] for t in rest["trace"]] == [t["cost_new"] for t in full["trace"][3:]]
+    assert [t["accepted"] for t in rest["trace"]] == [t["accepted"] for t in full["trace"][3:]]
+    np.testing.assert_array_equal(rest["cameras"], full["cameras"])
+    np.testing.assert_array_equal(rest["points"], full["points"])
