@@ -63,11 +63,11 @@ def _load():
             lib.orc_stable_sort.argtypes = [i64, P, i32, P, P]
             lib.orc_blocks.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, P, P, P, P, P]
             lib.orc_step.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, C.c_int,
-                                     C.c_int, dbl, P, P, P, P, P, C.c_int]
+                                     C.c_int, dbl, P, P, P, P, P, C.c_int, P, P]
             lib.orc_schur_jacobi_blocks.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, P]
             lib.orc_schur.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, P, P, P, P]
             lib.orc_lm_solve.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, C.c_int, C.c_int, dbl,
-                                         C.c_int, dbl, dbl, dbl, C.c_int, P, P, P, P, C.c_int, C.c_int]
+                                         C.c_int, dbl, dbl, dbl, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P]
             lib.orc_adjoint.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, C.c_int, dbl, P, P,
                                         P, P, P, P, C.c_int]
             lib.orc_num_threads.restype = C.c_int
@@ -159,15 +159,27 @@ def blocks(cams, pts, obs, cam_idx, pt_idx, loss="none", delta=0.0, with_E=False
     return (Hpp, v, Hll, w, E) if with_E else (Hpp, v, Hll, w)
 
 
+def _fixed(mask, m):
+    """A uint8 mask of m nodes held constant, or None."""
+    if mask is None:
+        return None
+    a = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    if a.shape[0] != m:
+        raise ValueError("fixed-node mask has the wrong length")
+    return a
+
+
 def step(cams, pts, obs, cam_idx, pt_idx, mu, loss="none", delta=0.0, damping="diag", schur="implicit_pcg",
-         pcg_max=100, pcg_tol=1e-10, precond="block_jacobi"):
-    """One damped Schur step: dict(dc (nc,9), dp (np,3), pcg_iters, rel_res, model_dec)."""
+         pcg_max=100, pcg_tol=1e-10, precond="block_jacobi", cam_fixed=None, pt_fixed=None):
+    """One damped Schur step: dict(dc (nc,9), dp (np,3), pcg_iters, rel_res, model_dec).
+    cam_fixed / pt_fixed: optional masks of nodes held constant."""
     cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
+    cf, pf = _fixed(cam_fixed, nc), _fixed(pt_fixed, np_)
     dc, dp = np.zeros((nc, 9)), np.zeros((np_, 3))
     it, rr, md = C.c_int(), C.c_double(), C.c_double()
     rc = _load().orc_step(nc, np_, n, _p(cams), _p(pts), _p(obs), _p(ci), _p(pi), LOSS[loss], float(delta),
                           float(mu), DAMPING[damping], SCHUR[schur], int(pcg_max), float(pcg_tol), _p(dc), _p(dp),
-                          C.byref(it), C.byref(rr), C.byref(md), PRECOND[precond])
+                          C.byref(it), C.byref(rr), C.byref(md), PRECOND[precond], _p(cf), _p(pf))
     if rc:
         raise RuntimeError(f"orc_step failed: {rc}")
     return dict(dc=dc, dp=dp, pcg_iters=it.value, rel_res=rr.value, model_dec=md.value)
@@ -200,16 +212,19 @@ def schur(cams, pts, obs, cam_idx, pt_idx, mu, x=None, loss="none", delta=0.0, d
 
 def lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=10, pcg_max=50, pcg_tol=1e-10, loss="none", delta=0.0,
              damping="diag", initial_radius=1e4, min_rel_dec=1e-3, function_tol=0.0, schur="implicit_pcg",
-             precond="block_jacobi", forcing=False):
-    """Run the LM loop; returns dict(cameras, points, trace (list of dict), iterations, final_cost, radius)."""
+             precond="block_jacobi", forcing=False, cam_fixed=None, pt_fixed=None):
+    """Run the LM loop; returns dict(cameras, points, trace (list of dict), iterations, final_cost, radius).
+    cam_fixed / pt_fixed: optional masks of nodes held constant."""
     cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
+    cf, pf = _fixed(cam_fixed, nc), _fixed(pt_fixed, np_)
     cams, pts = cams.copy(), pts.copy()
     tr = (Trace * max(1, max_iter))()
     it, fc, rad = C.c_int(), C.c_double(), C.c_double()
     rc = _load().orc_lm_solve(nc, np_, n, _p(cams), _p(pts), _p(obs), _p(ci), _p(pi), LOSS[loss], float(delta),
                               int(max_iter), int(pcg_max), float(pcg_tol), DAMPING[damping], float(initial_radius),
                               float(min_rel_dec), float(function_tol), SCHUR[schur], C.cast(tr, C.c_void_p),
-                              C.byref(it), C.byref(fc), C.byref(rad), PRECOND[precond], 1 if forcing else 0)
+                              C.byref(it), C.byref(fc), C.byref(rad), PRECOND[precond], 1 if forcing else 0,
+                              _p(cf), _p(pf))
     if rc:
         raise RuntimeError(f"orc_lm_solve failed: {rc}")
     trace = [{f: getattr(tr[i], f) for f, _ in Trace._fields_} for i in range(it.value)]

@@ -287,6 +287,8 @@ typedef struct {
     double *E;                   /* n*27: E_k = W_k Jc_k^T Jp_k (9x3), the non-zero block of E */
     double *Hpp, *v;             /* nc*81, nc*9 : B block and camera gradient */
     double *Hll, *w;             /* np*9,  np*3 : C block and point gradient */
+    const uint8_t *cam_fixed;    /* nc or NULL: nonzero = camera held constant */
+    const uint8_t *pt_fixed;     /* np or NULL: nonzero = point held constant */
 } lin_t;
 
 static void lin_free(lin_t *L) {
@@ -317,13 +319,20 @@ static int lin_alloc(lin_t *L, int32_t nc, int32_t np, int64_t n, const int32_t 
 }
 
 /* r_k, J_k at the current state; then [B E; E^T C] = J^T W J and [v w] = -J^T W r
- * as sums of per-edge terms (Alg. 1).  W_k is the IRLS weight rho'(s_k). */
+ * as sums of per-edge terms (Alg. 1).  W_k is the IRLS weight rho'(s_k).
+ * Fixed nodes (nodes held constant, the g2o / Ceres convention the paper's
+ * graph API follows, Sec. 5.3): the Jacobian columns of a fixed camera or
+ * point are zero.  Their rows of B, C, E and the gradient vanish, the damping
+ * floor keeps their damped blocks positive definite, and the damped step is
+ * that of the problem over the free parameters alone, zero on the fixed ones. */
 static void linearise(lin_t *L, const double *cams, const double *pts, const double *obs, int loss, double delta) {
     const int64_t n = L->n;
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; ++k) {
         double *e = L->e + 2 * k, *Jc = L->Jc + 18 * k, *Jp = L->Jp + 6 * k, *E = L->E + 27 * k;
         orc_residual_jacobian(cams + 9 * (int64_t)L->cam_idx[k], pts + 3 * (int64_t)L->pt_idx[k], obs + 2 * k, e, Jc, Jp);
+        if (L->cam_fixed && L->cam_fixed[L->cam_idx[k]]) memset(Jc, 0, sizeof(double) * 18);
+        if (L->pt_fixed && L->pt_fixed[L->pt_idx[k]]) memset(Jp, 0, sizeof(double) * 6);
         double rho, wt;
         loss_eval(loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &wt);
         L->W[k] = wt;
@@ -755,10 +764,12 @@ static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, i
 int orc_step(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
              const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
              int schur_mode, int pcg_max, double pcg_tol, double *dc, double *dp, int *pcg_iters, double *rel_res,
-             double *model_dec, int precond) {
+             double *model_dec, int precond, const uint8_t *cam_fixed, const uint8_t *pt_fixed) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
+    L.cam_fixed = cam_fixed;
+    L.pt_fixed = pt_fixed;
     linearise(&L, cams, pts, obs, loss, delta);
     rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, pcg_iters, rel_res, precond, NULL);
     if (!rc && model_dec) {
@@ -881,10 +892,12 @@ int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, c
                  const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, int max_iter, int pcg_max,
                  double pcg_tol, int damping, double initial_radius, double min_rel_dec, double function_tol,
                  int schur_mode, orc_trace_t *trace, int *iterations, double *final_cost, double *final_radius,
-                 int precond, int forcing) {
+                 int precond, int forcing, const uint8_t *cam_fixed, const uint8_t *pt_fixed) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
+    L.cam_fixed = cam_fixed;
+    L.pt_fixed = pt_fixed;
     double *cand_c = malloc(sizeof(double) * 9 * (size_t)nc), *cand_p = malloc(sizeof(double) * 3 * (size_t)np);
     double *dc = malloc(sizeof(double) * 9 * (size_t)nc), *dp = malloc(sizeof(double) * 3 * (size_t)np);
     double *scr = malloc(sizeof(double) * (size_t)n);

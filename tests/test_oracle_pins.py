@@ -407,3 +407,59 @@ def test_resume_from_a_checkpoint_continues_the_trajectory():
     assert [t["accepted"] for t in rest["trace"]] == [t["accepted"] for t in full["trace"][3:]]
     np.testing.assert_array_equal(rest["cameras"], full["cameras"])
     np.testing.assert_array_equal(rest["points"], full["points"])
+
+
+def _fixed_masks(sc):
+    cf = np.zeros(sc.nc, np.uint8)
+    cf[[0, 3]] = 1
+    pf = np.zeros(sc.np_, np.uint8)
+    pf[::7] = 1
+    return cf, pf
+
+
+@pytest.mark.parametrize("damping", ["diag", "identity"])
+def test_fixed_nodes_step_equals_the_reduced_dense_solve(damping):
+    """Nodes held constant (the g2o / Ceres convention of Sec. 5.3): the damped
+    step equals a dense solve of the damped normal equations with the fixed
+    parameters' rows and columns deleted, and is exactly zero on them."""
+    sc = make_scene(5, 40, sigma=1.0, seed=31)
+    cf, pf = _fixed_masks(sc)
+    mu = 1e-3
+    Hd, g, *_ = _damped_dense(sc, mu, damping)
+    nc = sc.nc
+    free = np.concatenate([np.repeat(cf == 0, 9), np.repeat(pf == 0, 3)])
+    dx = np.zeros(Hd.shape[0])
+    dx[free] = np.linalg.solve(Hd[np.ix_(free, free)], g[free])
+    for mode, tol in [("dense", 1e-9), ("explicit_pcg", 1e-7), ("implicit_pcg", 1e-7)]:
+        r = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, damping=damping,
+                        schur=mode, pcg_max=500, pcg_tol=1e-15, cam_fixed=cf, pt_fixed=pf)
+        assert np.all(r["dc"][cf == 1] == 0.0) and np.all(r["dp"][pf == 1] == 0.0), mode
+        got = np.concatenate([r["dc"].reshape(-1), r["dp"].reshape(-1)])
+        np.testing.assert_allclose(got, dx, atol=tol * np.abs(dx).max(), err_msg=mode)
+    # and it is not the unconstrained step
+    r0 = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, damping=damping,
+                     schur="dense")
+    assert np.abs(np.concatenate([r0["dc"].reshape(-1), r0["dp"].reshape(-1)]) - dx).max() > 1e-3 * np.abs(dx).max()
+    assert r0["dc"].shape == (nc, 9)
+
+
+def test_fixed_nodes_stay_constant_through_a_solve():
+    sc = make_scene(6, 300, sigma=0.5, seed=32)
+    cf, pf = _fixed_masks(sc)
+    r = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=8, pcg_max=50,
+                        cam_fixed=cf, pt_fixed=pf)
+    np.testing.assert_array_equal(r["cameras"][cf == 1], sc.cameras[cf == 1])
+    np.testing.assert_array_equal(r["points"][pf == 1], sc.points[pf == 1])
+    assert np.any(r["cameras"][cf == 0] != sc.cameras[cf == 0])
+    acc = [t["cost_new"] for t in r["trace"] if t["accepted"]]
+    assert acc and r["final_cost"] < r["trace"][0]["cost"]
+    assert all(b <= a for a, b in zip(acc, acc[1:]))
+
+
+def test_all_nodes_fixed_gives_no_step():
+    sc = make_scene(3, 30, sigma=0.5, seed=33)
+    r = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=3, pcg_max=20,
+                        cam_fixed=np.ones(sc.nc), pt_fixed=np.ones(sc.np_))
+    assert all(t["model_dec"] == 0.0 and t["accepted"] == 0 for t in r["trace"])
+    np.testing.assert_array_equal(r["cameras"], sc.cameras)
+    np.testing.assert_array_equal(r["points"], sc.points)
