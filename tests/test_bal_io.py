@@ -1,6 +1,7 @@
-"""Bundle-Adjustment-in-the-Large text files (mba_bal_read / mba_bal_write) and
-the graph-style problem declaration (mba.Graph).  Host only, except the last
-test, which solves a graph-declared problem on the GPU."""
+"""Bundle-Adjustment-in-the-Large text files (mba_bal_read / mba_bal_write), the
+graph-style problem declaration (mba.Graph) and the batched windows' array
+assembly (mba.concat_windows).  Host only, except
+test_graph_problem_solves_like_the_arrays, which solves on the GPU."""
 import numpy as np
 import pytest
 
@@ -145,3 +146,20 @@ def test_graph_problem_solves_like_the_arrays(mba, tmp_path):
     assert s1["final_cost"] == s2["final_cost"]
     np.testing.assert_array_equal(c1, c2)
     np.testing.assert_array_equal(p1, p2)
+
+
+def test_concat_windows_keeps_window_local_indices(mba):
+    """Batched windows are passed as concatenated arrays plus per-window
+    offsets; indices stay local to their window (host logic, no GPU)."""
+    ws = [make_scene(nc, npt, sigma=0.5, seed=40 + nc) for nc, npt in ((5, 30), (7, 44), (6, 25))]
+    co, po, oo, cams, pts, obs, ci, pi = mba.concat_windows(
+        [(s.cameras, s.points, s.observations, s.cam_idx, s.pt_idx) for s in ws])
+    assert co.tolist() == [0, 5, 12, 18] and po.tolist() == [0, 30, 74, 99]
+    assert oo.tolist() == np.cumsum([0] + [s.n for s in ws]).tolist()
+    assert co.dtype == po.dtype == oo.dtype == np.int64 and ci.dtype == pi.dtype == np.int32
+    for w, s in enumerate(ws):
+        np.testing.assert_array_equal(cams[co[w]:co[w + 1]], s.cameras)
+        np.testing.assert_array_equal(pts[po[w]:po[w + 1]], s.points)
+        np.testing.assert_array_equal(obs[oo[w]:oo[w + 1]], s.observations)
+        np.testing.assert_array_equal(ci[oo[w]:oo[w + 1]], s.cam_idx)
+        np.testing.assert_array_equal(pi[oo[w]:oo[w + 1]], s.pt_idx)
