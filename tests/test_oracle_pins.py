@@ -463,3 +463,94 @@ def test_all_nodes_fixed_gives_no_step():
     assert all(t["model_dec"] == 0.0 and t["accepted"] == 0 for t in r["trace"])
     np.testing.assert_array_equal(r["cameras"], sc.cameras)
     np.testing.assert_array_equal(r["points"], sc.points)
+
+
+# ---------------------------------------------------------------------------
+# Truncated PCG iterates (Alg. 2 with a capped iteration count).  A converged
+# PCG only shows that the loop reaches the solution; a capped one returns its
+# k-th iterate, which every capped solve depends on.  The k-th iterate of
+# preconditioned CG from x0 = 0 is, by the optimality property of CG (Saad,
+# Iterative Methods for Sparse Linear Systems, 2nd ed., Sec. 6.11 and 9.2), the
+# minimiser of the S-energy error |x - x*|_S over the preconditioned Krylov
+# space span{M^-1 g, (M^-1 S) M^-1 g, ..., (M^-1 S)^(k-1) M^-1 g}.  That
+# minimiser is computed here by a dense Galerkin projection, with S and M
+# formed from the dense damped normal equations, so a wrong beta, a p/z or
+# p/q mix-up in the update, or a restart at the second step changes the
+# iterate and fails.
+def _krylov_minimiser(S, Minv, g, k):
+    V = []
+    v = Minv @ g
+    for _ in range(k):
+        for _rep in range(2):  # Gram-Schmidt twice: the span is what matters
+            for u in V:
+                v = v - (u @ v) * u
+        V.append(v / np.linalg.norm(v))
+        v = Minv @ (S @ V[-1])
+    V = np.array(V).T
+    return V @ np.linalg.solve(V.T @ S @ V, V.T @ g)
+
+
+def _block_inverse(A, nb):
+    Ai = np.zeros_like(A)
+    for i in range(nb):
+        s = slice(9 * i, 9 * i + 9)
+        Ai[s, s] = np.linalg.inv(A[s, s])
+    return Ai
+
+
+@pytest.mark.parametrize("precond", ["block_jacobi", "schur_jacobi"])
+@pytest.mark.parametrize("schur", ["explicit_pcg", "implicit_pcg"])
+def test_truncated_pcg_iterate_is_the_krylov_energy_minimiser(precond, schur):
+    sc = make_scene(4, 25, sigma=1.0, seed=21)
+    mu = 1e-3
+    Hd, g, *_ = _damped_dense(sc, mu)
+    m = 9 * sc.nc
+    B, E, Cm = Hd[:m, :m], Hd[:m, m:], Hd[m:, m:]
+    S = B - E @ np.linalg.solve(Cm, E.T)
+    b = g[:m] - E @ np.linalg.solve(Cm, g[m:])
+    # block-Jacobi: M = blockdiag(B~_i) (Alg. 2); Schur-Jacobi: M = the diagonal
+    # 9x9 blocks of S (every (camera, point) pair is observed once here)
+    Minv = _block_inverse(B if precond == "block_jacobi" else S, sc.nc)
+    for k in range(1, 7):
+        ref = _krylov_minimiser(S, Minv, b, k)
+        r = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, schur=schur,
+                        pcg_max=k, pcg_tol=0.0, precond=precond)
+        assert r["pcg_iters"] == k
+        np.testing.assert_allclose(r["dc"].reshape(-1), ref, atol=1e-9 * np.abs(ref).max(), err_msg=f"k={k}")
+    # the iterates differ from step to step, so the comparison above has teeth
+    assert np.abs(_krylov_minimiser(S, Minv, b, 6) - _krylov_minimiser(S, Minv, b, 5)).max() > 1e-6 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# Trust-region radius after an ACCEPTED step (Nielsen's rule, H. B. Nielsen,
+# "Damping parameter in Marquardt's method", IMM-REP-1999-05; the rule the
+# Ceres trust region documents): radius /= max(1/3, 1 - (2 rho - 1)^3).  The
+# gain rho is recomputed here from costs and the linear model outside the LM
+# loop: F and F' by oracle.evaluate at x and x + dx, the model decrease from
+# the per-observation residuals and Jacobians, dx from the dense Schur solve
+# (pinned against a direct solve above).  The three scenes put rho in each
+# branch of the rule: below 1/2 (radius shrinks), between 1/2 and the knee
+# (grows by less than 3) and above the knee (grows by 3); max -> min, a
+# squared term or a dropped "- 1" each changes the next iteration's mu.
+@pytest.mark.parametrize("rot_sigma,point_sigma,seed,radius,lo,hi", [
+    (0.3, 0.3, 1, 1e3, 1e-3, 0.5),
+    (0.2, 0.1, 1, 1e3, 0.5, 0.9),
+    (0.01, 0.02, 0, 1.0, 0.95, 1.5),
+])
+def test_accepted_step_radius_follows_nielsen_rule(rot_sigma, point_sigma, seed, radius, lo, hi):
+    sc = make_scene(4, 25, sigma=1.0, seed=seed, rot_sigma=rot_sigma, point_sigma=point_sigma)
+    args = (sc.observations, sc.cam_idx, sc.pt_idx)
+    mu = 1.0 / radius
+    st = oracle.step(sc.cameras, sc.points, *args, mu, schur="dense")
+    F, e, Jc, Jp, W = oracle.evaluate(sc.cameras, sc.points, *args)
+    Fn = oracle.evaluate(sc.cameras + st["dc"], sc.points + st["dp"], *args, jacobians=False)[0]
+    f = e + np.einsum("kab,kb->ka", Jc, st["dc"][sc.cam_idx]) + np.einsum("kab,kb->ka", Jp, st["dp"][sc.pt_idx])
+    L = 0.5 * np.sum(W * (np.sum(e * e, axis=1) - np.sum(f * f, axis=1)))
+    rho = (F - Fn) / L
+    assert lo < rho < hi and L > 0
+    r = oracle.lm_solve(sc.cameras, sc.points, *args, max_iter=2, schur="dense", initial_radius=radius)
+    t0, t1 = r["trace"]
+    assert t0["accepted"] == 1 and t0["mu"] == pytest.approx(mu, rel=1e-15)
+    assert t0["gain"] == pytest.approx(rho, rel=1e-9)
+    expected_radius = radius / max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
+    assert t1["mu"] == pytest.approx(1.0 / expected_radius, rel=1e-9)
