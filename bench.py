@@ -32,6 +32,9 @@ UNIT = "LM iterations/s"
 CONFIG = 2
 LM_ITERS = 20
 PCG_MAX = 100
+FINAL_LM_ITERS = 30   # the Final-shaped problem's LM iterations
+CPU_LM_ITERS = 2      # LM iterations of the oracle's bounded sample
+CPU_SINGLE_SCALE = 0.1  # workload scale of the single-thread oracle sample
 
 
 def workload_desc(sc) -> str:
@@ -55,10 +58,28 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def pcg_bytes_per_iter(sc, w: int) -> float:
-    """Algorithmic bytes of one PCG iteration: the Jacobian stream and camera
-    index per observation, C~^-1 and a CSR offset per point, B~, B~^-1 and the
-    camera vectors per camera."""
-    return sc.n * (24 * w + 4) + sc.np_ * (6 * w + 4) + sc.nc * (2 * 81 * 8 + 6 * 9 * 8)
+    """Algorithmic bytes of one PCG iteration, by the method's per-unit counts
+    with the stored Jacobian taken as the minimum: per observation the Jacobian
+    (24 values) and a camera index; per point C~^-1 (6 doubles) and about six
+    vector entries; per camera the Cholesky factor of B~ (45 doubles) and about
+    six 9-vectors."""
+    return sc.n * (24 * w + 4) + sc.np_ * (6 * 8 + 6 * w) + sc.nc * (45 * 8 + 54 * w)
+
+
+def pcg_streamed_bytes_per_iter(sc) -> float:
+    """Bytes the factored FP32 Schur product streams per PCG iteration: per
+    observation (px, py, 1/P_z) 12, W Jp 24, camera index 4, position of s 4,
+    s written 8 in the point pass and (RX, 1/P_z) 16, s 8 in the camera pass;
+    per point C~^-1 (6 floats) and a CSR offset; per camera B~ and B~^-1 (81
+    doubles each) and six FP64 vectors of stride 12."""
+    return sc.n * 76 + sc.np_ * 28 + sc.nc * (2 * 81 * 8 + 6 * 12 * 8)
+
+
+def lin_bytes_per_obs(sc, w: int) -> float:
+    """Algorithmic bytes of the residual + Jacobian + block step per observation:
+    pixels (2w), two indices (8), the point amortised over its track (3w/L) and
+    the Jacobian written (24w)."""
+    return (26.0 + 3.0 * sc.np_ / sc.n) * w + 8.0
 
 
 # FP32 non-tensor peak derived from unit counts and clocks: 152 SMs x 128 FP32
@@ -93,15 +114,31 @@ def batch_flops(ws, summaries, schur: str) -> float:
     return tot
 
 
-# DRAM bytes per observation per PCG pass of pcg_kernel, measured by ncu on the
-# same kernel (profiles/pcg_kernel_fp32_venice_0.3.md: 5.317 GB read + 32.1 MB
-# written over 31 passes of 1,501,396 observations; FP64: 16.32 GB + 52.1 MB).
-# Traffic grows with the observation count, so a full launch moves this many
-# bytes per observation per pass.
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one PCG launch (30 iterations
-# plus the right-hand-side pass) on the full Venice-shaped problem, per observation
-# per pass (profiles/pcg_kernel_fp32_venice.md, profiles/pcg_kernel_fp64_venice.md)
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per observation
+# per pass of one pcg_kernel launch on the full Venice-shaped problem (30 PCG
+# iterations plus the right-hand-side pass, 5,004,484 observations), FP32-mixed
+# and FP64.  Traffic grows with the observation count, so a launch moves this
+# many bytes per observation per pass; None once the kernel has changed since
+# the capture.
 PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9394786048 + 97457664) / 31 / 5004484, 8: (63629832448 + 3470636288) / 31 / 5004484}
+
+
+def oracle_sample_time(threads: int, scale: float) -> dict:
+    """Seconds of one oracle LM iteration on the workload scaled by `scale`, in a
+    fresh process with `threads` OpenMP threads (0 = the default, all cores)."""
+    code = ("import json, sys, time; sys.path.insert(0, %r); import oracle; from scenes import config_scene; "
+            "sc = config_scene(%d, scale=%r); oracle.build(); t = time.perf_counter(); "
+            "oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=1, "
+            "pcg_max=%d, pcg_tol=1e-10); "
+            "print(json.dumps({'s': time.perf_counter() - t, 'threads': oracle.num_threads(), 'n': int(sc.n)}))"
+            % (ROOT, CONFIG, scale, PCG_MAX))
+    env = dict(os.environ)
+    if threads > 0:
+        env["OMP_NUM_THREADS"] = str(threads)
+    else:
+        env.pop("OMP_NUM_THREADS", None)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def pcg_flops_per_iter(sc) -> float:
@@ -288,6 +325,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-final", action="store_true", help="skip the Final-shaped leg")
     ap.add_argument("--profile-case", choices=["fp32", "fp64", "batch"], default=None,
                     help="profiling aid: run one small solve of the workload (see --scale, --windows) and exit; "
                          "prints no bench line")
@@ -336,7 +374,7 @@ def main():
             e0.record(stream)
             for _ in range(args.steps):
                 pr.reset()
-                sums.append(pr.solve(**opts))
+                sums.append(pr.solve(trace_capacity=LM_ITERS, **opts))
             e1.record(stream)
             torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
@@ -353,17 +391,25 @@ def main():
         pcg_ms = sum(s["ms_pcg"] for s in sums)
         pcg_iters = sum(s["pcg_iters_total"] for s in sums)
         launches = len(sums) * LM_ITERS  # one persistent PCG launch per LM iteration
-        alg_bytes = (pcg_iters + launches) * pcg_bytes_per_iter(sc, w)
-        alg_flops = (pcg_iters + launches) * pcg_flops_per_iter(sc)
+        passes = pcg_iters + launches  # the right-hand-side pass counts as one
+        alg_bytes = passes * pcg_bytes_per_iter(sc, w)
+        alg_flops = passes * pcg_flops_per_iter(sc)
+        traffic = PCG_TRAFFIC_B_PER_OBS_PASS.get(w)
+        # linearisations: the first one, then one after every accepted step that
+        # is not the solve's last iteration (a rejected step reuses the last one)
+        lins = sum(1 + sum(t["accepted"] for t in s["trace"][:-1]) for s in sums)
+        lin_ms = sum(s["ms_linearize"] for s in sums)
         return dict(value=value, ms_per_step=ms / args.steps, pcg_ms=pcg_ms, pcg_iters=pcg_iters,
                     pcg_launches=launches, gbs=alg_bytes / (pcg_ms / 1e3) / 1e9,
-                    traffic_per_launch=PCG_TRAFFIC_B_PER_OBS_PASS[w] * sc.n * (pcg_iters + launches) / launches,
-                    dram_gbs=PCG_TRAFFIC_B_PER_OBS_PASS[w] * sc.n * (pcg_iters + launches) / (pcg_ms / 1e3) / 1e9,
+                    streamed_gbs=passes * pcg_streamed_bytes_per_iter(sc) / (pcg_ms / 1e3) / 1e9,
+                    traffic_per_launch=None if traffic is None else traffic * sc.n * passes / launches,
+                    dram_gbs=None if traffic is None else traffic * sc.n * passes / (pcg_ms / 1e3) / 1e9,
                     alg_bytes_per_launch=alg_bytes / launches,
                     tflops=alg_flops / (pcg_ms / 1e3) / 1e12,
-                    us_per_pcg_iter=1e3 * pcg_ms / max(1, pcg_iters + launches),
+                    us_per_pcg_iter=1e3 * pcg_ms / max(1, passes),
+                    lin_ms_each=lin_ms / lins, lin_gbs=lins * sc.n * lin_bytes_per_obs(sc, w) / (lin_ms / 1e3) / 1e9,
                     final_cost=sums[-1]["final_cost"], kernel_launches=sum(s["kernel_launches"] for s in sums),
-                    pcg_share=pcg_ms / sum(s["ms_total"] for s in sums))
+                    accepted=sums[-1]["accepted"], pcg_share=pcg_ms / sum(s["ms_total"] for s in sums))
 
     a32, a64 = stats(ms32, s32, 4), stats(ms64, s64, 8)
     hbm_peak, peak_kind = peaks()
@@ -403,7 +449,8 @@ def main():
         variants = {}
         with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision="fp32",
                          stream=stream) as prv:
-            for name, kw in (("schur_jacobi", dict(preconditioner="schur_jacobi")), ("forcing", dict(forcing=1)),
+            for name, kw in (("float_float_cost", dict(cost_arithmetic="float-float")),
+                             ("schur_jacobi", dict(preconditioner="schur_jacobi")), ("forcing", dict(forcing=1)),
                              ("schur_jacobi+forcing", dict(preconditioner="schur_jacobi", forcing=1))):
                 ms_v = []
                 for _ in range(2):
@@ -411,16 +458,21 @@ def main():
                     torch.cuda.synchronize()
                     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     ev0.record(stream)
-                    sv = prv.solve(max_iter=LM_ITERS, pcg_max_iter=PCG_MAX, pcg_rel_tol=1e-10, **kw)
+                    sv = prv.solve(trace_capacity=LM_ITERS, max_iter=LM_ITERS, pcg_max_iter=PCG_MAX,
+                                   pcg_rel_tol=1e-10, **kw)
                     ev1.record(stream)
                     torch.cuda.synchronize()
                     ms_v.append(ev0.elapsed_time(ev1))
                 variants[name] = {"value": LM_ITERS / (min(ms_v) / 1e3), "unit": UNIT, "ms_per_solve": min(ms_v),
                                   "pcg_iters": sv["pcg_iters_total"], "final_cost": sv["final_cost"],
+                                  "accepted": sv["accepted"],
+                                  "same_accept_decisions_as_headline":
+                                      [t["accepted"] for t in sv["trace"]] == [t["accepted"] for t in s32[-1]["trace"]],
                                   "final_cost_rel_diff_vs_paper_solver":
                                       (sv["final_cost"] - a32["final_cost"]) / a32["final_cost"]}
-        variants["note"] = ("solver variants of the same workload (20 LM iterations, PCG <= 100): the headline "
-                            "value is Alg. 2 (block-Jacobi, fixed tolerance 1e-10)")
+        variants["note"] = ("variants of the same workload (20 LM iterations, PCG <= 100, FP32-mixed): the "
+                            "headline value is Alg. 2 (block-Jacobi, fixed tolerance 1e-10) with the FP64 "
+                            "accept/reject cost; float_float_cost evaluates that cost in float-float arithmetic")
 
     # Jacobian source (Sec. 3.2): the same solve with the Jacobian from the edge
     # functor on dual numbers instead of the hand-derived chain rule
@@ -549,21 +601,77 @@ def main():
                          "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
                          "counted": "FP32 operations of the schedule's Schur form (see batch_flops)",
                          "note": "whole launch time; the launch is latency-bound (FP64 vector chains, CTA "
-                                 "barriers), see profiles/batch_kernel_windows128.md"},
+                                 "barriers)"},
             "e2e": {"ms": 1e3 * e2e_b, "windows_per_s": len(ws) / e2e_b, "h2d_bytes_per_step": h2d_b,
                     "d2h_bytes_per_step": d2h_b},
         }
 
+    # Final-13682-shaped problem (13,000 cameras, 4.5M points, ~29M observations,
+    # 1% outliers, Huber delta 2 px): 30 LM iterations, PCG <= 100, FP32-mixed
+    # and FP64; one warm-up solve and one timed solve each
+    final = None
+    if rank == 0 and not args.no_final:
+        sc3 = config_scene(3)
+        final = {"workload": f"final-shaped synthetic BA: {sc3.nc} cameras, {sc3.np_} points, {sc3.n} observations, "
+                             f"1% outliers at 50 px, Huber delta 2 px, {FINAL_LM_ITERS} LM iterations, PCG <= "
+                             f"{PCG_MAX}, seed 2"}
+        for prec, w in (("fp32", 4), ("fp64", 8)):
+            with mba.Problem(sc3.cameras, sc3.points, sc3.observations, sc3.cam_idx, sc3.pt_idx, precision=prec,
+                             loss="huber", huber_delta=2.0, stream=stream) as pr3:
+                for rep in range(2):
+                    pr3.reset()
+                    torch.cuda.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    s3 = pr3.solve(max_iter=FINAL_LM_ITERS, pcg_max_iter=PCG_MAX, pcg_rel_tol=1e-10,
+                                   collect_timing=1)
+                    ev1.record(stream)
+                    torch.cuda.synchronize()
+                ms3 = ev0.elapsed_time(ev1)
+            passes = s3["pcg_iters_total"] + FINAL_LM_ITERS
+            final[prec] = {"value": FINAL_LM_ITERS / (ms3 / 1e3), "unit": UNIT, "ms_per_solve": ms3,
+                           "pcg_iters": s3["pcg_iters_total"], "accepted": s3["accepted"],
+                           "us_per_pcg_iter": 1e3 * s3["ms_pcg"] / passes,
+                           "pcg_alg_gbs": passes * pcg_bytes_per_iter(sc3, w) / (s3["ms_pcg"] / 1e3) / 1e9,
+                           "initial_cost": s3["initial_cost"], "final_cost": s3["final_cost"]}
+        final["final_cost_rel_diff_fp32_vs_fp64"] = ((final["fp32"]["final_cost"] - final["fp64"]["final_cost"]) /
+                                                     final["fp64"]["final_cost"])
+        del sc3
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
+        from oracle.align import parameter_error
 
         oracle.build()
+        # the oracle (FP64, host cores) on a bounded sample of the workload: its
+        # first CPU_LM_ITERS LM iterations; the GPU solves the same iterations in
+        # both forms and its cost and parameters are compared with the oracle's
         t = time.perf_counter()
-        oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=1, pcg_max=PCG_MAX)
+        ref = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=CPU_LM_ITERS,
+                              pcg_max=PCG_MAX, pcg_tol=1e-10)
         dt = time.perf_counter() - t
-        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": "one LM iteration (linearise, PCG <= 100, back-substitution, cost) of the same workload, FP64"}
+        parity = {"sample": f"first {CPU_LM_ITERS} LM iterations of the workload, PCG <= {PCG_MAX}",
+                  "oracle_accepted": [t_["accepted"] for t_ in ref["trace"]]}
+        for prec in ("fp64", "fp32"):
+            with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=prec,
+                             stream=stream) as prp:
+                sp = prp.solve(trace_capacity=CPU_LM_ITERS, max_iter=CPU_LM_ITERS, pcg_max_iter=PCG_MAX,
+                               pcg_rel_tol=1e-10)
+                cg, pg = prp.parameters()
+            parity[prec] = {"final_cost_rel_diff": (sp["final_cost"] - ref["final_cost"]) / ref["final_cost"],
+                            "accepted": [t_["accepted"] for t_ in sp["trace"]],
+                            "parameter_error": parameter_error(cg, pg, ref["cameras"], ref["points"])}
+        single = oracle_sample_time(1, CPU_SINGLE_SCALE)
+        multi = oracle_sample_time(0, CPU_SINGLE_SCALE)
+        cpu = {"value": CPU_LM_ITERS / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{CPU_LM_ITERS} LM iterations (linearise, PCG <= {PCG_MAX}, back-substitution, cost) of the "
+                         "same workload, FP64",
+               "single_thread": {"value": 1.0 / single["s"], "unit": UNIT, "cores": single["threads"],
+                                 "value_all_cores_same_sample": 1.0 / multi["s"], "cores_all": multi["threads"],
+                                 "sample": f"one LM iteration of the workload scaled by {CPU_SINGLE_SCALE} "
+                                           f"({single['n']} observations)"},
+               "parity_vs_gpu": parity}
 
     if rank != 0:
         return 0
@@ -571,36 +679,51 @@ def main():
         "metric": METRIC, "value": a32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": a32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64 (FP32-mixed)", "data": "synthetic",
-        "config": {"workload": workload_desc(sc), "precision": "fp32-mixed",
-                   "l2": "inputs larger than L2 (per PCG pass: 0.26 GB streamed FP32, 1.7 GB FP64)",
+        "config": {"workload": workload_desc(sc), "precision": "fp32-mixed (FP64 accept/reject cost)",
+                   "l2": "inputs larger than L2 (per PCG pass: 0.38 GB streamed FP32, 1.7 GB FP64)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"kernel": "pcg_kernel (persistent PCG, implicit Schur product)", "bound": "hbm",
                      "achieved": a32["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": a32["gbs"] / hbm_peak,
                      "peak_kind": peak_kind, "traffic": a32["traffic_per_launch"],
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read+write per observation per pass of a "
-                                     "full-size launch, times this run's observations and passes; profiles/)",
+                                     "full-size launch, times this run's observations and passes)",
                      "algorithmic_bytes_per_launch": a32["alg_bytes_per_launch"],
-                     "algorithmic": "stored-Jacobian count: 100 B per observation per pass plus per-point and "
-                                    "per-camera terms; the factored FP32 product streams fewer bytes than that",
-                     "dram_gbs": a32["dram_gbs"], "dram_frac": a32["dram_gbs"] / hbm_peak,
+                     "algorithmic": "per PCG iteration 100 B per observation (stored Jacobian + camera index), "
+                                    "72 B per point, 576 B per camera",
+                     "streamed_gbs": a32["streamed_gbs"], "streamed_frac": a32["streamed_gbs"] / hbm_peak,
+                     "streamed": "bytes the factored FP32 product actually streams: 76 B per observation per "
+                                 "iteration, 28 B per point, 1.9 KB per camera",
+                     "dram_gbs": a32["dram_gbs"],
+                     "dram_frac": None if a32["dram_gbs"] is None else a32["dram_gbs"] / hbm_peak,
                      "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"],
-                     "pcg_iters_per_solve": a32["pcg_iters"] / max(1, len(s32))},
-        "fp64": {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms_per_step"],
-                 "final_cost": a64["final_cost"],
-                 "roofline": {"kernel": "pcg_kernel<double>", "bound": "alu", "achieved": a64["tflops"],
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a64["tflops"] / FP64_PEAK_TFLOPS,
-                              "peak_kind": "derived (152 SMs x 2 DFMA/clk x 2.07 GHz)", "hbm_gbs": a64["gbs"],
-                              "us_per_pcg_iter": a64["us_per_pcg_iter"]},
-                 "clocks": clk64},
-        "final_cost": a32["final_cost"],
+                     "pcg_iters_per_solve": a32["pcg_iters"] / max(1, len(s32)),
+                     "other_kernels": {
+                         "linearize_fp32": {"kernel": "lin_point + lin_camera + cam_finalize (+ camera table)",
+                                            "bound": "hbm", "achieved": a32["lin_gbs"], "unit": "GB/s",
+                                            "frac": a32["lin_gbs"] / hbm_peak,
+                                            "ms_per_linearisation": a32["lin_ms_each"],
+                                            "algorithmic_bytes_per_obs": lin_bytes_per_obs(sc, 4)},
+                         "linearize_fp64": {"achieved": a64["lin_gbs"], "unit": "GB/s",
+                                            "frac": a64["lin_gbs"] / hbm_peak,
+                                            "ms_per_linearisation": a64["lin_ms_each"],
+                                            "algorithmic_bytes_per_obs": lin_bytes_per_obs(sc, 8)},
+                         "pcg_fp64": {"bound": "alu", "achieved": a64["tflops"], "peak": FP64_PEAK_TFLOPS,
+                                      "unit": "TFLOP/s", "frac": a64["tflops"] / FP64_PEAK_TFLOPS,
+                                      "peak_kind": "derived (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                                      "alg_gbs": a64["gbs"], "dram_gbs": a64["dram_gbs"],
+                                      "us_per_pcg_iter": a64["us_per_pcg_iter"]}}},
+        "final_cost": a32["final_cost"], "accepted": a32["accepted"],
         "final_cost_rel_diff_vs_fp64": abs(a32["final_cost"] - a64["final_cost"]) / a64["final_cost"],
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": s32 and sum(s["kernel_launches"] for s in s32),
-        "layer": layer,
         "variants": variants,
         "autodiff": autodiff,
+        "layer": layer,
         "batched": batched,
+        "final": final,
+        "fp64": {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms_per_step"],
+                 "final_cost": a64["final_cost"], "accepted": a64["accepted"], "clocks": clk64},
         "clocks": clk32,
     }
     print(json.dumps(line), flush=True)

@@ -70,6 +70,16 @@ typedef enum { MBA_PRECOND_BLOCK_JACOBI = 0, MBA_PRECOND_SCHUR_JACOBI = 1 } mba_
  * Jacobian (72 bytes per observation) for the PCG camera pass. */
 typedef enum { MBA_JACOBIAN_ANALYTIC = 0, MBA_JACOBIAN_AUTODIFF = 1 } mba_jacobian;
 
+/* Arithmetic of the cost F(x) and F(x + dx) that decides LM accept/reject (Alg. 1;
+ * supplement, trust region).  FP64 (default): every residual and the sum in FP64.
+ * FLOAT_FLOAT (option of the FP32-mixed analytic form only; other problems ignore it
+ * and keep FP64): residuals and sums in float-float arithmetic (pairs of floats,
+ * about 48 significant bits, Dekker's and Knuth's error-free transformations) on the
+ * FP32 pipe, which is faster than the FP64 pipe; its relative error per residual is
+ * about 1e-13, so accept/reject decisions can differ from FP64 only where the gain
+ * ratio sits within that of the acceptance threshold. */
+typedef enum { MBA_COST_FP64 = 0, MBA_COST_FLOAT_FLOAT = 1 } mba_cost_arithmetic;
+
 typedef struct {
     int32_t precision;   /* mba_precision.  FP32_MIXED: Jacobian, Hessian blocks and the
                             PCG Schur product in FP32; block inversions, PCG dot
@@ -96,6 +106,7 @@ typedef struct {
                                       PCG tolerance is max(pcg_rel_tol, min(0.1, sqrt(|g|/|g_1|))), |g| the
                                       norm of its reduced right-hand side, |g_1| that of the solve's first
                                       damped step; 0: pcg_rel_tol throughout (default) */
+    int32_t cost_arithmetic;       /* mba_cost_arithmetic (default FP64) */
 } mba_solver_options;
 
 /* One LM iteration as recorded by mba_solve. */
@@ -128,7 +139,8 @@ typedef struct {
 } mba_summary;
 
 /* Defaults: FP64, no loss, delta 0, default stream / max_iter 10, pcg_max_iter 100,
- * pcg_rel_tol 1e-10, DIAG damping, radius 1e4, min decrease 1e-3, function_tol 0. */
+ * pcg_rel_tol 1e-10, DIAG damping, radius 1e4, min decrease 1e-3, function_tol 0,
+ * FP64 accept/reject cost. */
 void mba_problem_options_default(mba_problem_options *opt);
 void mba_solver_options_default(mba_solver_options *opt);
 
@@ -376,6 +388,16 @@ mba_status mba_batch_get_gradients(const mba_batch *batch, double *grad_obs, dou
 const char *mba_status_string(mba_status status);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mba_last_error(void);
+
+/* Process-wide cap on the device memory that one mba_problem_create (its pool
+ * plus the set-up scratch it frees before returning) or one mba_batch_create may
+ * allocate; 0 (the default) means no cap.  A creation that would exceed the cap
+ * returns MBA_ERR_OOM before allocating anything, exactly as if the device had
+ * run out of memory, so callers can budget device memory per handle and test
+ * their out-of-memory handling without exhausting the GPU.  Handles created
+ * earlier are not affected.  The paper has no counterpart (its tables report
+ * memory use only).  Always returns MBA_OK. */
+mba_status mba_set_device_memory_limit(size_t bytes);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 // iterations without host round trips, and the inspection entry points.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,12 @@ struct Carve {
 }  // namespace
 
 namespace mba {
+// process-wide cap on the device memory one creation may allocate (0 = none)
+static std::atomic<unsigned long long> g_mem_limit{0};
+bool over_memory_limit(size_t bytes) {
+    const unsigned long long l = g_mem_limit.load();
+    return l != 0 && (unsigned long long)bytes > l;
+}
 mba_status api_fail(mba_status st, const char *msg) {
     g_err = msg ? msg : "";
     return st;
@@ -94,6 +101,7 @@ void mba_solver_options_default(mba_solver_options *o) {
     o->collect_timing = 0;
     o->preconditioner = MBA_PRECOND_BLOCK_JACOBI;
     o->forcing = 0;
+    o->cost_arithmetic = MBA_COST_FP64;
 }
 
 const char *mba_status_string(mba_status s) {
@@ -110,6 +118,11 @@ const char *mba_status_string(mba_status s) {
 }
 
 const char *mba_last_error(void) { return g_err.c_str(); }
+
+mba_status mba_set_device_memory_limit(size_t bytes) {
+    mba::g_mem_limit.store((unsigned long long)bytes);
+    return MBA_OK;
+}
 
 void mba_problem_destroy(mba_problem *pr) {
     if (!pr) return;
@@ -213,6 +226,9 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
         P.pm2cm = c.take<int32_t>(n);
+        P.pm_uv32 = P.fp32 ? c.take<float2>(n) : nullptr;
+        P.cm_uv32 = P.fp32 ? c.take<float2>(n) : nullptr;
+        P.pts32 = P.fp32 ? c.take<float4>((size_t)np) : nullptr;
         // copies for the PCG: the camera-major stored Jacobian (FP64, or FP32-mixed
         // with dual numbers), else the factored form's per-observation data
         const bool fact = P.fact != 0;
@@ -241,6 +257,13 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     layout(sizing);
     pr->pool_bytes = sizing.off;
     P.red_len = red_len;
+    const size_t sort_tmp = stable_sort_tmp_bytes(n, np > nc ? np : nc);
+    const size_t setup_bytes = sort_tmp + al(sizeof(double) * 2 * (size_t)n) + 256;
+    if (mba::over_memory_limit(pr->pool_bytes + setup_bytes)) {
+        const size_t need = pr->pool_bytes + setup_bytes;
+        delete pr;
+        return fail(MBA_ERR_OOM, "device memory limit: creation needs " + std::to_string(need) + " bytes");
+    }
     if (cudaMalloc(&pr->pool, pr->pool_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete pr;
@@ -252,9 +275,8 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     P.cfirst = pr->cfirst;
 
     // temporary buffers for the set-up only
-    const size_t sort_tmp = stable_sort_tmp_bytes(n, np > nc ? np : nc);
     void *tmp = nullptr;
-    if (cudaMalloc(&tmp, sort_tmp + al(sizeof(double) * 2 * (size_t)n) + 256) != cudaSuccess) {
+    if (cudaMalloc(&tmp, setup_bytes) != cudaSuccess) {
         cudaGetLastError();
         mba_problem_destroy(pr);
         return fail(MBA_ERR_OOM, "set-up scratch");
@@ -448,7 +470,8 @@ bool valid_solver_opts(const mba_solver_options &o) {
            (o.damping == MBA_DAMP_DIAG || o.damping == MBA_DAMP_IDENTITY) && o.initial_radius > 0.0 &&
            o.function_tol >= 0.0 && o.barrier_spin_limit >= 0 &&
            (o.preconditioner == MBA_PRECOND_BLOCK_JACOBI || o.preconditioner == MBA_PRECOND_SCHUR_JACOBI) &&
-           (o.forcing == 0 || o.forcing == 1);
+           (o.forcing == 0 || o.forcing == 1) &&
+           (o.cost_arithmetic == MBA_COST_FP64 || o.cost_arithmetic == MBA_COST_FLOAT_FLOAT);
 }
 
 }  // namespace
@@ -633,10 +656,13 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
     for (int i = 0; i < ne; ++i) CK(cudaEventCreate(&ev[i]));
     auto rec = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(ev[i], s) : cudaSuccess; };
 
+    // accept/reject cost: FP64, or float-float on the FP32 pipe when asked for
+    // (FP32-mixed analytic problems only: the float-float pixels exist there)
+    const bool ff = P.fact != 0 && o.cost_arithmetic == MBA_COST_FLOAT_FLOAT;
     CK(rec(0));
     CK(launch_state_init(P, o.initial_radius, -1.0, 0, s));
     CK(launch_camera_tables(P, P.cams, false, s));
-    CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s, P.fact != 0));
+    CK(launch_cost_impl(P, P.pts, pr->part_b, &P.st->cost, &P.st->initial_cost, 1, s, ff));
     for (int it = 0; it < o.max_iter; ++it) {
         CK(rec(1 + 4 * it));
         CK(launch_camera_tables(P, P.cams, true, s));
@@ -648,19 +674,19 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         CK(rec(4 + 4 * it));
         CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
         CK(launch_camera_tables(P, P.cams_new, false, s));
-        CK(launch_cost_impl(P, P.pts_new, pr->part_b, &P.st->cost_new, nullptr, 1, s, P.fact != 0));
+        CK(launch_cost_impl(P, P.pts_new, pr->part_b, &P.st->cost_new, nullptr, 1, s, ff));
         CK(launch_lm_update(P, o, s));
         CK(launch_accept(P, s));
     }
     CK(rec(ne > 0 ? ne - 1 : 0));
     // state_init, camera table, 2 cost kernels; per iteration: camera table, 3
     // linearisation, 2 damping, PCG, 3 back-substitution, camera table, 2 cost,
-    // LM update, accept; the factored form adds the camera rows of dc and the
-    // float-float point copy before each cost, the Schur-Jacobi preconditioner
-    // two damping kernels
-    const int fact = P.fact ? 1 : 0;
+    // LM update, accept; the factored form adds the camera rows of dc, the
+    // float-float cost its point copy before each cost, the Schur-Jacobi
+    // preconditioner two damping kernels
+    const int fact = P.fact ? 1 : 0, ffc = ff ? 1 : 0;
     const int launches =
-        4 + fact + (15 + 2 * fact + (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI ? 2 : 0)) * o.max_iter;
+        4 + ffc + (15 + fact + ffc + (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI ? 2 : 0)) * o.max_iter;
     DevState hs;
     mba_status st = check_device_state(pr, &hs);
     if (summary) {

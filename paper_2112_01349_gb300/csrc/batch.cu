@@ -1988,6 +1988,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                  o_bptr = explicit_ok ? take(4 * blk_ptr.size()) : 0,
                  o_jcm = explicit_ok ? take(24 * w * (size_t)N) : 0,
                  o_S = explicit_ok ? take(w * (size_t)smax * (size_t)b->sms * kMaxCtasPerSm) : 0;
+    if (over_memory_limit(off)) return fail_free(MBA_ERR_OOM, "device memory limit: the batch needs more");
     if (cudaMalloc(&b->pool, off) != cudaSuccess) {
         cudaGetLastError();
         return fail_free(MBA_ERR_OOM, "device allocation of the batch failed");

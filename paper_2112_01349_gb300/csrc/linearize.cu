@@ -64,6 +64,24 @@ __global__ void split_points_kernel(const double *__restrict__ pts, int64_t m, f
     }
 }
 
+// FP32 copy of the pixels for the FP32-mixed linearisation (made once).
+__global__ void uv32_kernel(const double2 *__restrict__ uv, int64_t n, float2 *__restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = uv[k];
+        out[k] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// FP32 copy of the current points for the FP32-mixed linearisation, one float4
+// per point; runs where the linearisation runs (same gate).
+__global__ void point_table_kernel(const double *__restrict__ pts, int32_t np, float4 *__restrict__ out,
+                                   const DevState *st, int gate) {
+    if (gate && (st->done || !st->relin)) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x)
+        out[j] = make_float4((float)pts[3 * (int64_t)j], (float)pts[3 * (int64_t)j + 1], (float)pts[3 * (int64_t)j + 2],
+                             0.f);
+}
+
 __global__ void split_uv_kernel(const double2 *__restrict__ uv, int64_t n, float4 *__restrict__ out) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const ff u = ff_from(uv[k].x), v = ff_from(uv[k].y);
@@ -132,11 +150,11 @@ __device__ __forceinline__ void lin_point_obs(const Prob &P, int64_t o, int cam,
     T *__restrict__ J = (T *)P.J;
     T *__restrict__ res = (T *)P.res;
     const int64_t np_ = P.npad;
-    const double2 uv = __ldg(P.pm_uv + o);
+    T X0, X1, X2, u0, u1;
+    load_point<T>(P, pt, X0, X1, X2);
+    load_uv<T>(P.pm_uv, P.pm_uv32, o, u0, u1);
     T e[2], Jc[18], Jp[6], pz[3];
-    edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)__ldg(P.pts + 3 * (int64_t)pt),
-                     (T)__ldg(P.pts + 3 * (int64_t)pt + 1), (T)__ldg(P.pts + 3 * (int64_t)pt + 2), (T)uv.x, (T)uv.y, e,
-                     Jc, Jp, FACT ? pz : nullptr);
+    edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, X0, X1, X2, u0, u1, e, Jc, Jp, FACT ? pz : nullptr);
     T rho, W;
     loss_weight<T>(P.loss, (T)P.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
     const T sw = sqrt(W);
@@ -261,11 +279,11 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
         for (int q = 0; q < 54; ++q) acc[q] = T(0);
         for (int s = b0 + lane; s < b1; s += 32) {
             const int pt = P.cm_pt[s];
-            const double2 uv = P.cm_uv[s];
+            T X0, X1, X2, u0, u1;
+            load_point<T>(P, pt, X0, X1, X2);
+            load_uv<T>(P.cm_uv, P.cm_uv32, s, u0, u1);
             T e[2], Jc[18], Jp[6], pz[3];
-            edge_eval<T, AD, true, false>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
-                                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp,
-                                          (sizeof(T) == 4 && !AD) ? pz : nullptr);
+            edge_eval<T, AD, true, false>(ctab, X0, X1, X2, u0, u1, e, Jc, Jp, (sizeof(T) == 4 && !AD) ? pz : nullptr);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);
@@ -281,8 +299,6 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
                 for (int q = 0; q < 18; ++q) ((T *)P.JcmT)[(int64_t)q * P.npad + s] = Jc[q];
             }
             if (sizeof(T) == 4 && !AD && P.fact) {
-                const T X0 = (T)P.pts[3 * (int64_t)pt], X1 = (T)P.pts[3 * (int64_t)pt + 1],
-                        X2 = (T)P.pts[3 * (int64_t)pt + 2];
                 ((float4 *)P.RXcm)[s] = make_float4((float)(ctab[0] * X0 + ctab[1] * X1 + ctab[2] * X2),
                                                     (float)(ctab[3] * X0 + ctab[4] * X1 + ctab[5] * X2),
                                                     (float)(ctab[6] * X0 + ctab[7] * X1 + ctab[8] * X2), (float)pz[2]);
@@ -408,6 +424,8 @@ cudaError_t launch_camera_tables_forced(const Prob &P, const double *cams, cudaS
 
 cudaError_t launch_split_observations(const Prob &P, cudaStream_t s) {
     if (P.uvff) split_uv_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_uv, P.n, P.uvff);
+    if (P.pm_uv32) uv32_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.pm_uv, P.n, P.pm_uv32);
+    if (P.cm_uv32) uv32_kernel<<<grid_for(P.n), kBlock, 0, s>>>(P.cm_uv, P.n, P.cm_uv32);
     return cudaGetLastError();
 }
 
@@ -423,6 +441,7 @@ static void launch_lin_pair(const Prob &P, int force, cudaStream_t s) {
 
 cudaError_t launch_linearize_impl(const Prob &P, const int32_t *cfirst, int force, cudaStream_t s) {
     if (P.fp32) {
+        point_table_kernel<<<grid_for(P.np), kBlock, 0, s>>>(P.pts, P.np, P.pts32, P.st, force ? 0 : 1);
         if (P.autodiff) launch_lin_pair<float, true>(P, force, s);
         else launch_lin_pair<float, false>(P, force, s);
     } else {

@@ -79,6 +79,12 @@ struct Prob {
     double2 *cm_uv;
     int32_t *cam_ptr;              // nc + 1
     int32_t *pm2cm;                // per point-major position: its camera-major position
+    // FP32-mixed: float copies of the pixels (point-major and camera-major, made at
+    // creation) and of the current points (refreshed at every linearisation), so
+    // the FP32 kernels convert nothing per observation (on GB300 a conversion from
+    // FP64 runs on the FP64 pipe); null in FP64 problems
+    float2 *pm_uv32, *cm_uv32;
+    float4 *pts32;
     // chunk tables
     int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
     int32_t *cfirst;               // nc + 1: first camera chunk of each camera
@@ -254,6 +260,35 @@ __device__ __forceinline__ void project(const T *__restrict__ ct, T X0, T X1, T 
     }
 }
 
+// The point and the pixels of an observation in the precision T of the
+// linearisation: FP64 problems read the FP64 arrays, FP32-mixed problems their
+// float copies (the same bits as converting here).
+template <typename T>
+__device__ __forceinline__ void load_point(const Prob &P, int pt, T &X0, T &X1, T &X2) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(P.pts32 + pt);
+        X0 = v.x;
+        X1 = v.y;
+        X2 = v.z;
+    } else {
+        X0 = __ldg(P.pts + 3 * (int64_t)pt);
+        X1 = __ldg(P.pts + 3 * (int64_t)pt + 1);
+        X2 = __ldg(P.pts + 3 * (int64_t)pt + 2);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void load_uv(const double2 *uv64, const float2 *uv32, int64_t o, T &u0, T &u1) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = __ldg(uv32 + o);
+        u0 = v.x;
+        u1 = v.y;
+    } else {
+        const double2 v = __ldg(uv64 + o);
+        u0 = v.x;
+        u1 = v.y;
+    }
+}
+
 // Residual and Jacobians of one observation from either source: the analytic
 // chain rule (project) or the edge functor on dual numbers (AD), whose camera
 // parameters come from the table row (w at 25..27, t, f, k1, k2 at 18..23).
@@ -407,6 +442,9 @@ cudaError_t launch_adjoint_init(const Prob &P, int damping, double mu, cudaStrea
 
 // api.cu: records msg as the calling thread's mba_last_error() text and returns st
 mba_status api_fail(mba_status st, const char *msg);
+// true if a creation needing `bytes` of device memory exceeds the cap set by
+// mba_set_device_memory_limit
+bool over_memory_limit(size_t bytes);
 
 // lm.cu
 cudaError_t launch_state_init(const Prob &P, double radius, double mu_override, int keep_cost, cudaStream_t s);

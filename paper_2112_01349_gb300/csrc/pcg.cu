@@ -175,10 +175,11 @@ __global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
         for (int q = 0; q < 45; ++q) acc[q] = T(0);
         for (int s = b0 + threadIdx.x; s < b1; s += kBlock) {
             const int pt = P.cm_pt[s];
-            const double2 uv = P.cm_uv[s];
+            T X0, X1, X2, u0, u1;
+            load_point<T>(P, pt, X0, X1, X2);
+            load_uv<T>(P.cm_uv, P.cm_uv32, s, u0, u1);
             T e[2], Jc[18], Jp[6];
-            edge_eval<T, AD>(ctab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
-                             (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+            edge_eval<T, AD>(ctab, X0, X1, X2, u0, u1, e, Jc, Jp);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             T c6[6], q0[3], q1[3];

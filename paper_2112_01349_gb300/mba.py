@@ -28,6 +28,8 @@ MBA_PRECOND_BLOCK_JACOBI, MBA_PRECOND_SCHUR_JACOBI = 0, 1
 PRECONDITIONER = {"block_jacobi": MBA_PRECOND_BLOCK_JACOBI, "schur_jacobi": MBA_PRECOND_SCHUR_JACOBI}
 MBA_JACOBIAN_ANALYTIC, MBA_JACOBIAN_AUTODIFF = 0, 1
 JACOBIAN = {"analytic": MBA_JACOBIAN_ANALYTIC, "autodiff": MBA_JACOBIAN_AUTODIFF}
+MBA_COST_FP64, MBA_COST_FLOAT_FLOAT = 0, 1
+COST_ARITHMETIC = {"fp64": MBA_COST_FP64, "float-float": MBA_COST_FLOAT_FLOAT}
 
 
 class MbaError(RuntimeError):
@@ -45,7 +47,7 @@ class SolverOptions(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("pcg_max_iter", C.c_int32), ("pcg_rel_tol", C.c_double),
                 ("damping", C.c_int32), ("initial_radius", C.c_double), ("min_relative_decrease", C.c_double),
                 ("function_tol", C.c_double), ("barrier_spin_limit", C.c_int64), ("collect_timing", C.c_int32),
-                ("preconditioner", C.c_int32), ("forcing", C.c_int32)]
+                ("preconditioner", C.c_int32), ("forcing", C.c_int32), ("cost_arithmetic", C.c_int32)]
 
 
 class Iteration(C.Structure):
@@ -129,6 +131,7 @@ def load():
             "mba_bal_write": (C.c_int, [C.c_char_p, i32, i32, i64, P, P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
+            "mba_set_device_memory_limit": (C.c_int, [C.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -242,6 +245,8 @@ def solver_options(**kw) -> SolverOptions:
             v = PRECONDITIONER[v]
         if k == "forcing":
             v = int(bool(v))
+        if k == "cost_arithmetic" and isinstance(v, str):
+            v = COST_ARITHMETIC[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown solver option {k}")
         setattr(o, k, v)
@@ -350,6 +355,12 @@ def mba_cost_noalloc(d_cameras, nc, d_points, np_, d_observations, d_cam_idx, d_
     _check(load().mba_cost_noalloc(C.c_void_p(d_cameras), int(nc), C.c_void_p(d_points), int(np_),
                                    C.c_void_p(d_observations), C.c_void_p(d_cam_idx), C.c_void_p(d_pt_idx), int(n),
                                    lb, float(huber_delta), C.c_void_p(d_cost), _stream_handle(stream)))
+
+
+def mba_set_device_memory_limit(nbytes: int) -> None:
+    """Cap the device memory one creation may allocate (0 = no cap); creations
+    over the cap fail with MBA_ERR_OOM before allocating."""
+    _check(load().mba_set_device_memory_limit(int(nbytes)))
 
 
 class Problem:

@@ -139,20 +139,22 @@ def test_step_fp64(mba, kind):
     assert st["model_dec"] == pytest.approx(ref["model_dec"], rel=1e-6)
 
 
+@pytest.mark.parametrize("arith,rtol", [("fp64", 1e-12), ("float-float", 1e-11)])
 @pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber"), ("cfg1", "none")])
-def test_fp32_mixed_solve_cost_matches_fp64(mba, kind, loss):
-    """The FP32-mixed solve evaluates the cost for accept/reject in float-float
-    arithmetic: its initial and final costs equal the oracle's FP64 costs at the
-    same parameters to 1e-11 relative."""
+def test_fp32_mixed_solve_cost_matches_fp64(mba, kind, loss, arith, rtol):
+    """The FP32-mixed solve evaluates the cost for accept/reject in FP64 (the
+    default) or, as an option, in float-float arithmetic: its initial and final
+    costs equal the oracle's FP64 costs at the same parameters to 1e-12 (FP64)
+    or 1e-11 (float-float) relative."""
     sc = _scene(kind)
     rc0 = oracle.evaluate(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0,
                           jacobians=False)[0]
     with _problem(mba, sc, "fp32", loss=loss, delta=2.0) as pr:
-        s = pr.solve(max_iter=3, pcg_max_iter=20)
+        s = pr.solve(max_iter=3, pcg_max_iter=20, cost_arithmetic=arith)
         cams, pts = pr.parameters()
     rc1 = oracle.evaluate(cams, pts, sc.observations, sc.cam_idx, sc.pt_idx, loss, 2.0, jacobians=False)[0]
-    assert s["initial_cost"] == pytest.approx(rc0, rel=1e-11)
-    assert s["final_cost"] == pytest.approx(rc1, rel=1e-11)
+    assert s["initial_cost"] == pytest.approx(rc0, rel=rtol)
+    assert s["final_cost"] == pytest.approx(rc1, rel=rtol)
 
 
 @pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber")])
@@ -269,3 +271,30 @@ def test_non_positive_definite_block_is_a_rejected_iteration(mba):
         if t["pcg_iters"] == 0:
             assert not t["accepted"] and not np.isfinite(t["cost_new"])
     assert s["final_cost"] <= s["initial_cost"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_resume_from_a_checkpoint_continues_the_trajectory(mba, precision):
+    """Checkpoint / resume through host memory: a solve stopped after an
+    accepted step, checkpointed (parameters read back, final radius kept) and
+    resumed in a fresh handle created from those parameters with that radius,
+    continues the uninterrupted solve bit for bit (after any accepted step the
+    trust region's decrease factor is 2, as at a start).  Tiny workload, split
+    after the third iteration, both forms."""
+    sc = _scene("cfg1")
+    kw = dict(pcg_max_iter=50, pcg_rel_tol=1e-10)
+    with _problem(mba, sc, precision) as pr:
+        full = pr.solve(trace_capacity=10, max_iter=10, **kw)
+        cams_full, pts_full = pr.parameters()
+        pr.reset()
+        first = pr.solve(trace_capacity=3, max_iter=3, **kw)
+        cams_ck, pts_ck = pr.parameters()
+    assert first["trace"][-1]["accepted"] == 1
+    with mba.Problem(cams_ck, pts_ck, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision) as pr2:
+        rest = pr2.solve(trace_capacity=7, max_iter=7, initial_radius=first["final_radius"], **kw)
+        cams, pts = pr2.parameters()
+    assert rest["final_cost"] == full["final_cost"]
+    assert [t["cost_new"] for t in rest["trace"]] == [t["cost_new"] for t in full["trace"][3:]]
+    assert [t["accepted"] for t in rest["trace"]] == [t["accepted"] for t in full["trace"][3:]]
+    np.testing.assert_array_equal(cams, cams_full)
+    np.testing.assert_array_equal(pts, pts_full)
