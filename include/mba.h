@@ -184,6 +184,22 @@ mba_status mba_set_parameters(mba_problem *problem, const double *cameras, const
 mba_status mba_reset(mba_problem *problem);
 
 /*
+ * Hold cameras and points constant, as the fixed vertices of the g2o / Ceres
+ * graph convention that the paper's API follows (Sec. 5.3).  cam_fixed (nc
+ * bytes) and pt_fixed (np bytes) are host arrays; a nonzero byte marks a node
+ * fixed; NULL means none of that kind is fixed (so mba_set_fixed(p, NULL, NULL)
+ * clears every mark).  A fixed node's Jacobian columns are taken as zero in
+ * every solve-side computation: its Hessian block and gradient vanish, it has no
+ * Schur coupling, its step (mba_step, mba_solve) is exactly zero and it stays
+ * bit-identical; its initial-estimate gradient (mba_adjoint) is the upstream
+ * gradient and it contributes nothing to the observation gradient.
+ * mba_evaluate still reports the model's full Jacobians.  The marks persist
+ * until the next call.  Errors: MBA_ERR_INVALID_ARG for a NULL problem,
+ * MBA_ERR_CUDA.
+ */
+mba_status mba_set_fixed(mba_problem *problem, const uint8_t *cam_fixed, const uint8_t *pt_fixed);
+
+/*
  * The stable orderings built at creation: pt_perm[n] lists observation indices
  * grouped by point (increasing index within a point), pt_ptr[np + 1] its CSR
  * offsets; cam_perm / cam_ptr likewise by camera.  Any output may be NULL.

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kBlock) adjoint_obs_kernel(Prob P, const int32
         T e[2], Jc[18], Jp[6];
         edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, (T)P.pts[3 * (int64_t)pt], (T)P.pts[3 * (int64_t)pt + 1],
                          (T)P.pts[3 * (int64_t)pt + 2], (T)uv.x, (T)uv.y, e, Jc, Jp);
+        zero_fixed_columns<T>(P, cam, pt, Jc, Jp);
         T rho, W;
         loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
         const double *vc = P.x + (int64_t)cam * kVec;

@@ -191,12 +191,15 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.pm_pt = c.take<int32_t>(n);
         P.pm_orig = c.take<int32_t>(n);
         P.pm_uv = c.take<double2>(n);
-        P.pt_ptr = c.take<int32_t>((size_t)np + 1);
+        P.pt_ptr = c.take<int32_t>((size_t)np + 64);  // slack for 16-byte-rounded bulk copies
         P.cm_pt = c.take<int32_t>(n);
         P.cm_orig = c.take<int32_t>(n);
         P.cm_uv = c.take<double2>(n);
         P.cam_ptr = c.take<int32_t>((size_t)nc + 1);
-        P.wchunk = c.take<int2>((size_t)np + 2);
+        P.wchunk = c.take<int2>((size_t)np + 64);
+        P.tiles = c.take<int2>((size_t)np + 2);
+        P.tdesc = c.take<int4>(3 * ((size_t)np + 2));
+        P.long_chunks = c.take<int32_t>((size_t)np + 2);
         P.cchunk_cam = c.take<int32_t>(cbound);
         P.cchunk_beg = c.take<int32_t>(cbound + 1);
         pr->cfirst = c.take<int32_t>((size_t)nc + 1);
@@ -214,7 +217,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.cpart = c.take<double>(54 * (size_t)cbound);
         P.Bd = c.take<double>(81 * (size_t)nc);
         P.Binv = c.take<double>(81 * (size_t)nc);
-        P.Cinv = c.take<char>(6 * (size_t)np * w);
+        P.Cinv = c.take<char>((6 * (size_t)np + 64) * w);
         P.x = c.take<double>((size_t)nc * kVec);
         P.r = c.take<double>((size_t)nc * kVec);
         P.z = c.take<double>((size_t)nc * kVec);
@@ -225,10 +228,12 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         P.p2 = c.take<double>((size_t)nc * kVec);
         P.sbuf = c.take<char>(2 * (size_t)P.npad * w);
         P.cta_cam = c.take<int32_t>(4096 + 1);
-        P.pm2cm = c.take<int32_t>(n);
+        P.pm2cm = c.take<int32_t>(n + 64);
         P.pm_uv32 = P.fp32 ? c.take<float2>(n) : nullptr;
         P.cm_uv32 = P.fp32 ? c.take<float2>(n) : nullptr;
         P.pts32 = P.fp32 ? c.take<float4>((size_t)np) : nullptr;
+        P.cam_fixed = c.take<uint8_t>((size_t)nc);
+        P.pt_fixed = c.take<uint8_t>((size_t)np);
         // copies for the PCG: the camera-major stored Jacobian (FP64, or FP32-mixed
         // with dual numbers), else the factored form's per-observation data
         const bool fact = P.fact != 0;
@@ -300,6 +305,8 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     CKC(cudaMemcpyAsync(obs_d, observations, sizeof(double) * 2 * (size_t)n, cudaMemcpyHostToDevice, s));
     CKC(cudaMemcpyAsync(pr->orig_cam, cam_idx, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
     CKC(cudaMemcpyAsync(pr->orig_pt, pt_idx, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemsetAsync(P.cam_fixed, 0, (size_t)nc, s));
+    CKC(cudaMemsetAsync(P.pt_fixed, 0, (size_t)np, s));
     CKC(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, s));
     CKC(validate_inputs(P.cams, nc, P.pts, np, obs_d, pr->orig_cam, pr->orig_pt, n, flags, s));
     int32_t hflags[4];
@@ -404,6 +411,50 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         }
         wc.push_back(make_int2(np, (int32_t)n));
         P.n_wchunks = (int32_t)wc.size() - 1;
+        // tiles of the staged point pass: greedy runs of consecutive chunks with at
+        // most 32 observations each, within the stage capacity; a chunk of a longer
+        // track ends the run and is listed apart
+        std::vector<int2> tiles;
+        std::vector<int32_t> longs;
+        {
+            int32_t tb = -1, tobs = 0, tpts = 0;
+            auto close = [&](int32_t end) {
+                if (tb >= 0) tiles.push_back(make_int2(tb, end));
+                tb = -1;
+                tobs = tpts = 0;
+            };
+            for (int32_t k = 0; k < P.n_wchunks; ++k) {
+                const int32_t m = wc[k + 1].y - wc[k].y, npts = wc[k + 1].x - wc[k].x;
+                if (m > 32) {
+                    close(k);
+                    longs.push_back(k);
+                    continue;
+                }
+                if (tb >= 0 && (tobs + m > kTileObs || tpts + npts > kTilePts || k - tb + 1 > kTileChunks)) close(k);
+                if (tb < 0) tb = k;
+                tobs += m;
+                tpts += npts;
+            }
+            close(P.n_wchunks);
+        }
+        P.n_tiles = (int32_t)tiles.size();
+        P.n_long = (int32_t)longs.size();
+        // copy ranges of each tile, rounded to 16 bytes: observations [w0.y, w1.y),
+        // C~^-1 floats of points [w0.x, w1.x), CSR offsets pt_ptr[w0.x .. w1.x], chunk
+        // entries [cb, ce]
+        std::vector<int4> tdesc(3 * tiles.size());
+        for (size_t t = 0; t < tiles.size(); ++t) {
+            const int2 w0 = wc[tiles[t].x], w1 = wc[tiles[t].y];
+            tdesc[3 * t] = make_int4(w0.y & ~3, (w1.y + 3) & ~3, (6 * w0.x) & ~3, (6 * w1.x + 3) & ~3);
+            tdesc[3 * t + 1] = make_int4(w0.x & ~3, (w1.x + 4) & ~3, tiles[t].x & ~1, (tiles[t].y + 2) & ~1);
+            tdesc[3 * t + 2] = make_int4(tiles[t].x, tiles[t].y, 0, 0);
+        }
+        if (!tiles.empty()) {
+            CKC(cudaMemcpyAsync(P.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s));
+            CKC(cudaMemcpyAsync(P.tdesc, tdesc.data(), sizeof(int4) * tdesc.size(), cudaMemcpyHostToDevice, s));
+        }
+        if (!longs.empty())
+            CKC(cudaMemcpyAsync(P.long_chunks, longs.data(), sizeof(int32_t) * longs.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaMemcpyAsync(P.wchunk, wc.data(), sizeof(int2) * wc.size(), cudaMemcpyHostToDevice, s));
         CKC(cudaStreamSynchronize(s));
     }
@@ -521,6 +572,24 @@ mba_status mba_set_parameters(mba_problem *pr, const double *cameras, const doub
     if (cameras) CK(cudaMemcpyAsync(P.cams, cameras, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyHostToDevice, pr->stream));
     if (points) CK(cudaMemcpyAsync(P.pts, points, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyHostToDevice, pr->stream));
     CK(cudaStreamSynchronize(pr->stream));
+    return MBA_OK;
+}
+
+mba_status mba_set_fixed(mba_problem *pr, const uint8_t *cam_fixed, const uint8_t *pt_fixed) {
+    g_err.clear();
+    if (!pr) return fail(MBA_ERR_INVALID_ARG, "problem is NULL");
+    Prob &P = pr->P;
+    int any = 0;
+    if (cam_fixed)
+        for (int32_t i = 0; i < P.nc && !any; ++i) any = cam_fixed[i] != 0;
+    if (pt_fixed)
+        for (int32_t j = 0; j < P.np && !any; ++j) any = pt_fixed[j] != 0;
+    if (cam_fixed) CK(cudaMemcpyAsync(P.cam_fixed, cam_fixed, (size_t)P.nc, cudaMemcpyHostToDevice, pr->stream));
+    else CK(cudaMemsetAsync(P.cam_fixed, 0, (size_t)P.nc, pr->stream));
+    if (pt_fixed) CK(cudaMemcpyAsync(P.pt_fixed, pt_fixed, (size_t)P.np, cudaMemcpyHostToDevice, pr->stream));
+    else CK(cudaMemsetAsync(P.pt_fixed, 0, (size_t)P.np, pr->stream));
+    CK(cudaStreamSynchronize(pr->stream));
+    P.has_fixed = any;
     return MBA_OK;
 }
 

@@ -155,6 +155,7 @@ __device__ __forceinline__ void lin_point_obs(const Prob &P, int64_t o, int cam,
     load_uv<T>(P.pm_uv, P.pm_uv32, o, u0, u1);
     T e[2], Jc[18], Jp[6], pz[3];
     edge_eval<T, AD>(camtab + (int64_t)cam * kCamTab, X0, X1, X2, u0, u1, e, Jc, Jp, FACT ? pz : nullptr);
+    zero_fixed_columns<T>(P, cam, pt, Jc, Jp);
     T rho, W;
     loss_weight<T>(P.loss, (T)P.delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
     const T sw = sqrt(W);
@@ -194,7 +195,7 @@ __device__ __forceinline__ void lin_point_obs(const Prob &P, int64_t o, int cam,
 // and per point C = sum Jp~^T Jp~ and w = -sum Jp~^T e~ by a segmented shuffle
 // scan in a fixed order, with no shared memory or CTA barrier.
 template <typename T, bool AD>
-__global__ void __launch_bounds__(kBlock) lin_point_kernel(Prob P, int force) {
+__global__ void __launch_bounds__(kBlock, 4) lin_point_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const unsigned full = 0xffffffffu;
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
             load_uv<T>(P.cm_uv, P.cm_uv32, s, u0, u1);
             T e[2], Jc[18], Jp[6], pz[3];
             edge_eval<T, AD, true, false>(ctab, X0, X1, X2, u0, u1, e, Jc, Jp, (sizeof(T) == 4 && !AD) ? pz : nullptr);
+            zero_fixed_columns<T>(P, cam, pt, Jc, (T *)nullptr);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             const T sw = sqrt(W);

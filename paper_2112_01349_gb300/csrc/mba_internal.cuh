@@ -18,6 +18,20 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kCamTab = 28;          // values per camera in the camera table
 constexpr int kVec = 12;             // padded stride of 9-vectors per camera (16-B aligned rows)
 constexpr int kRow = 12;             // floats per camera row of the factored FP32 Schur product
+// Staged point pass of the factored FP32 PCG: tiles of whole warp chunks copied
+// into shared memory by 1-D bulk copies.  A tile holds at most kTileObs
+// observations, kTilePts points and kTileChunks chunks; a stage holds one tile:
+// per observation the camera index, the camera-major position of s, W Jp (6) and
+// (px, py, 1/Pz) (3), each row with 8 words of slack for 16-byte rounding, then
+// the points' C~^-1 (6 floats each), their CSR offsets and the chunk table.
+constexpr int kTileObs = 1024, kTilePts = 384, kTileChunks = 31, kMaxStages = 4;
+constexpr int kTileRow = kTileObs + 8;
+constexpr int kStwSo = kTileRow, kStwJh = 2 * kTileRow, kStwPx = 8 * kTileRow, kStwCinv = 11 * kTileRow;
+constexpr int kStwPtp = kStwCinv + 6 * kTilePts + 8, kStwWch = kStwPtp + kTilePts + 8;
+constexpr int kStageWords = kStwWch + 2 * (kTileChunks + 4);
+constexpr int kStageBytes = (kStageWords * 4 + 127) & ~127;
+static_assert(kTileRow % 4 == 0 && kStwCinv % 4 == 0 && kStwPtp % 4 == 0 && kStwWch % 4 == 0,
+              "16-byte aligned stage rows");
 constexpr int kCamChunk = 256;       // observations per camera-major chunk (at least)
 constexpr int kMaxTrack = 1024;      // longest supported point track
 
@@ -85,6 +99,22 @@ struct Prob {
     // FP64 runs on the FP64 pipe); null in FP64 problems
     float2 *pm_uv32, *cm_uv32;
     float4 *pts32;
+    // nodes held constant (mba_set_fixed): nonzero bytes mark fixed cameras and
+    // points; has_fixed = 0 while none is fixed, so no kernel reads the masks
+    uint8_t *cam_fixed, *pt_fixed;
+    int32_t has_fixed;
+    // staged point pass (factored FP32 form): tiles (first chunk, end chunk) of
+    // whole warp chunks with <= 32 observations, tile t worked by CTA t mod grid;
+    // chunks of longer tracks are listed apart and read from global memory
+    int2 *tiles;
+    int4 *tdesc;            // per tile: (oa, ob, ca, cz), (pa, pz, wa, wz), (first chunk, end chunk, 0, 0):
+                            // the 16-byte-rounded copy ranges of its observation rows, C~^-1 floats,
+                            // CSR offsets and chunk entries
+    int32_t n_tiles;
+    int32_t *long_chunks;
+    int32_t n_long;
+    int32_t pcg_stages;     // stages of the staged point pass (0: not staged)
+    int32_t pcg_stage_off;  // byte offset of the stages in the PCG kernel's dynamic shared memory
     // chunk tables
     int32_t *cchunk_cam, *cchunk_beg;  // n_cchunks, n_cchunks + 1
     int32_t *cfirst;               // nc + 1: first camera chunk of each camera
@@ -289,6 +319,23 @@ __device__ __forceinline__ void load_uv(const double2 *uv64, const float2 *uv32,
     }
 }
 
+// Nodes held constant (mba_set_fixed) have zero Jacobian columns, the convention
+// of g2o / Ceres for fixed vertices that the paper's graph API follows (Sec.
+// 5.3): their blocks, gradients and Schur couplings vanish, so their step is
+// exactly zero and they stay bit-identical.  Jc or Jp may be null.
+template <typename T>
+__device__ __forceinline__ void zero_fixed_columns(const Prob &P, int cam, int pt, T *Jc, T *Jp) {
+    if (!P.has_fixed) return;
+    if (Jc && P.cam_fixed[cam]) {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) Jc[q] = T(0);
+    }
+    if (Jp && P.pt_fixed[pt]) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) Jp[q] = T(0);
+    }
+}
+
 // Residual and Jacobians of one observation from either source: the analytic
 // chain rule (project) or the edge functor on dual numbers (AD), whose camera
 // parameters come from the table row (w at 25..27, t, f, k1, k2 at 18..23).
@@ -369,6 +416,43 @@ __device__ __forceinline__ double block_sum(double v, double *sbuf) {
 // acquire load sees k * gridDim.x.  A CTA that polls more than `limit` times, or sees the error
 // flag raised, records MBA_ERR_TIMEOUT and returns false; the caller must
 // then leave the kernel.  Returns true when every CTA has arrived.
+// ---------------------------------------------------------------------------
+// mbarrier and 1-D bulk copy (cp.async.bulk) helpers for shared-memory staging.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival that also expects `bytes` of bulk-copy completions in this phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// wait for the phase of the given parity to complete; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long long limit) {
     __shared__ int s_ok;
     __syncthreads();

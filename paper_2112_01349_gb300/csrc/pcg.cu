@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kBlock) sj_camera_kernel(Prob P) {
             load_uv<T>(P.cm_uv, P.cm_uv32, s, u0, u1);
             T e[2], Jc[18], Jp[6];
             edge_eval<T, AD>(ctab, X0, X1, X2, u0, u1, e, Jc, Jp);
+            zero_fixed_columns<T>(P, cam, pt, Jc, Jp);
             T rho, W;
             loss_weight<T>(P.loss, delta, e[0] * e[0] + e[1] * e[1], &rho, &W);
             T c6[6], q0[3], q1[3];
@@ -576,6 +577,52 @@ __device__ __forceinline__ void fact_jc_v(float px, float py, float iz, const fl
     t[1] = -(a01 * z0 + a11 * z1) + py * ei;
 }
 
+// One point with a long track (more than 32 observations, one warp): two
+// sweeps over 32-observation slices, reading global memory.
+template <bool RHS>
+__device__ void long_chunk_fact(const Prob &P, const float *ps, const float *pT, float2 *sbuf, int pt, int o0, int m) {
+    const float *__restrict__ Jh = P.Jph;
+    const float *__restrict__ PX = P.PXpm;
+    const int64_t npad = P.npad;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    float ci[6], b[3];
+    load_sym3((const float *)P.Cinv + 6 * (int64_t)pt, ci);
+    if (RHS) {
+        apply_sym3(ci, (float)P.w[3 * (int64_t)pt], (float)P.w[3 * (int64_t)pt + 1], (float)P.w[3 * (int64_t)pt + 2],
+                   b);
+    } else {
+        float a[3] = {0.f, 0.f, 0.f};
+        for (int base = 0; base < m; base += 32) {
+            if (base + lane < m) {
+                const int64_t o = (int64_t)o0 + base + lane;
+                float r[kRow], t[2];
+                gather_row(ps, pT, __ldcs(P.pm_cam + o), r);
+                fact_jc_v(__ldcs(PX + o), __ldcs(PX + npad + o), __ldcs(PX + 2 * npad + o), r, t);
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    a[q] += __ldcs(Jh + q * npad + o) * t[0] + __ldcs(Jh + (3 + q) * npad + o) * t[1];
+            }
+        }
+#pragma unroll
+        for (int dl = 16; dl > 0; dl >>= 1) {
+            a[0] += __shfl_xor_sync(full, a[0], dl);
+            a[1] += __shfl_xor_sync(full, a[1], dl);
+            a[2] += __shfl_xor_sync(full, a[2], dl);
+        }
+        apply_sym3(ci, a[0], a[1], a[2], b);
+    }
+    for (int base = 0; base < m; base += 32) {
+        if (base + lane < m) {
+            const int64_t o = (int64_t)o0 + base + lane;
+            float jh[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) jh[q] = __ldcs(Jh + q * npad + o);
+            store_s<float>(sbuf, __ldcs(P.pm2cm + o), jh, b);
+        }
+    }
+}
+
 // Point pass of the factored form: as point_pass, with u = (W Jp)^T (Jc p)
 // and s = (W Jp) b, so the camera pass forms sum Jc^T s with unscaled Jc.
 template <bool RHS>
@@ -666,47 +713,214 @@ __device__ void point_pass_fact(const Prob &P, const float *ps, const float *pT,
             }
             if (act) store_s<float>(sbuf, so, jh, b);
         } else {
-            // one point with a long track: two sweeps over 32-observation slices
-            const int pt = c0.x;
-            float ci[6], b[3];
-            load_sym3(Cinv + 6 * (int64_t)pt, ci);
-            if (RHS) {
-                apply_sym3(ci, (float)P.w[3 * (int64_t)pt], (float)P.w[3 * (int64_t)pt + 1],
-                           (float)P.w[3 * (int64_t)pt + 2], b);
-            } else {
-                float a[3] = {0.f, 0.f, 0.f};
-                for (int base = 0; base < m; base += 32) {
-                    if (base + lane < m) {
-                        const int64_t o = (int64_t)o0 + base + lane;
-                        float r[kRow], t[2];
-                        gather_row(ps, pT, __ldcs(P.pm_cam + o), r);
-                        fact_jc_v(__ldcs(PX + o), __ldcs(PX + npad + o), __ldcs(PX + 2 * npad + o), r, t);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            a[q] += __ldcs(Jh + q * npad + o) * t[0] + __ldcs(Jh + (3 + q) * npad + o) * t[1];
-                    }
-                }
-#pragma unroll
-                for (int dl = 16; dl > 0; dl >>= 1) {
-                    a[0] += __shfl_xor_sync(full, a[0], dl);
-                    a[1] += __shfl_xor_sync(full, a[1], dl);
-                    a[2] += __shfl_xor_sync(full, a[2], dl);
-                }
-                apply_sym3(ci, a[0], a[1], a[2], b);
-            }
-            for (int base = 0; base < m; base += 32) {
-                if (base + lane < m) {
-                    const int64_t o = (int64_t)o0 + base + lane;
-                    float jh[6];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) jh[q] = __ldcs(Jh + q * npad + o);
-                    store_s<float>(sbuf, __ldcs(P.pm2cm + o), jh, b);
-                }
-            }
+            long_chunk_fact<RHS>(P, ps, pT, sbuf, c0.x, o0, m);
         }
         c0 = n0;
         c1 = n1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Staged point pass of the factored form (iterations and the single product;
+// the right-hand-side pass keeps point_pass_fact).  A producer/consumer
+// pipeline in shared memory: the CTA's last warp copies the CTA's tiles (tile t
+// belongs to CTA t mod grid) into S stages with 1-D bulk copies, each stage
+// completing on its "full" mbarrier; the other warps wait for a stage, work on
+// it from shared memory (one warp chunk each), and release it on its "empty"
+// mbarrier, which the producer waits on before refilling the stage.  There is no
+// CTA-wide barrier between tiles, so warps drift across tiles and the copies run
+// up to S tiles ahead of the slowest consumer.  The per-observation streams do
+// not change within a launch, so the producer also runs ahead into the next
+// pass, across the camera pass and the grid barriers.  Use index u of the CTA
+// (counted over the whole launch) lives in stage u mod S; its full phase has
+// parity (u / S) mod 2, and so has the empty phase that releases it.
+// ---------------------------------------------------------------------------
+struct StageOrg {
+    int32_t oa, ca, pa, wa;  // first index copied of the observation rows, C~^-1 floats, pt_ptr, chunk table
+    int32_t cb, ce;          // the tile's chunks [cb, ce)
+    int32_t ok, pad;         // 0: the tile did not fit its stage (not copied)
+};
+constexpr long long kStageSpin = 1ll << 20;  // polls of a stage barrier before giving up
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Producer warp (all lanes): the copies of use `use` into stage use mod S, one
+// array per lane; d0..d2 is the tile's descriptor (in every lane).
+__device__ void stage_issue(const Prob &P, unsigned char *stages, uint64_t *full, StageOrg *org, int S, uint32_t use,
+                            int4 d0, int4 d1, int4 d2) {
+    const int lane = threadIdx.x & 31;
+    const int sidx = (int)(use % (uint32_t)S);
+    const int oa = d0.x, ob = d0.y, ca = d0.z, cz = d0.w, pa = d1.x, pz = d1.y, wa = d1.z, wz = d1.w;
+    const bool fits = d2.y > d2.x && ob - oa <= kTileRow && cz - ca <= 6 * kTilePts + 8 && pz - pa <= kTilePts + 8 &&
+                      wz - wa <= kTileChunks + 4 && d2.y - d2.x <= kTileChunks;
+    const uint32_t bo = 4u * (uint32_t)(ob - oa);
+    uint64_t *bar = full + sidx;
+    float *st = (float *)(stages + (size_t)sidx * kStageBytes);
+    if (lane == 0) {
+        org[sidx] = StageOrg{oa, ca, pa, wa, d2.x, d2.y, fits ? 1 : 0, 0};
+        const uint32_t total = 11u * bo + 4u * (uint32_t)(cz - ca) + 4u * (uint32_t)(pz - pa) + 8u * (uint32_t)(wz - wa);
+        mbar_arrive_expect_tx(bar, fits ? total : 0u);
+    }
+    __syncwarp();
+    if (!fits || lane >= 14) return;
+    const void *src;
+    void *dst;
+    uint32_t bytes = bo;
+    if (lane == 0) {
+        src = P.pm_cam + oa;
+        dst = st;
+    } else if (lane == 1) {
+        src = P.pm2cm + oa;
+        dst = st + kStwSo;
+    } else if (lane < 8) {
+        src = P.Jph + (int64_t)(lane - 2) * P.npad + oa;
+        dst = st + kStwJh + (lane - 2) * kTileRow;
+    } else if (lane < 11) {
+        src = P.PXpm + (int64_t)(lane - 8) * P.npad + oa;
+        dst = st + kStwPx + (lane - 8) * kTileRow;
+    } else if (lane == 11) {
+        src = (const float *)P.Cinv + ca;
+        dst = st + kStwCinv;
+        bytes = 4u * (uint32_t)(cz - ca);
+    } else if (lane == 12) {
+        src = P.pt_ptr + pa;
+        dst = st + kStwPtp;
+        bytes = 4u * (uint32_t)(pz - pa);
+    } else {
+        src = P.wchunk + wa;
+        dst = st + kStwWch;
+        bytes = 8u * (uint32_t)(wz - wa);
+    }
+    bulk_g2s(dst, src, bytes, bar);
+}
+
+// One warp chunk of a stage (at most 32 observations), as point_pass_fact with
+// every per-observation and per-point input read from the stage.
+__device__ __forceinline__ void staged_chunk(const float *ps, const float *pT, float2 *sbuf, const float *st,
+                                             const StageOrg &o, int k) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int *s_cam = (const int *)st, *s_so = (const int *)(st + kStwSo);
+    const float *s_jh = st + kStwJh, *s_px = st + kStwPx, *s_ci = st + kStwCinv;
+    const int *s_ptp = (const int *)(st + kStwPtp);
+    const int2 *s_wch = (const int2 *)(st + kStwWch);
+    const int2 c0 = s_wch[k - o.wa], c1 = s_wch[k + 1 - o.wa];
+    const int o0 = c0.y, m = c1.y - c0.y;  // at most 32: longer tracks are not in tiles
+    const bool act = lane < m;
+    const int li = o0 - o.oa + (act ? lane : 0);
+    const int npts = c1.x - c0.x;
+    const int rs = lane < npts ? s_ptp[c0.x + lane - o.pa] - o0 : 32;
+    const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+    const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+    float jh[6], ci[6], u[3] = {0.f, 0.f, 0.f};
+    int so = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) jh[q] = ci[q] = 0.f;
+    if (act) {
+        so = s_so[li];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) jh[q] = s_jh[q * kTileRow + li];
+        // C~^-1 of the point, from the stage (plain shared-memory loads)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ci[q] = s_ci[6 * pt - o.ca + q];
+        float r[kRow], t[2];
+        gather_row(ps, pT, s_cam[li], r);
+        fact_jc_v(s_px[li], s_px[kTileRow + li], s_px[2 * kTileRow + li], r, t);
+        u[0] = jh[0] * t[0] + jh[3] * t[1];
+        u[1] = jh[1] * t[0] + jh[4] * t[1];
+        u[2] = jh[2] * t[0] + jh[5] * t[1];
+    }
+    // inclusive segmented scan keyed by point (segments are contiguous)
+#pragma unroll
+    for (int dl = 1; dl < 32; dl <<= 1) {
+        const int kp = __shfl_up_sync(full, pt, dl);
+        const float v0 = __shfl_up_sync(full, u[0], dl), v1 = __shfl_up_sync(full, u[1], dl),
+                    v2 = __shfl_up_sync(full, u[2], dl);
+        if (lane >= dl && kp == pt) {
+            u[0] += v0;
+            u[1] += v1;
+            u[2] += v2;
+        }
+    }
+    const int nxt = __shfl_down_sync(full, pt, 1);
+    const bool tail = act && (lane == 31 || lane == m - 1 || nxt != pt);
+    const unsigned tails = __ballot_sync(full, tail);
+    float bt[3], b[3];
+    apply_sym3(ci, u[0], u[1], u[2], bt);
+    const unsigned mine = tails & (0xffffffffu << lane);
+    const int src = mine ? __ffs(mine) - 1 : lane;
+    b[0] = __shfl_sync(full, bt[0], src);
+    b[1] = __shfl_sync(full, bt[1], src);
+    b[2] = __shfl_sync(full, bt[2], src);
+    if (act) store_s<float>(sbuf, so, jh, b);
+}
+
+// The staged pass.  `base` counts the uses consumed before this pass (the same
+// in every thread); `issued` the uses issued so far (the producer warp's).
+// Returns false in every thread if a stage barrier gave up (the error is recorded).
+__device__ bool point_pass_fact_staged(const Prob &P, const float *ps, const float *pT, float2 *sbuf,
+                                       unsigned char *stages, uint64_t *full, uint64_t *empty, StageOrg *org, int S,
+                                       int my_nt, uint32_t &base, uint32_t &issued) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const uint32_t Su = (uint32_t)S;
+    bool ok = true;
+    if (wid == nwarp - 1) {
+        // producer: through the first S uses of the next pass, each after the
+        // consumers released its stage (the tile's descriptor is read first, so
+        // its latency overlaps the wait)
+        const uint32_t target = my_nt > 0 ? base + (uint32_t)my_nt + Su : 0u;
+        while (issued < target) {
+            const uint32_t u = issued;
+            const int t = (int)blockIdx.x + (int)(u % (uint32_t)my_nt) * (int)gridDim.x;
+            int4 d = make_int4(0, 0, 0, 0);
+            if (lane < 3) d = __ldg(P.tdesc + 3 * (int64_t)t + lane);
+            if (u >= Su && !mbar_wait(empty + u % Su, (u / Su - 1u) & 1u, kStageSpin)) {
+                if (lane == 0) atomicCAS(&P.st->err, 0, (int)MBA_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            int4 d0, d1, d2;
+            d0.x = __shfl_sync(0xffffffffu, d.x, 0), d0.y = __shfl_sync(0xffffffffu, d.y, 0);
+            d0.z = __shfl_sync(0xffffffffu, d.z, 0), d0.w = __shfl_sync(0xffffffffu, d.w, 0);
+            d1.x = __shfl_sync(0xffffffffu, d.x, 1), d1.y = __shfl_sync(0xffffffffu, d.y, 1);
+            d1.z = __shfl_sync(0xffffffffu, d.z, 1), d1.w = __shfl_sync(0xffffffffu, d.w, 1);
+            d2.x = __shfl_sync(0xffffffffu, d.x, 2), d2.y = __shfl_sync(0xffffffffu, d.y, 2);
+            d2.z = 0, d2.w = 0;
+            stage_issue(P, stages, full, org, S, u, d0, d1, d2);
+            ++issued;
+        }
+    } else {
+        // consumers: warp w works chunk w of every tile, then releases the stage
+        for (int j = 0; j < my_nt; ++j) {
+            const uint32_t u = base + (uint32_t)j;
+            const int sidx = (int)(u % Su);
+            if (!mbar_wait(full + sidx, (u / Su) & 1u, kStageSpin)) {
+                if (lane == 0) atomicCAS(&P.st->err, 0, (int)MBA_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            const StageOrg o = org[sidx];
+            if (o.ok) {
+                const int k = o.cb + wid;
+                if (k < o.ce) staged_chunk(ps, pT, sbuf, (const float *)(stages + (size_t)sidx * kStageBytes), o, k);
+            } else if (wid == 0 && lane == 0) {
+                atomicCAS(&P.st->err, 0, (int)MBA_ERR_INVALID_ARG);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + sidx);
+        }
+    }
+    base += (uint32_t)my_nt;
+    // chunks of tracks longer than 32 observations, over every warp of the grid
+    if (ok)
+        for (int i = (int)blockIdx.x * nwarp + wid; i < P.n_long; i += (int)gridDim.x * nwarp) {
+            const int k = P.long_chunks[i];
+            const int2 c0 = P.wchunk[k], c1 = P.wchunk[k + 1];
+            long_chunk_fact<false>(P, ps, pT, sbuf, c0.x, c0.y, c1.y - c0.y);
+        }
+    return __syncthreads_or(ok ? 0 : 1) == 0;
 }
 
 template <typename T, bool RHS, bool FACT>
@@ -877,6 +1091,9 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         double cs = 0.0;
         if (act)
             for (int k = P.cfirst[cm]; k < P.cfirst[cm + 1]; ++k) cs += cslot[(k - k0) * 9 + a];
+        // a fixed camera has no Schur coupling (its Jacobian columns are zero; the
+        // factored product forms Jc^T s from the geometry, so it is masked here)
+        if (P.has_fixed && act && P.cam_fixed[cm]) cs = 0.0;
         double v1 = 0.0, v2 = 0.0;
         if (MODE == CAM_RHS) {
             const double g = act ? P.v[9 * (int64_t)cm + a] - cs : 0.0;
@@ -1103,6 +1320,42 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     double *cslot = (double *)(smem_raw + P.pcg_ps_bytes);
     bool ok = true;
     auto barrier = [&]() -> bool { return grid_barrier(st, epoch, spin); };
+    // staged point pass (factored form): stage barriers, use counters, and the
+    // drain that waits for copies still in flight before the CTA leaves
+    __shared__ __align__(8) uint64_t s_full[kMaxStages], s_empty[kMaxStages];
+    __shared__ StageOrg s_org[kMaxStages];
+    const int S = FACT ? P.pcg_stages : 0;
+    const uint32_t Su = S > 0 ? (uint32_t)S : 1u;
+    unsigned char *stages = smem_raw + P.pcg_stage_off;
+    const int my_nt = (S && P.n_tiles > (int)blockIdx.x) ? (P.n_tiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+    uint32_t use = 0, issued = 0;
+    if (S) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < S; ++i) {
+                mbar_init(s_full + i, 1);
+                mbar_init(s_empty + i, (uint32_t)(nwarp - 1));
+            }
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
+    // the producer warp's first lane waits for the copies it issued beyond the
+    // last consumed use before the CTA leaves
+    auto drain = [&]() {
+        if (S && threadIdx.x == (unsigned)(nwarp - 1) * 32)
+            for (uint32_t u = use; u < issued; ++u)
+                if (!mbar_wait(s_full + u % Su, (u / Su) & 1u, kStageSpin)) {
+                    atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
+                    break;
+                }
+    };
+    auto point_pass_iter = [&]() -> bool {
+        if (FACT && S)
+            return point_pass_fact_staged(P, (const float *)ps, (const float *)pT, (float2 *)sbuf, stages, s_full,
+                                          s_empty, s_org, S, my_nt, use, issued);
+        point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
+        return true;
+    };
     // owner phase: p = z + beta p_prev written in FP64 and, for the gathers, as
     // T (or, in the factored form, as the camera's row)
     auto phase_p = [&](const double *p_prev, double *p_cur, double beta, bool first, const double *given) {
@@ -1128,9 +1381,9 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             phase_p(nullptr, nullptr, 0.0, true, P.p);
             if (!(ok = barrier())) return;
         }
-        point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
-        if (!barrier()) return;
-        camera_pass<T, CAM_MATVEC, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
+        const bool pok = point_pass_iter();
+        if (pok && barrier()) camera_pass<T, CAM_MATVEC, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
+        drain();
         return;
     }
 
@@ -1188,7 +1441,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                 phase_p(p_prev, p_cur, beta, n == 0, nullptr);
                 if (!(ok = barrier())) break;
             }
-            point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
+            if (!(ok = point_pass_iter())) break;
             if (!(ok = barrier())) break;
             {
                 const double2 d = camera_pass<T, CAM_ITER, JS>(P, sbuf, p_prev, p_cur,
@@ -1257,6 +1510,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             if (!s_go) break;
         }
     }
+    drain();
     if (!ok) atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
     if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
         st->pcg_iters = n;
@@ -1485,7 +1739,18 @@ void plan_pcg_smem(Prob &P) {
     const int64_t psb = (((int64_t)P.nc * per_cam * w) + 127) & ~(int64_t)127;
     P.pcg_use_ps = (psb + slots <= budget) ? 1 : 0;
     P.pcg_ps_bytes = P.pcg_use_ps ? (int)psb : 0;
-    P.pcg_smem = (int)(P.pcg_ps_bytes + slots);
+    // the staged point pass of the factored form: as many stages (3..kMaxStages)
+    // as fit beside the rest, else none.  With two stages the next tile's copy is
+    // not covered by one tile of work and the pass runs slower than the direct
+    // one (Venice-shaped problem: 134 against 109 us per PCG iteration)
+    const int64_t base = ((P.pcg_ps_bytes + slots) + 127) & ~(int64_t)127;
+    const bool ranges_ok = 6 * (int64_t)P.np + 64 < (int64_t)INT32_MAX && (int64_t)P.n + 64 < (int64_t)INT32_MAX;
+    int64_t stages = P.fact && P.n_tiles > 0 && ranges_ok ? (budget - base) / kStageBytes : 0;
+    if (stages > kMaxStages) stages = kMaxStages;
+    if (stages < 3) stages = 0;
+    P.pcg_stages = (int)stages;
+    P.pcg_stage_off = (int)base;
+    P.pcg_smem = stages ? (int)(base + stages * kStageBytes) : (int)(P.pcg_ps_bytes + slots);
 }
 
 int pcg_block(const Prob &P) { return P.fp32 ? PcgBlock<float>::value : PcgBlock<double>::value; }
@@ -1514,6 +1779,10 @@ cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long l
     const size_t smem = (size_t)P.pcg_smem;
     // the barrier targets count arrivals from zero in every launch
     cudaError_t e = cudaMemsetAsync(&P.st->barrier, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    // the shared-memory plan differs between problems (stages, search direction),
+    // so the kernel's dynamic shared-memory limit is set for this launch
+    e = cudaFuncSetAttribute(pcg_fn(P), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     Prob Pc = P;
     void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit, (void *)&forcing};

@@ -132,6 +132,7 @@ def load():
             "mba_status_string": (C.c_char_p, [C.c_int]),
             "mba_last_error": (C.c_char_p, []),
             "mba_set_device_memory_limit": (C.c_int, [C.c_size_t]),
+            "mba_set_fixed": (C.c_int, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -357,6 +358,15 @@ def mba_cost_noalloc(d_cameras, nc, d_points, np_, d_observations, d_cam_idx, d_
                                    lb, float(huber_delta), C.c_void_p(d_cost), _stream_handle(stream)))
 
 
+def mba_set_fixed(h, cam_fixed=None, pt_fixed=None):
+    """Mark cameras / points constant (boolean masks of nc / np entries; None = none fixed)."""
+    info = mba_problem_info(h)
+    cf = None if cam_fixed is None else np.ascontiguousarray(cam_fixed, dtype=np.uint8).reshape(info["nc"])
+    pf = None if pt_fixed is None else np.ascontiguousarray(pt_fixed, dtype=np.uint8).reshape(info["np"])
+    f = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(load().mba_set_fixed(h, f(cf), f(pf)))
+
+
 def mba_set_device_memory_limit(nbytes: int) -> None:
     """Cap the device memory one creation may allocate (0 = no cap); creations
     over the cap fail with MBA_ERR_OOM before allocating."""
@@ -403,6 +413,9 @@ class Problem:
 
     def reset(self):
         mba_reset(self.handle)
+
+    def set_fixed(self, cam_fixed=None, pt_fixed=None):
+        mba_set_fixed(self.handle, cam_fixed, pt_fixed)
 
     def ordering(self):
         return mba_get_ordering(self.handle)
@@ -629,16 +642,24 @@ class Graph:
 
     def __init__(self):
         self._cams, self._pts, self._obs, self._ci, self._pi = [], [], [], [], []
+        self._cfix, self._pfix = [], []
 
-    def add_camera(self, params) -> int:
-        """9 parameters: angle-axis w (3), t (3), f, k1, k2."""
+    def add_camera(self, params, fixed: bool = False) -> int:
+        """9 parameters: angle-axis w (3), t (3), f, k1, k2; fixed=True holds the camera constant."""
         p = np.asarray(params, dtype=np.float64).reshape(9)
         self._cams.append(p)
+        self._cfix.append(bool(fixed))
         return len(self._cams) - 1
 
-    def add_point(self, xyz) -> int:
+    def add_point(self, xyz, fixed: bool = False) -> int:
+        """3-D point; fixed=True holds it constant."""
         self._pts.append(np.asarray(xyz, dtype=np.float64).reshape(3))
+        self._pfix.append(bool(fixed))
         return len(self._pts) - 1
+
+    def fixed_masks(self):
+        """(camera mask, point mask) of the nodes declared fixed."""
+        return np.array(self._cfix, dtype=bool), np.array(self._pfix, dtype=bool)
 
     def add_edge(self, camera: int, point: int, uv) -> int:
         """Observation uv of point `point` in camera `camera` (residual pi(c, X) - uv)."""
@@ -655,8 +676,13 @@ class Graph:
                 np.array(self._obs).reshape(-1, 2), np.array(self._ci, np.int32), np.array(self._pi, np.int32))
 
     def problem(self, **opts) -> "Problem":
-        """A device problem (mba_problem_create) of this graph; opts as Problem's."""
-        return Problem(*self.arrays(), **opts)
+        """A device problem (mba_problem_create) of this graph, with its fixed
+        nodes marked (mba_set_fixed); opts as Problem's."""
+        pr = Problem(*self.arrays(), **opts)
+        cf, pf = self.fixed_masks()
+        if cf.any() or pf.any():
+            pr.set_fixed(cf, pf)
+        return pr
 
     @classmethod
     def from_bal(cls, path) -> "Graph":
@@ -664,6 +690,7 @@ class Graph:
         cams, pts, obs, ci, pi = mba_bal_read(path)
         g._cams, g._pts, g._obs = list(cams), list(pts), list(obs)
         g._ci, g._pi = [int(i) for i in ci], [int(i) for i in pi]
+        g._cfix, g._pfix = [False] * len(g._cams), [False] * len(g._pts)
         return g
 
     def to_bal(self, path):
