@@ -6,6 +6,14 @@ Workload: the Venice-1778-shaped synthetic problem (1,700 cameras, 1M points,
 (the device-side reset of the parameters is inside the step).  The headline
 value is the FP32-mixed form; the plain FP64 form is measured beside it.
 
+Beside the headline the line carries the FP64 form, the solver variants (the
+float-float accept/reject cost among them), the dual-number Jacobians, the
+differentiable-layer and batched-window workloads, and the Final-13682-shaped
+problem (13,000 cameras, 4.5M points, 29M observations, Huber, 30 LM iterations)
+in both forms.  The CPU-baseline leg times the oracle on a bounded sample (the
+workload's first two LM iterations, and one iteration of a 0.1-scale sample on
+one thread) and compares the GPU's first two iterations with the oracle's.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead (bounded sample: one LM iteration per step).
 Multi-GPU runs (torchrun) are independent replicas: the method's single-GPU
@@ -120,7 +128,7 @@ def batch_flops(ws, summaries, schur: str) -> float:
 # and FP64.  Traffic grows with the observation count, so a launch moves this
 # many bytes per observation per pass; None once the kernel has changed since
 # the capture.
-PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9394786048 + 97457664) / 31 / 5004484, 8: (63629832448 + 3470636288) / 31 / 5004484}
+PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9407.0e6 + 103.7e6) / 31 / 5004484, 8: (63436.1e6 + 3459.4e6) / 31 / 5004484}
 
 
 def oracle_sample_time(threads: int, scale: float) -> dict:

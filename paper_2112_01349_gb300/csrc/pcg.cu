@@ -1292,7 +1292,9 @@ __device__ __forceinline__ double sum_parts(const double *parts, int n, double *
 // ---------------------------------------------------------------------------
 // JS: the camera pass reads the stored camera-major Jacobian (always in FP64;
 // in FP32-mixed when the Jacobian comes from dual numbers).
-template <typename T, bool JS>
+// STG: the staged point pass (factored form only, a separate instantiation so
+// that its code does not weigh on the direct pass's registers).
+template <typename T, bool JS, bool STG>
 __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin, int forcing) {
     using T2 = typename V2<T>::type;
@@ -1324,12 +1326,12 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     // drain that waits for copies still in flight before the CTA leaves
     __shared__ __align__(8) uint64_t s_full[kMaxStages], s_empty[kMaxStages];
     __shared__ StageOrg s_org[kMaxStages];
-    const int S = FACT ? P.pcg_stages : 0;
+    const int S = (FACT && STG) ? P.pcg_stages : 0;
     const uint32_t Su = S > 0 ? (uint32_t)S : 1u;
     unsigned char *stages = smem_raw + P.pcg_stage_off;
     const int my_nt = (S && P.n_tiles > (int)blockIdx.x) ? (P.n_tiles - 1 - (int)blockIdx.x) / G + 1 : 0;
     uint32_t use = 0, issued = 0;
-    if (S) {
+    if (STG && S) {
         if (threadIdx.x == 0) {
             for (int i = 0; i < S; ++i) {
                 mbar_init(s_full + i, 1);
@@ -1342,7 +1344,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     // the producer warp's first lane waits for the copies it issued beyond the
     // last consumed use before the CTA leaves
     auto drain = [&]() {
-        if (S && threadIdx.x == (unsigned)(nwarp - 1) * 32)
+        if (STG && S && threadIdx.x == (unsigned)(nwarp - 1) * 32)
             for (uint32_t u = use; u < issued; ++u)
                 if (!mbar_wait(s_full + u % Su, (u / Su) & 1u, kStageSpin)) {
                     atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
@@ -1350,9 +1352,11 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                 }
     };
     auto point_pass_iter = [&]() -> bool {
-        if (FACT && S)
-            return point_pass_fact_staged(P, (const float *)ps, (const float *)pT, (float2 *)sbuf, stages, s_full,
-                                          s_empty, s_org, S, my_nt, use, issued);
+        if constexpr (FACT && STG) {
+            if (S)
+                return point_pass_fact_staged(P, (const float *)ps, (const float *)pT, (float2 *)sbuf, stages,
+                                              s_full, s_empty, s_org, S, my_nt, use, issued);
+        }
         point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
         return true;
     };
@@ -1739,15 +1743,17 @@ void plan_pcg_smem(Prob &P) {
     const int64_t psb = (((int64_t)P.nc * per_cam * w) + 127) & ~(int64_t)127;
     P.pcg_use_ps = (psb + slots <= budget) ? 1 : 0;
     P.pcg_ps_bytes = P.pcg_use_ps ? (int)psb : 0;
-    // the staged point pass of the factored form: as many stages (3..kMaxStages)
-    // as fit beside the rest, else none.  With two stages the next tile's copy is
-    // not covered by one tile of work and the pass runs slower than the direct
-    // one (Venice-shaped problem: 134 against 109 us per PCG iteration)
+    // the staged point pass of the factored form, when the camera rows do not fit
+    // in shared memory (their gather from L2 then sits on the direct pass's
+    // critical path), with as many stages (2..kMaxStages) as fit.  Where the rows
+    // fit, the direct pass is faster (Venice-shaped problem: 109 us per PCG
+    // iteration against 134 with two stages and 152 with three stages and the
+    // rows in L2); Final-shaped: 1,321 against 1,428 us with two stages
     const int64_t base = ((P.pcg_ps_bytes + slots) + 127) & ~(int64_t)127;
     const bool ranges_ok = 6 * (int64_t)P.np + 64 < (int64_t)INT32_MAX && (int64_t)P.n + 64 < (int64_t)INT32_MAX;
-    int64_t stages = P.fact && P.n_tiles > 0 && ranges_ok ? (budget - base) / kStageBytes : 0;
+    int64_t stages = P.fact && !P.pcg_use_ps && P.n_tiles > 0 && ranges_ok ? (budget - base) / kStageBytes : 0;
     if (stages > kMaxStages) stages = kMaxStages;
-    if (stages < 3) stages = 0;
+    if (stages < 2) stages = 0;
     P.pcg_stages = (int)stages;
     P.pcg_stage_off = (int)base;
     P.pcg_smem = stages ? (int)(base + stages * kStageBytes) : (int)(P.pcg_ps_bytes + slots);
@@ -1756,8 +1762,9 @@ void plan_pcg_smem(Prob &P) {
 int pcg_block(const Prob &P) { return P.fp32 ? PcgBlock<float>::value : PcgBlock<double>::value; }
 
 static const void *pcg_fn(const Prob &P) {
-    if (!P.fp32) return (const void *)pcg_kernel<double, true>;
-    return P.autodiff ? (const void *)pcg_kernel<float, true> : (const void *)pcg_kernel<float, false>;
+    if (!P.fp32) return (const void *)pcg_kernel<double, true, false>;
+    if (P.autodiff) return (const void *)pcg_kernel<float, true, false>;
+    return P.pcg_stages ? (const void *)pcg_kernel<float, false, true> : (const void *)pcg_kernel<float, false, false>;
 }
 
 // One CTA per SM (the camera partition is built for exactly that many);

@@ -34,6 +34,8 @@ def _scene(kind):
         return config_scene(1)
     if kind == "longtrack":  # heavy-tailed tracks up to 300 observations
         return make_scene(320, 3000, track=("lognormal", 6.5, 300), sigma=1.0, seed=24)
+    if kind == "manycams":  # camera rows too large for shared memory: the staged FP32 point pass
+        return make_scene(5000, 20000, track=("lognormal", 6.5, 300), sigma=1.0, seed=25)
     raise KeyError(kind)
 
 
@@ -113,8 +115,9 @@ def test_schur_matvec_fp64(mba, kind, damping):
     _colwise(y, ref, 1e-9, "Sx")
 
 
-def test_schur_matvec_fp32_mixed(mba):
-    sc = _scene("ragged")
+@pytest.mark.parametrize("kind", ["ragged", "manycams"])
+def test_schur_matvec_fp32_mixed(mba, kind):
+    sc = _scene(kind)
     mu = 1e-2
     x = np.random.default_rng(6).normal(size=(sc.nc, 9))
     with _problem(mba, sc, "fp32") as pr:
@@ -157,7 +160,7 @@ def test_fp32_mixed_solve_cost_matches_fp64(mba, kind, loss, arith, rtol):
     assert s["final_cost"] == pytest.approx(rc1, rel=rtol)
 
 
-@pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber")])
+@pytest.mark.parametrize("kind,loss", [("ragged", "none"), ("huber", "huber"), ("manycams", "none")])
 def test_step_fp32_mixed(mba, kind, loss):
     """One damped step in FP32-mixed (the factored Schur product and
     back-substitution) against the FP64 oracle: camera and point steps and the
@@ -195,14 +198,28 @@ def test_solve_fp64_final_cost(mba, kind, loss, iters, pcg):
     assert rc == pytest.approx(s["final_cost"], rel=1e-12)
 
 
-@pytest.mark.parametrize("kind,loss", [("cfg1", "none"), ("huber", "huber")])
-def test_solve_fp32_mixed_final_cost(mba, kind, loss):
+@pytest.mark.parametrize("kind,loss,iters", [("cfg1", "none", 10), ("huber", "huber", 10), ("manycams", "none", 5)])
+def test_solve_fp32_mixed_final_cost(mba, kind, loss, iters):
     sc = _scene(kind)
-    ref = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=10, pcg_max=50,
+    ref = oracle.lm_solve(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, max_iter=iters, pcg_max=50,
                           loss=loss, delta=2.0)
     with _problem(mba, sc, "fp32", loss=loss, delta=2.0) as pr:
-        s = pr.solve(max_iter=10, pcg_max_iter=50)
+        s = pr.solve(max_iter=iters, pcg_max_iter=50)
     assert s["final_cost"] == pytest.approx(ref["final_cost"], rel=1e-4)
+
+
+def test_staged_point_pass_repeats_bit_for_bit(mba):
+    """The staged FP32 point pass (camera rows too large for shared memory, so
+    tiles are copied into shared-memory stages while warps drift across them)
+    gives the same bits on every run: each chunk's sums do not depend on which
+    warp or stage took it."""
+    sc = _scene("manycams")
+    mu = 1e-2
+    with _problem(mba, sc, "fp32") as pr:
+        a = pr.step(mu, pcg_max_iter=15, pcg_rel_tol=0.0)
+        b = pr.step(mu, pcg_max_iter=15, pcg_rel_tol=0.0)
+    np.testing.assert_array_equal(a["dc"], b["dc"])
+    np.testing.assert_array_equal(a["dp"], b["dp"])
 
 
 def test_degenerate_minimal_problem(mba):
