@@ -796,38 +796,20 @@ __device__ void stage_issue(const Prob &P, unsigned char *stages, uint64_t *full
     bulk_g2s(dst, src, bytes, bar);
 }
 
-// One warp chunk of a stage (at most 32 observations), as point_pass_fact with
-// every per-observation and per-point input read from the stage.
-__device__ __forceinline__ void staged_chunk(const float *ps, const float *pT, float2 *sbuf, const float *st,
-                                             const StageOrg &o, int k) {
+// The arithmetic of one warp chunk (at most 32 observations) once its inputs
+// are in registers: t = Jc p from the camera row, u = (W Jp)^T t, the
+// segmented scan by point, b = C~^-1 u at each point's last lane, and
+// s = (W Jp) b written to the camera-major position so.
+__device__ __forceinline__ void chunk_tail(const float *ps, const float *pT, float2 *sbuf, bool act, int m, int pt,
+                                           int cam, int so, const float *jh, const float *ci, float px, float py,
+                                           float iz) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const int *s_cam = (const int *)st, *s_so = (const int *)(st + kStwSo);
-    const float *s_jh = st + kStwJh, *s_px = st + kStwPx, *s_ci = st + kStwCinv;
-    const int *s_ptp = (const int *)(st + kStwPtp);
-    const int2 *s_wch = (const int2 *)(st + kStwWch);
-    const int2 c0 = s_wch[k - o.wa], c1 = s_wch[k + 1 - o.wa];
-    const int o0 = c0.y, m = c1.y - c0.y;  // at most 32: longer tracks are not in tiles
-    const bool act = lane < m;
-    const int li = o0 - o.oa + (act ? lane : 0);
-    const int npts = c1.x - c0.x;
-    const int rs = lane < npts ? s_ptp[c0.x + lane - o.pa] - o0 : 32;
-    const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
-    const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
-    float jh[6], ci[6], u[3] = {0.f, 0.f, 0.f};
-    int so = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) jh[q] = ci[q] = 0.f;
+    float u[3] = {0.f, 0.f, 0.f};
     if (act) {
-        so = s_so[li];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) jh[q] = s_jh[q * kTileRow + li];
-        // C~^-1 of the point, from the stage (plain shared-memory loads)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) ci[q] = s_ci[6 * pt - o.ca + q];
         float r[kRow], t[2];
-        gather_row(ps, pT, s_cam[li], r);
-        fact_jc_v(s_px[li], s_px[kTileRow + li], s_px[2 * kTileRow + li], r, t);
+        gather_row(ps, pT, cam, r);
+        fact_jc_v(px, py, iz, r, t);
         u[0] = jh[0] * t[0] + jh[3] * t[1];
         u[1] = jh[1] * t[0] + jh[4] * t[1];
         u[2] = jh[2] * t[0] + jh[5] * t[1];
@@ -855,6 +837,43 @@ __device__ __forceinline__ void staged_chunk(const float *ps, const float *pT, f
     b[1] = __shfl_sync(full, bt[1], src);
     b[2] = __shfl_sync(full, bt[2], src);
     if (act) store_s<float>(sbuf, so, jh, b);
+}
+
+// One warp chunk of a stage (at most 32 observations), as point_pass_fact with
+// every per-observation and per-point input read from the stage.
+__device__ __forceinline__ void staged_chunk(const float *ps, const float *pT, float2 *sbuf, const float *st,
+                                             const StageOrg &o, int k) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int *s_cam = (const int *)st, *s_so = (const int *)(st + kStwSo);
+    const float *s_jh = st + kStwJh, *s_px = st + kStwPx, *s_ci = st + kStwCinv;
+    const int *s_ptp = (const int *)(st + kStwPtp);
+    const int2 *s_wch = (const int2 *)(st + kStwWch);
+    const int2 c0 = s_wch[k - o.wa], c1 = s_wch[k + 1 - o.wa];
+    const int o0 = c0.y, m = c1.y - c0.y;  // at most 32: longer tracks are not in tiles
+    const bool act = lane < m;
+    const int li = o0 - o.oa + (act ? lane : 0);
+    const int npts = c1.x - c0.x;
+    const int rs = lane < npts ? s_ptp[c0.x + lane - o.pa] - o0 : 32;
+    const unsigned starts = __reduce_or_sync(full, rs < 32 ? (1u << rs) : 0u);
+    const int pt = act ? c0.x + __popc(starts & (0xffffffffu >> (31 - lane))) - 1 : -1 - lane;
+    float jh[6], ci[6], px = 0.f, py = 0.f, iz = 0.f;
+    int so = 0, cam = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) jh[q] = ci[q] = 0.f;
+    if (act) {
+        so = s_so[li];
+        cam = s_cam[li];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) jh[q] = s_jh[q * kTileRow + li];
+        // C~^-1 of the point, from the stage (plain shared-memory loads)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ci[q] = s_ci[6 * pt - o.ca + q];
+        px = s_px[li];
+        py = s_px[kTileRow + li];
+        iz = s_px[2 * kTileRow + li];
+    }
+    chunk_tail(ps, pT, sbuf, act, m, pt, cam, so, jh, ci, px, py, iz);
 }
 
 // The staged pass.  `base` counts the uses consumed before this pass (the same
@@ -1747,8 +1766,9 @@ void plan_pcg_smem(Prob &P) {
     // in shared memory (their gather from L2 then sits on the direct pass's
     // critical path), with as many stages (2..kMaxStages) as fit.  Where the rows
     // fit, the direct pass is faster (Venice-shaped problem: 109 us per PCG
-    // iteration against 134 with two stages and 152 with three stages and the
-    // rows in L2); Final-shaped: 1,321 against 1,428 us with two stages
+    // iteration against 134 with two stages, 152 with three stages and the rows
+    // in L2, and 147 with a per-warp cp.async prefetch of the next chunk);
+    // Final-shaped: 1,215 against 1,428 us with two stages
     const int64_t base = ((P.pcg_ps_bytes + slots) + 127) & ~(int64_t)127;
     const bool ranges_ok = 6 * (int64_t)P.np + 64 < (int64_t)INT32_MAX && (int64_t)P.n + 64 < (int64_t)INT32_MAX;
     int64_t stages = P.fact && !P.pcg_use_ps && P.n_tiles > 0 && ranges_ok ? (budget - base) / kStageBytes : 0;
