@@ -1768,7 +1768,7 @@ void plan_pcg_smem(Prob &P) {
     // fit, the direct pass is faster (Venice-shaped problem: 109 us per PCG
     // iteration against 134 with two stages, 152 with three stages and the rows
     // in L2, and 147 with a per-warp cp.async prefetch of the next chunk);
-    // Final-shaped: 1,318 against 1,428 us with two stages
+    // Final-shaped: 1,318 against 1,475 us with two stages
     const int64_t base = ((P.pcg_ps_bytes + slots) + 127) & ~(int64_t)127;
     const bool ranges_ok = 6 * (int64_t)P.np + 64 < (int64_t)INT32_MAX && (int64_t)P.n + 64 < (int64_t)INT32_MAX;
     int64_t stages = P.fact && !P.pcg_use_ps && P.n_tiles > 0 && ranges_ok ? (budget - base) / kStageBytes : 0;
