@@ -280,10 +280,11 @@ def run_reference(args, rank, world):
     return 0
 
 
-def profile_case(precision: str, scale: float) -> int:
+def profile_case(precision: str, scale: float, config: int = CONFIG) -> int:
     """A small solve for ncu captures: the workload scaled by `scale` (0.3 gives
     1.5M observations, a Jacobian stream larger than L2), 2 LM iterations with
-    PCG <= 30, so one capture holds a bounded number of PCG launches."""
+    PCG <= 30, so one capture holds a bounded number of PCG launches.  config 3
+    is the Final-shaped problem (Huber, delta 2 px)."""
     import torch
 
     from paper_2112_01349_gb300 import _build, mba
@@ -291,10 +292,12 @@ def profile_case(precision: str, scale: float) -> int:
 
     torch.cuda.set_device(0)
     _build.build()
-    sc = config_scene(CONFIG, scale=scale)
-    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision) as pr:
+    sc = config_scene(config, scale=scale)
+    loss = "huber" if config == 3 else "none"
+    with mba.Problem(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, precision=precision, loss=loss,
+                     huber_delta=2.0) as pr:
         s = pr.solve(max_iter=2, pcg_max_iter=30, collect_timing=1)
-    print(json.dumps({"profile_case": precision, "scale": scale, "nc": sc.nc, "np": sc.np_, "n": sc.n,
+    print(json.dumps({"profile_case": precision, "config": config, "scale": scale, "nc": sc.nc, "np": sc.np_, "n": sc.n,
                       "pcg_iters_total": s["pcg_iters_total"], "final_cost": s["final_cost"]}))
     return 0
 
@@ -338,12 +341,14 @@ def main():
                     help="profiling aid: run one small solve of the workload (see --scale, --windows) and exit; "
                          "prints no bench line")
     ap.add_argument("--scale", type=float, default=0.3, help="camera/point scale of --profile-case fp32/fp64")
+    ap.add_argument("--config", type=int, default=CONFIG, choices=[2, 3],
+                    help="workload of --profile-case fp32/fp64: 2 Venice-shaped, 3 Final-shaped")
     ap.add_argument("--windows", type=int, default=128, help="windows of --profile-case batch")
     args = ap.parse_args()
     if args.profile_case == "batch":
         return profile_batch(args.windows)
     if args.profile_case:
-        return profile_case(args.profile_case, args.scale)
+        return profile_case(args.profile_case, args.scale, args.config)
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local, dist = dist_setup(args.gpus)

@@ -261,8 +261,10 @@ __global__ void __launch_bounds__(kBlock, 4) lin_point_kernel(Prob P, int force)
 // One warp per camera chunk: each lane accumulates the 54 block terms of its
 // observations, then one shuffle tree per chunk (a CTA-wide reduction per
 // chunk of a few hundred observations cost as much as the Jacobians).
+// The FP32 instance is held to two CTAs per SM (128 registers); the FP64 one is
+// bound by the FP64 pipe and keeps its registers.
 template <typename T, bool AD>
-__global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) lin_camera_kernel(Prob P, int force) {
     if (!force && (P.st->done || !P.st->relin)) return;
     __shared__ T ctabs[kWarps][kCamTab];
     const T *__restrict__ camtab = (const T *)P.camtab;
@@ -278,11 +280,27 @@ __global__ void __launch_bounds__(kBlock) lin_camera_kernel(Prob P, int force) {
         T acc[54];
 #pragma unroll
         for (int q = 0; q < 54; ++q) acc[q] = T(0);
-        for (int s = b0 + lane; s < b1; s += 32) {
-            const int pt = P.cm_pt[s];
-            T X0, X1, X2, u0, u1;
-            load_point<T>(P, pt, X0, X1, X2);
-            load_uv<T>(P.cm_uv, P.cm_uv32, s, u0, u1);
+        // two-deep pipeline over this lane's observations (the point index two
+        // ahead, the point and pixels one ahead), so that the dependent point
+        // gather is in flight while the previous observation is worked
+        int s = b0 + lane;
+        int pa = s < b1 ? P.cm_pt[s] : 0;
+        int pb = s + 32 < b1 ? P.cm_pt[s + 32] : 0;
+        T Xa0 = T(0), Xa1 = T(0), Xa2 = T(0), ua0 = T(0), ua1 = T(0);
+        if (s < b1) {
+            load_point<T>(P, pa, Xa0, Xa1, Xa2);
+            load_uv<T>(P.cm_uv, P.cm_uv32, s, ua0, ua1);
+        }
+        for (; s < b1; s += 32) {
+            const int pt = pa;
+            const T X0 = Xa0, X1 = Xa1, X2 = Xa2, u0 = ua0, u1 = ua1;
+            const int pc = s + 64 < b1 ? P.cm_pt[s + 64] : 0;
+            if (s + 32 < b1) {
+                load_point<T>(P, pb, Xa0, Xa1, Xa2);
+                load_uv<T>(P.cm_uv, P.cm_uv32, s + 32, ua0, ua1);
+            }
+            pa = pb;
+            pb = pc;
             T e[2], Jc[18], Jp[6], pz[3];
             edge_eval<T, AD, true, false>(ctab, X0, X1, X2, u0, u1, e, Jc, Jp, (sizeof(T) == 4 && !AD) ? pz : nullptr);
             zero_fixed_columns<T>(P, cam, pt, Jc, (T *)nullptr);
