@@ -26,6 +26,7 @@ LOSS = {"none": 0, "huber": 1}
 DAMPING = {"diag": 0, "identity": 1}
 SCHUR = {"implicit_pcg": 0, "explicit_pcg": 1, "dense": 2}
 PRECOND = {"block_jacobi": 0, "schur_jacobi": 1}
+PCG_VARIANT = {"standard": 0, "single_reduction": 1}
 
 
 def build(force: bool = False) -> str:
@@ -63,13 +64,14 @@ def _load():
             lib.orc_stable_sort.argtypes = [i64, P, i32, P, P]
             lib.orc_blocks.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, P, P, P, P, P]
             lib.orc_step.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, C.c_int,
-                                     C.c_int, dbl, P, P, P, P, P, C.c_int, P, P]
+                                     C.c_int, dbl, P, P, P, P, P, C.c_int, P, P, C.c_int]
             lib.orc_schur_jacobi_blocks.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, P]
             lib.orc_schur.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, P, P, P, P]
             lib.orc_lm_solve.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, C.c_int, C.c_int, dbl,
-                                         C.c_int, dbl, dbl, dbl, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P]
+                                         C.c_int, dbl, dbl, dbl, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P,
+                                         C.c_int]
             lib.orc_adjoint.argtypes = [i32, i32, i64, P, P, P, P, P, C.c_int, dbl, dbl, C.c_int, C.c_int, dbl, P, P,
-                                        P, P, P, P, C.c_int]
+                                        P, P, P, P, C.c_int, C.c_int]
             lib.orc_num_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -170,16 +172,19 @@ def _fixed(mask, m):
 
 
 def step(cams, pts, obs, cam_idx, pt_idx, mu, loss="none", delta=0.0, damping="diag", schur="implicit_pcg",
-         pcg_max=100, pcg_tol=1e-10, precond="block_jacobi", cam_fixed=None, pt_fixed=None):
+         pcg_max=100, pcg_tol=1e-10, precond="block_jacobi", cam_fixed=None, pt_fixed=None,
+         pcg_variant="standard"):
     """One damped Schur step: dict(dc (nc,9), dp (np,3), pcg_iters, rel_res, model_dec).
-    cam_fixed / pt_fixed: optional masks of nodes held constant."""
+    cam_fixed / pt_fixed: optional masks of nodes held constant; pcg_variant:
+    "standard" (Alg. 2) or "single_reduction" (Chronopoulos-Gear form)."""
     cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
     cf, pf = _fixed(cam_fixed, nc), _fixed(pt_fixed, np_)
     dc, dp = np.zeros((nc, 9)), np.zeros((np_, 3))
     it, rr, md = C.c_int(), C.c_double(), C.c_double()
     rc = _load().orc_step(nc, np_, n, _p(cams), _p(pts), _p(obs), _p(ci), _p(pi), LOSS[loss], float(delta),
                           float(mu), DAMPING[damping], SCHUR[schur], int(pcg_max), float(pcg_tol), _p(dc), _p(dp),
-                          C.byref(it), C.byref(rr), C.byref(md), PRECOND[precond], _p(cf), _p(pf))
+                          C.byref(it), C.byref(rr), C.byref(md), PRECOND[precond], _p(cf), _p(pf),
+                          PCG_VARIANT[pcg_variant])
     if rc:
         raise RuntimeError(f"orc_step failed: {rc}")
     return dict(dc=dc, dp=dp, pcg_iters=it.value, rel_res=rr.value, model_dec=md.value)
@@ -212,7 +217,7 @@ def schur(cams, pts, obs, cam_idx, pt_idx, mu, x=None, loss="none", delta=0.0, d
 
 def lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=10, pcg_max=50, pcg_tol=1e-10, loss="none", delta=0.0,
              damping="diag", initial_radius=1e4, min_rel_dec=1e-3, function_tol=0.0, schur="implicit_pcg",
-             precond="block_jacobi", forcing=False, cam_fixed=None, pt_fixed=None):
+             precond="block_jacobi", forcing=False, cam_fixed=None, pt_fixed=None, pcg_variant="standard"):
     """Run the LM loop; returns dict(cameras, points, trace (list of dict), iterations, final_cost, radius).
     cam_fixed / pt_fixed: optional masks of nodes held constant."""
     cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
@@ -224,7 +229,7 @@ def lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=10, pcg_max=50, pcg_tol=1
                               int(max_iter), int(pcg_max), float(pcg_tol), DAMPING[damping], float(initial_radius),
                               float(min_rel_dec), float(function_tol), SCHUR[schur], C.cast(tr, C.c_void_p),
                               C.byref(it), C.byref(fc), C.byref(rad), PRECOND[precond], 1 if forcing else 0,
-                              _p(cf), _p(pf))
+                              _p(cf), _p(pf), PCG_VARIANT[pcg_variant])
     if rc:
         raise RuntimeError(f"orc_lm_solve failed: {rc}")
     trace = [{f: getattr(tr[i], f) for f, _ in Trace._fields_} for i in range(it.value)]
@@ -232,7 +237,7 @@ def lm_solve(cams, pts, obs, cam_idx, pt_idx, max_iter=10, pcg_max=50, pcg_tol=1
 
 
 def adjoint(cams, pts, obs, cam_idx, pt_idx, mu, gbar_c, gbar_p, loss="none", delta=0.0, damping="diag",
-            pcg_max=500, pcg_tol=1e-14, precond="block_jacobi"):
+            pcg_max=500, pcg_tol=1e-14, precond="block_jacobi", pcg_variant="standard"):
     """dict(grad_obs (n,2), grad_c0 (nc,9), grad_p0 (np,3), pcg_iters) for upstream gradient (gbar_c, gbar_p)."""
     cams, pts, obs, ci, pi, nc, np_, n = _prob(cams, pts, obs, cam_idx, pt_idx)
     gc, gp = _f64(gbar_c, (nc, 9)), _f64(gbar_p, (np_, 3))
@@ -240,7 +245,7 @@ def adjoint(cams, pts, obs, cam_idx, pt_idx, mu, gbar_c, gbar_p, loss="none", de
     it = C.c_int()
     rc = _load().orc_adjoint(nc, np_, n, _p(cams), _p(pts), _p(obs), _p(ci), _p(pi), LOSS[loss], float(delta),
                              float(mu), DAMPING[damping], int(pcg_max), float(pcg_tol), _p(gc), _p(gp), _p(go),
-                             _p(gc0), _p(gp0), C.byref(it), PRECOND[precond])
+                             _p(gc0), _p(gp0), C.byref(it), PRECOND[precond], PCG_VARIANT[pcg_variant])
     if rc:
         raise RuntimeError(f"orc_adjoint failed: {rc}")
     return dict(grad_obs=go, grad_c0=gc0, grad_p0=gp0, pcg_iters=it.value)

@@ -653,6 +653,71 @@ static int pcg(const lin_t *L, const damped_t *D, const double *Sd, const double
     return n;
 }
 
+/* Single-reduction form of the same PCG (a solver variant, off by default):
+ * A. T. Chronopoulos and C. W. Gear, "s-step iterative methods for symmetric
+ * linear systems", J. Comput. Appl. Math. 25 (1989), the one-step method with
+ * a preconditioner.  Each step forms u = M^-1 r and w = S u, then takes the
+ * three inner products gamma = r.u, delta = w.u and r.r together, which a
+ * parallel implementation gathers in one global reduction instead of two:
+ *   beta  = gamma / gamma_prev               (0 on the first step)
+ *   alpha = gamma / (delta - beta gamma / alpha_prev)   (gamma / delta first)
+ *   p = u + beta p,  s = w + beta s          (so s = S p),
+ *   x += alpha p,    r -= alpha s.
+ * The denominator of alpha equals p.S p in exact arithmetic (expand p.S p with
+ * p = u + beta p_prev, use r.u_prev = 0 and p_prev.S p_prev =
+ * gamma_prev / alpha_prev), so the iterates are those of pcg() above; only
+ * the rounding differs.  Start, stopping test and breakdown rules as there:
+ * stop, keeping x, if gamma is not finite or the denominator is not positive. */
+static int pcg_single_reduction(const lin_t *L, const damped_t *D, const double *Sd, const double *g, double *x,
+                                int max_iter, double tol, double *rel_res) {
+    const int64_t m = 9 * (int64_t)L->nc;
+    double *r = malloc(sizeof(double) * m), *u = malloc(sizeof(double) * m), *w = malloc(sizeof(double) * m),
+           *p = malloc(sizeof(double) * m), *sv = malloc(sizeof(double) * m);
+    double *sa = malloc(sizeof(double) * 3 * (size_t)L->np), *sb = malloc(sizeof(double) * 3 * (size_t)L->np);
+    int n = 0;
+    memset(x, 0, sizeof(double) * m);
+    memcpy(r, g, sizeof(double) * m);
+    double r0 = sqrt(vdot(r, r, m)), rn = r0, gamma_prev = 0.0, alpha_prev = 0.0;
+    if (r0 > 0.0) {
+        for (;;) {
+            for (int32_t i = 0; i < L->nc; ++i) chol_solve(D->Lb + 81 * (int64_t)i, 9, r + 9 * (int64_t)i, u + 9 * (int64_t)i);
+            if (Sd) {
+                for (int64_t a = 0; a < m; ++a) w[a] = vdot(Sd + a * m, u, m);
+            } else {
+                schur_matvec(L, D, u, w, sa, sb);
+            }
+            const double gamma = vdot(r, u, m), delta = vdot(w, u, m);
+            if (!isfinite(gamma)) break;
+            const double beta = n == 0 ? 0.0 : gamma / gamma_prev;
+            const double den = n == 0 ? delta : delta - beta * gamma / alpha_prev;
+            if (!(den > 0.0) || !isfinite(den)) break;
+            const double alpha = gamma / den;
+            for (int64_t t = 0; t < m; ++t) {
+                p[t] = n == 0 ? u[t] : u[t] + beta * p[t];
+                sv[t] = n == 0 ? w[t] : w[t] + beta * sv[t];
+                x[t] += alpha * p[t];
+                r[t] -= alpha * sv[t];
+            }
+            ++n;
+            gamma_prev = gamma;
+            alpha_prev = alpha;
+            rn = sqrt(vdot(r, r, m));
+            if (rn <= tol * r0 || n >= max_iter) break;
+        }
+    }
+    if (rel_res) *rel_res = r0 > 0.0 ? rn / r0 : 0.0;
+    free(r); free(u); free(w); free(p); free(sv); free(sa); free(sb);
+    return n;
+}
+
+/* The PCG of a damped solve: variant 0 the two-reduction loop of Alg. 2,
+ * 1 the single-reduction form. */
+static int pcg_any(int variant, const lin_t *L, const damped_t *D, const double *Sd, const double *g, double *x,
+                   int max_iter, double tol, double *rel_res) {
+    return variant == 1 ? pcg_single_reduction(L, D, Sd, g, x, max_iter, tol, rel_res)
+                        : pcg(L, D, Sd, g, x, max_iter, tol, rel_res);
+}
+
 /* Dense Cholesky solve of S x = g (small problems). */
 static int dense_solve(double *S, int64_t m, const double *g, double *x) {
     for (int64_t j = 0; j < m; ++j) {
@@ -727,7 +792,8 @@ static double model_decrease(const lin_t *L, const double *dc, const double *dp,
  * solve's reduced right-hand side and |g_first| that of the first solve
  * (*g0n <= 0 on entry marks the first solve; it is then set). */
 static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, int pcg_max, double pcg_tol,
-                       double *dc, double *dp, int *pcg_iters, double *rel_res, int precond, double *g0n) {
+                       double *dc, double *dp, int *pcg_iters, double *rel_res, int precond, double *g0n,
+                       int variant) {
     damped_t D;
     int rc = damp(L, mu, damping, &D);
     if (rc) return rc;
@@ -745,12 +811,12 @@ static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, i
     *pcg_iters = 0;
     if (rel_res) *rel_res = 0.0;
     if (schur_mode == 0) {
-        *pcg_iters = pcg(L, &D, NULL, g, dc, pcg_max, pcg_tol, rel_res);
+        *pcg_iters = pcg_any(variant, L, &D, NULL, g, dc, pcg_max, pcg_tol, rel_res);
     } else {
         double *S = malloc(sizeof(double) * m * m);
         if (!S) { free(g); free(sb); damped_free(&D); return ORC_ERR_OOM; }
         schur_explicit(L, &D, S);
-        if (schur_mode == 1) *pcg_iters = pcg(L, &D, S, g, dc, pcg_max, pcg_tol, rel_res);
+        if (schur_mode == 1) *pcg_iters = pcg_any(variant, L, &D, S, g, dc, pcg_max, pcg_tol, rel_res);
         else rc = dense_solve(S, m, g, dc);
         free(S);
     }
@@ -764,14 +830,15 @@ static int damped_step(const lin_t *L, double mu, int damping, int schur_mode, i
 int orc_step(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
              const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
              int schur_mode, int pcg_max, double pcg_tol, double *dc, double *dp, int *pcg_iters, double *rel_res,
-             double *model_dec, int precond, const uint8_t *cam_fixed, const uint8_t *pt_fixed) {
+             double *model_dec, int precond, const uint8_t *cam_fixed, const uint8_t *pt_fixed, int pcg_variant) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
     L.cam_fixed = cam_fixed;
     L.pt_fixed = pt_fixed;
     linearise(&L, cams, pts, obs, loss, delta);
-    rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, pcg_iters, rel_res, precond, NULL);
+    rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, pcg_iters, rel_res, precond, NULL,
+                     pcg_variant);
     if (!rc && model_dec) {
         double *scr = malloc(sizeof(double) * n);
         *model_dec = model_decrease(&L, dc, dp, scr);
@@ -834,7 +901,7 @@ int orc_schur(int32_t nc, int32_t np, int64_t n, const double *cams, const doubl
 int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const double *pts, const double *obs,
                 const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, double mu, int damping,
                 int pcg_max, double pcg_tol, const double *gbar_c, const double *gbar_p, double *grad_obs,
-                double *grad_c0, double *grad_p0, int *pcg_iters, int precond) {
+                double *grad_c0, double *grad_p0, int *pcg_iters, int precond, int pcg_variant) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
@@ -849,7 +916,7 @@ int orc_adjoint(int32_t nc, int32_t np, int64_t n, const double *cams, const dou
     memcpy(L.v, gbar_c, sizeof(double) * 9 * (size_t)nc);
     memcpy(L.w, gbar_p, sizeof(double) * 3 * (size_t)np);
     int it = 0;
-    rc = damped_step(&L, mu, damping, 0, pcg_max, pcg_tol, vc, vp, &it, NULL, precond, NULL);
+    rc = damped_step(&L, mu, damping, 0, pcg_max, pcg_tol, vc, vp, &it, NULL, precond, NULL, pcg_variant);
     if (!rc) {
         for (int64_t k = 0; k < n; ++k) {
             const double *Jc = L.Jc + 18 * k, *Jp = L.Jp + 6 * k;
@@ -892,7 +959,7 @@ int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, c
                  const int32_t *cam_idx, const int32_t *pt_idx, int loss, double delta, int max_iter, int pcg_max,
                  double pcg_tol, int damping, double initial_radius, double min_rel_dec, double function_tol,
                  int schur_mode, orc_trace_t *trace, int *iterations, double *final_cost, double *final_radius,
-                 int precond, int forcing, const uint8_t *cam_fixed, const uint8_t *pt_fixed) {
+                 int precond, int forcing, const uint8_t *cam_fixed, const uint8_t *pt_fixed, int pcg_variant) {
     lin_t L;
     int rc = lin_alloc(&L, nc, np, n, cam_idx, pt_idx);
     if (rc) return rc;
@@ -912,7 +979,7 @@ int orc_lm_solve(int32_t nc, int32_t np, int64_t n, double *cams, double *pts, c
         int pcg_iters = 0;
         double rel_res = 0.0;
         rc = damped_step(&L, mu, damping, schur_mode, pcg_max, pcg_tol, dc, dp, &pcg_iters, &rel_res, precond,
-                         forcing ? &g0n : NULL);
+                         forcing ? &g0n : NULL, pcg_variant);
         if (rc == ORC_ERR_NOT_SPD) {
             /* a damped block that is not positive definite gives no step: the
                iteration counts as rejected (mu grows, the linearisation is kept) */

@@ -498,9 +498,16 @@ def _block_inverse(A, nb):
     return Ai
 
 
+@pytest.mark.parametrize("variant", ["standard", "single_reduction"])
 @pytest.mark.parametrize("precond", ["block_jacobi", "schur_jacobi"])
 @pytest.mark.parametrize("schur", ["explicit_pcg", "implicit_pcg"])
-def test_truncated_pcg_iterate_is_the_krylov_energy_minimiser(precond, schur):
+def test_truncated_pcg_iterate_is_the_krylov_energy_minimiser(precond, schur, variant):
+    """Both PCG forms (Alg. 2's two-reduction loop and the single-reduction
+    Chronopoulos-Gear form) return, after k steps, the minimiser of the S-energy
+    error over the k-dimensional preconditioned Krylov space (Saad, Iterative
+    Methods for Sparse Linear Systems, Sec. 6.11 and 9.2): a wrong beta, a mixed
+    p / p_prev, or a wrong alpha denominator in the single-reduction recurrence
+    leaves the space or the minimum."""
     sc = make_scene(4, 25, sigma=1.0, seed=21)
     mu = 1e-3
     Hd, g, *_ = _damped_dense(sc, mu)
@@ -514,7 +521,7 @@ def test_truncated_pcg_iterate_is_the_krylov_energy_minimiser(precond, schur):
     for k in range(1, 7):
         ref = _krylov_minimiser(S, Minv, b, k)
         r = oracle.step(sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx, mu, schur=schur,
-                        pcg_max=k, pcg_tol=0.0, precond=precond)
+                        pcg_max=k, pcg_tol=0.0, precond=precond, pcg_variant=variant)
         assert r["pcg_iters"] == k
         np.testing.assert_allclose(r["dc"].reshape(-1), ref, atol=1e-9 * np.abs(ref).max(), err_msg=f"k={k}")
     # the iterates differ from step to step, so the comparison above has teeth
@@ -554,3 +561,22 @@ def test_accepted_step_radius_follows_nielsen_rule(rot_sigma, point_sigma, seed,
     assert t0["gain"] == pytest.approx(rho, rel=1e-9)
     expected_radius = radius / max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
     assert t1["mu"] == pytest.approx(1.0 / expected_radius, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# The single-reduction PCG stops where the standard one does: with a tolerance,
+# both take the same number of steps and return the same solution (rounding
+# apart), and an LM solve on either reaches the same accept decisions and
+# final cost.
+def test_single_reduction_pcg_matches_standard_with_a_tolerance():
+    sc = make_scene(12, 800, track=("geom", 0.25), sigma=1.0, seed=27)
+    args = (sc.cameras, sc.points, sc.observations, sc.cam_idx, sc.pt_idx)
+    a = oracle.step(*args, 1e-2, pcg_max=200, pcg_tol=1e-8)
+    b = oracle.step(*args, 1e-2, pcg_max=200, pcg_tol=1e-8, pcg_variant="single_reduction")
+    assert 5 < a["pcg_iters"] < 200 and a["pcg_iters"] == b["pcg_iters"]
+    np.testing.assert_allclose(b["dc"], a["dc"], rtol=0, atol=1e-9 * np.abs(a["dc"]).max())
+    assert b["rel_res"] == pytest.approx(a["rel_res"], rel=1e-6)
+    ra = oracle.lm_solve(*args, max_iter=6, pcg_max=50)
+    rb = oracle.lm_solve(*args, max_iter=6, pcg_max=50, pcg_variant="single_reduction")
+    assert [t["accepted"] for t in ra["trace"]] == [t["accepted"] for t in rb["trace"]]
+    assert rb["final_cost"] == pytest.approx(ra["final_cost"], rel=1e-10)
