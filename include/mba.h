@@ -80,6 +80,20 @@ typedef enum { MBA_JACOBIAN_ANALYTIC = 0, MBA_JACOBIAN_AUTODIFF = 1 } mba_jacobi
  * ratio sits within that of the acceptance threshold. */
 typedef enum { MBA_COST_FP64 = 0, MBA_COST_FLOAT_FLOAT = 1 } mba_cost_arithmetic;
 
+/* Recurrence of the PCG (Alg. 2).  STANDARD (default): the loop as Alg. 2 writes it,
+ * two inner-product reductions per iteration (p.q for alpha, r.z for beta).
+ * SINGLE_REDUCTION (solver variant, not in the paper): the one-step method of
+ * Chronopoulos and Gear (J. Comput. Appl. Math. 25, 1989): with u = M^-1 r and
+ * w = S u, the products r.u, w.u and r.r are taken together after the Schur product,
+ * alpha = r.u / (w.u - beta r.u / alpha_prev), and s = S p follows by the recurrence
+ * s = w + beta s.  The iterates equal the standard ones in exact arithmetic; the
+ * persistent PCG kernel then needs one global reduction per iteration instead of two,
+ * and three grid barriers per iteration where the standard loop needs three (search
+ * direction in shared memory) or four.  The iteration count and stopping test are
+ * unchanged; a solve that meets the tolerance forms one Schur product more than it
+ * uses. */
+typedef enum { MBA_PCG_STANDARD = 0, MBA_PCG_SINGLE_REDUCTION = 1 } mba_pcg_variant;
+
 typedef struct {
     int32_t precision;   /* mba_precision.  FP32_MIXED: Jacobian, Hessian blocks and the
                             PCG Schur product in FP32; block inversions, PCG dot
@@ -107,6 +121,7 @@ typedef struct {
                                       norm of its reduced right-hand side, |g_1| that of the solve's first
                                       damped step; 0: pcg_rel_tol throughout (default) */
     int32_t cost_arithmetic;       /* mba_cost_arithmetic (default FP64) */
+    int32_t pcg_variant;           /* mba_pcg_variant (default STANDARD) */
 } mba_solver_options;
 
 /* One LM iteration as recorded by mba_solve. */

@@ -102,6 +102,7 @@ void mba_solver_options_default(mba_solver_options *o) {
     o->preconditioner = MBA_PRECOND_BLOCK_JACOBI;
     o->forcing = 0;
     o->cost_arithmetic = MBA_COST_FP64;
+    o->pcg_variant = MBA_PCG_STANDARD;
 }
 
 const char *mba_status_string(mba_status s) {
@@ -472,7 +473,7 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
         mba_problem_destroy(pr);
         return fail(MBA_ERR_INVALID_ARG, "the PCG kernel does not fit one CTA per SM for this problem shape");
     }
-    if (3 * pr->pcg_grid > red_len) {
+    if (4 * pr->pcg_grid > red_len) {
         mba_problem_destroy(pr);
         return fail(MBA_ERR_INVALID_ARG, "internal: reduction buffer");
     }
@@ -522,7 +523,8 @@ bool valid_solver_opts(const mba_solver_options &o) {
            o.function_tol >= 0.0 && o.barrier_spin_limit >= 0 &&
            (o.preconditioner == MBA_PRECOND_BLOCK_JACOBI || o.preconditioner == MBA_PRECOND_SCHUR_JACOBI) &&
            (o.forcing == 0 || o.forcing == 1) &&
-           (o.cost_arithmetic == MBA_COST_FP64 || o.cost_arithmetic == MBA_COST_FLOAT_FLOAT);
+           (o.cost_arithmetic == MBA_COST_FP64 || o.cost_arithmetic == MBA_COST_FLOAT_FLOAT) &&
+           (o.pcg_variant == MBA_PCG_STANDARD || o.pcg_variant == MBA_PCG_SINGLE_REDUCTION);
 }
 
 }  // namespace
@@ -692,7 +694,7 @@ mba_status mba_step(mba_problem *pr, double mu, const mba_solver_options *opt, d
     mba_status st = prepare_step(pr, mu, o.damping, o.preconditioner);
     if (st) return st;
     const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
-    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s, 0, o.pcg_variant));
     CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
     DevState hs;
     st = check_device_state(pr, &hs);
@@ -739,7 +741,7 @@ mba_status mba_solve(mba_problem *pr, const mba_solver_options *opt, mba_summary
         CK(rec(2 + 4 * it));
         CK(launch_damp(P, o.damping, o.preconditioner, pr->cfirst, s));
         CK(rec(3 + 4 * it));
-        CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s, o.forcing));
+        CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s, o.forcing, o.pcg_variant));
         CK(rec(4 + 4 * it));
         CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));
         CK(launch_camera_tables(P, P.cams_new, false, s));
@@ -815,7 +817,7 @@ mba_status mba_adjoint(mba_problem *pr, const mba_solver_options *opt, double mu
     CK(cudaMemcpyAsync(P.v, grad_cameras, sizeof(double) * 9 * (size_t)P.nc, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(P.w, grad_points, sizeof(double) * 3 * (size_t)P.np, cudaMemcpyHostToDevice, s));
     const long long spin = o.barrier_spin_limit > 0 ? o.barrier_spin_limit : kDefaultSpin;
-    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s));
+    CK(launch_pcg(P, PCG_SOLVE, o.pcg_max_iter, o.pcg_rel_tol, spin, pr->pcg_grid, s, 0, o.pcg_variant));
     CK(launch_backsub(P, pr->part_a, pr->nb_chunk, s));  // dp = v_p
     DevState hs;
     st = check_device_state(pr, &hs);

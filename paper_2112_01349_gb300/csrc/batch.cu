@@ -63,6 +63,7 @@ struct BatchOpts {
     int32_t max_iter, pcg_max_iter, damping, adjoint, adj_pcg_max, explicit_schur;
     double pcg_tol, initial_radius, min_rel_dec, function_tol, adj_pcg_tol, adj_mu;
     int32_t precond, forcing;  // mba_preconditioner; 1: forcing sequence for the forward solves
+    int32_t pcg_variant, pad;  // mba_pcg_variant
 };
 
 struct BatchArgs {
@@ -112,7 +113,9 @@ struct V2<double> {
 template <typename T>
 struct WinMem {
     double *cams, *camn, *tab64, *Hpp, *v, *x, *r, *z, *p, *q, *slot, *sb;
+    double *sv;  // s = S~ p of the single-reduction PCG
     T *tabT, *pv, *stage, *BinvT;
+    T *rT;  // r rounded to T, the preconditioner's input (FP64: r itself)
     T *S;  // explicit S~ in shared memory (NULL: the CTA's global scratch)
     int32_t *cptr, *wf, *wl, *wcam0;
 };
@@ -145,14 +148,16 @@ __host__ __device__ inline size_t win_carve(unsigned char *base, int ncmax, int 
     m.z = (double *)take(8 * c9);
     m.p = (double *)take(8 * c9);
     m.q = (double *)take(8 * c9);
+    m.sv = (double *)take(8 * c9);
     // camera-pass slots and the Schur-build staging are never live together
     const size_t slot_b = 8 * 54 * (size_t)(nwarp + ncmax),
                  stage_b = sizeof(T) * Stage<T>::pairs * Stage<T>::stride * (size_t)nwarp;
     m.slot = (double *)take(slot_b > stage_b ? slot_b : stage_b);
     m.stage = (T *)m.slot;
-    m.sb = (double *)take(8 * (2 * 32 * (size_t)nwarp + 4));
+    m.sb = (double *)take(8 * (3 * 32 * (size_t)nwarp + 8));
     m.tabT = (T *)take(sizeof(T) * kTabS * (size_t)ncmax);
     m.pv = (T *)take(sizeof(T) * c9);
+    m.rT = sizeof(T) == 8 ? (T *)m.r : (T *)take(sizeof(T) * c9);
     m.cptr = (int32_t *)take(4 * (size_t)(ncmax + 1));
     m.wf = (int32_t *)take(4 * (size_t)ncmax);
     m.wl = (int32_t *)take(4 * (size_t)ncmax);
@@ -247,6 +252,44 @@ __device__ __forceinline__ void cta_sum2f(double a, double b, double *sb, F &&fi
             y += __shfl_xor_sync(0xffffffffu, y, o);
         }
         if (lane == 0) fin(x, y);
+    }
+    __syncthreads();
+}
+
+// Three sums with fin(x, y, z) run by thread 0 before the closing barrier
+// (the single-reduction PCG takes r.r, r.u and w.u in one pass).  sb holds
+// 3 NT values; the same fixed order as cta_sum2f.
+template <int NT, typename F>
+__device__ __forceinline__ void cta_sum3f(double a, double b, double c, double *sb, F &&fin) {
+    sb[threadIdx.x] = a;
+    sb[NT + threadIdx.x] = b;
+    sb[2 * NT + threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double xv[NT / 32], yv[NT / 32], zv[NT / 32];
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) {
+            xv[k] = sb[lane + 32 * k];
+            yv[k] = sb[NT + lane + 32 * k];
+            zv[k] = sb[2 * NT + lane + 32 * k];
+        }
+#pragma unroll
+        for (int h = NT / 64; h > 0; h >>= 1)
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                xv[k] += xv[k + h];
+                yv[k] += yv[k + h];
+                zv[k] += zv[k + h];
+            }
+        double x = xv[0], y = yv[0], z = zv[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) fin(x, y, z);
     }
     __syncthreads();
 }
@@ -886,17 +929,19 @@ __device__ __forceinline__ void make_pv(const WinMem<T> &M, const double *vec, i
 }
 
 // z = B~^-1 r per camera, with B~^-1 (inverted in FP64) applied in the
-// problem's precision T; returns (r.r, r.z) partials in FP64.
+// problem's precision T to M.rT, the T copy of r that every update of r keeps
+// (one conversion per entry instead of nine); returns (r.r, r.z) partials in
+// FP64.
 template <typename T, int NT>
 __device__ __forceinline__ double2 precond(const WinMem<T> &M, int nc) {
     double rr = 0.0, rz = 0.0;
     for (int t = threadIdx.x; t < 9 * nc; t += NT) {
         const int i = t / 9, a = t - 9 * (t / 9);
         const T *Bi = M.BinvT + 45 * i;
-        const double *ri = M.r + 9 * i;
+        const T *ri = M.rT + 9 * i;
         T zt = T(0);
 #pragma unroll
-        for (int b = 0; b < 9; ++b) zt = fma(Bi[sym9(a, b)], (T)ri[b], zt);
+        for (int b = 0; b < 9; ++b) zt = fma(Bi[sym9(a, b)], ri[b], zt);
         const double z = (double)zt;
         M.z[t] = z;
         rr = fma(M.r[t], M.r[t], rr);
@@ -1177,9 +1222,110 @@ __device__ void sj_from_s(const BatchArgs &A, const WinMem<T> &M, const WinDesc 
 // PCG of Alg. 2 on S x = g, g = vvec - E C~^-1 wvec (Sec. 3 Eq. 3), x0 = 0;
 // leaves x in M.x and returns the iteration count.  The product S p is the
 // implicit two-pass form of Alg. 3, or the explicit S~ of s_build.
+// Single-reduction form of the same PCG (mba_pcg_variant SINGLE_REDUCTION; the
+// oracle's pcg_single_reduction, after Chronopoulos and Gear): each step forms
+// u = B~^-1 r and w = S~ u, takes r.r, r.u and w.u in one block reduction, and
+// updates alpha = r.u / (w.u - beta r.u / alpha_prev), beta = r.u / (r.u)_prev,
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.  One reduction
+// per step instead of two; the test |r| <= tol |r0| is taken on the r.r of that
+// reduction, i.e. after the product of the step that would follow.  Entered
+// with r = g (and its T copy) and x = 0; returns the number of steps.
+template <typename T, int NT>
+__device__ __noinline__ int pcg_single_reduction(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, double mu,
+                                    int damping, int max_iter, double tol, bool xs, double *g0) {
+    const int m9 = 9 * d.nc;
+    double *sc = M.sb + 3 * NT + 4;  // alpha, beta (written by thread 0)
+    int *go = reinterpret_cast<int *>(M.sb + 3 * NT + 6);
+    double r0 = 0.0, stop2 = 0.0, gamma_prev = 0.0, alpha_prev = 0.0;  // meaningful in thread 0
+    int n = 0;
+    while (n == 0 || n < max_iter) {
+        // u = B~^-1 r into M.z (FP64) and, as the explicit product's input, M.pv (T)
+        double rr = 0.0, ru = 0.0;
+        for (int t = threadIdx.x; t < m9; t += NT) {
+            const int i = t / 9, a = t - 9 * (t / 9);
+            const T *Bi = M.BinvT + 45 * i;
+            const T *ri = M.rT + 9 * i;
+            T zt = T(0);
+#pragma unroll
+            for (int b = 0; b < 9; ++b) zt = fma(Bi[sym9(a, b)], ri[b], zt);
+            const double u = (double)zt;
+            M.z[t] = u;
+            if (xs) M.pv[t] = zt;
+            rr = fma(M.r[t], M.r[t], rr);
+            ru = fma(M.r[t], u, ru);
+        }
+        __syncthreads();
+        // w = S~ u into M.q, and this thread's part of w.u
+        double wu = 0.0;
+        if (xs) {
+            s_matvec<T, NT>(A, M, d);
+            for (int t = threadIdx.x; t < m9; t += NT) wu = fma(M.z[t], M.q[t], wu);
+        } else {
+            make_pv<T, NT>(M, M.z, d.nc);
+            __syncthreads();
+            iter_points<T, NT>(A, M, d);
+            __syncthreads();
+            camera_pass<T, NT, false>(A, M, d);
+            __syncthreads();
+            for (int t = threadIdx.x; t < m9; t += NT) {
+                const int i = t / 9, a = t - 9 * (t / 9);
+                const double *Hi = M.Hpp + 45 * i;
+                const double *ui = M.z + 9 * i;
+                double bu = 0.0;
+#pragma unroll
+                for (int b = 0; b < 9; ++b) bu = fma(Hi[sym9(a, b)], ui[b], bu);
+                bu = fma(mu * damp_term_b(damping, Hi[sym9(a, a)]), ui[a], bu);
+                const double w = bu - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
+                M.q[t] = w;
+                wu = fma(M.z[t], w, wu);
+            }
+        }
+        cta_sum3f<NT>(rr, ru, wu, M.sb, [&](double x, double y, double z) {
+            bool ok;
+            if (n == 0) {
+                r0 = sqrt(x);
+                if (g0) {  // forcing sequence, as in the standard form
+                    if (!(*g0 > 0.0)) *g0 = r0;
+                    tol = fmax(tol, fmin(0.1, *g0 > 0.0 ? sqrt(r0 / *g0) : 0.0));
+                }
+                stop2 = (tol * r0) * (tol * r0);
+                ok = r0 > 0.0;
+            } else {
+                ok = !(x <= stop2);
+            }
+            ok = ok && isfinite(y);
+            const double beta = n == 0 ? 0.0 : y / gamma_prev;
+            const double den = n == 0 ? z : z - beta * y / alpha_prev;  // p.S p in exact arithmetic
+            ok = ok && den > 0.0 && isfinite(den);
+            const double alpha = ok ? y / den : 0.0;
+            gamma_prev = y;
+            alpha_prev = alpha;
+            *go = ok ? 1 : 0;
+            sc[0] = alpha;
+            sc[1] = beta;
+        });
+        if (!*go) break;
+        const double alpha = sc[0], beta = sc[1];
+        for (int t = threadIdx.x; t < m9; t += NT) {
+            const double u = M.z[t], w = M.q[t];
+            const double pn = n == 0 ? u : fma(beta, M.p[t], u);
+            const double sn = n == 0 ? w : fma(beta, M.sv[t], w);
+            M.p[t] = pn;
+            M.sv[t] = sn;
+            M.x[t] = fma(alpha, pn, M.x[t]);
+            const double rv = fma(-alpha, sn, M.r[t]);
+            M.r[t] = rv;
+            M.rT[t] = (T)rv;
+        }
+        ++n;
+        __syncthreads();
+    }
+    return n;
+}
+
 template <typename T, int NT>
 __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, const double *vvec, const double *wvec,
-                   double mu, int damping, int max_iter, double tol, bool xs, double *g0) {
+                   double mu, int damping, int max_iter, double tol, bool xs, double *g0, bool sr) {
     const int m9 = 9 * d.nc;
     rhs_points<T, NT>(A, M, d, wvec);
     __syncthreads();
@@ -1187,26 +1333,31 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
     __syncthreads();
     for (int t = threadIdx.x; t < m9; t += NT) {
         const int i = t / 9, a = t - 9 * (t / 9);
-        M.r[t] = vvec[t] - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
+        const double rv = vvec[t] - slot_sum(M.slot, M.wf, M.wl, i, 9, a);
+        M.r[t] = rv;
+        M.rT[t] = (T)rv;
         M.x[t] = 0.0;
     }
     __syncthreads();
+    if (sr) return pcg_single_reduction<T, NT>(A, M, d, mu, damping, max_iter, tol, xs, g0);
     // scalar recurrences in thread 0 (see cta_sum2f): sc[0] holds beta or alpha,
     // *go the continue flag
     double *sc = M.sb + 2 * NT + 2;
     int *go = reinterpret_cast<int *>(M.sb + 2 * NT + 3);
-    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, rn = 0.0;  // meaningful in thread 0
+    // meaningful in thread 0; the stopping test |r| <= tol |r0| compares squares
+    // (r.r <= stop2), which keeps a square root off each iteration's scalar chain
+    double r0 = 0.0, rho = 0.0, rho_prev = 0.0, stop2 = 0.0;
     int n = 0;
     {
         const double2 s0 = precond<T, NT>(M, d.nc);
         cta_sum2f<NT>(s0.x, s0.y, M.sb, [&](double x, double y) {
             r0 = sqrt(x);
             rho = y;
-            rn = r0;
             if (g0) {  // forcing sequence: tol = max(tol, min(0.1, sqrt(|g| / |g_first|)))
                 if (!(*g0 > 0.0)) *g0 = r0;
                 tol = fmax(tol, fmin(0.1, *g0 > 0.0 ? sqrt(r0 / *g0) : 0.0));
             }
+            stop2 = (tol * r0) * (tol * r0);
             *go = (r0 > 0.0 && isfinite(rho)) ? 1 : 0;
             sc[0] = 0.0;
         });
@@ -1255,7 +1406,9 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
             const double alpha = sc[0];
             for (int t = threadIdx.x; t < m9; t += NT) {
                 M.x[t] = fma(alpha, M.p[t], M.x[t]);
-                M.r[t] = fma(-alpha, M.q[t], M.r[t]);
+                const double rv = fma(-alpha, M.q[t], M.r[t]);
+                M.r[t] = rv;
+                M.rT[t] = (T)rv;
             }
             __syncthreads();
             const double2 s = precond<T, NT>(M, d.nc);
@@ -1263,8 +1416,7 @@ __device__ int pcg(const BatchArgs &A, const WinMem<T> &M, const WinDesc &d, con
             cta_sum2f<NT>(s.x, s.y, M.sb, [&](double x, double y) {
                 rho_prev = rho;
                 rho = y;
-                rn = sqrt(x);
-                const bool ok = !(rn <= tol * r0 || n >= max_iter) && isfinite(rho);
+                const bool ok = !(x <= stop2 || n >= max_iter) && isfinite(rho);
                 *go = ok ? 1 : 0;
                 sc[0] = ok ? rho / rho_prev : 0.0;
             });
@@ -1314,7 +1466,7 @@ __device__ int owner_warp(int r, int n) {
 }
 
 template <typename T, int NT>
-__device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMem<T> &M, WinState &S, int wi) {
+__device__ __forceinline__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMem<T> &M, WinState &S, int wi) {
     constexpr int NW = NT / 32;
     const WinDesc d = A.desc[wi];
     const int tid = threadIdx.x, m9 = 9 * d.nc;
@@ -1389,7 +1541,7 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
             }
         }
         const int np_ = pcg<T, NT>(A, M, d, M.v, A.wv, mu, O.damping, O.pcg_max_iter, O.pcg_tol,
-                                   O.explicit_schur != 0, O.forcing ? &S.g0 : nullptr);
+                                   O.explicit_schur != 0, O.forcing ? &S.g0 : nullptr, O.pcg_variant != 0);
         make_pv<T, NT>(M, M.x, d.nc);
         __syncthreads();
         double ld = back_points<T, NT>(A, M, d, A.wv, false);
@@ -1457,7 +1609,8 @@ __device__ void solve_window(const BatchArgs &A, const BatchOpts &O, const WinMe
                     }
                 }
                 const int na = pcg<T, NT>(A, M, d, A.gbar_c + 9 * (int64_t)d.cam0, A.gbar_p, mu, O.damping,
-                                          O.adj_pcg_max, O.adj_pcg_tol, O.explicit_schur != 0, nullptr);
+                                          O.adj_pcg_max, O.adj_pcg_tol, O.explicit_schur != 0, nullptr,
+                                          O.pcg_variant != 0);
                 make_pv<T, NT>(M, M.x, d.nc);
                 __syncthreads();
                 back_points<T, NT>(A, M, d, A.gbar_p, true);
@@ -2129,8 +2282,9 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
         (o.damping != MBA_DAMP_DIAG && o.damping != MBA_DAMP_IDENTITY))
         return api_fail(MBA_ERR_INVALID_ARG, "bad solver options");
     if ((o.preconditioner != MBA_PRECOND_BLOCK_JACOBI && o.preconditioner != MBA_PRECOND_SCHUR_JACOBI) ||
-        (o.forcing != 0 && o.forcing != 1))
-        return api_fail(MBA_ERR_INVALID_ARG, "bad preconditioner or forcing option");
+        (o.forcing != 0 && o.forcing != 1) ||
+        (o.pcg_variant != MBA_PCG_STANDARD && o.pcg_variant != MBA_PCG_SINGLE_REDUCTION))
+        return api_fail(MBA_ERR_INVALID_ARG, "bad preconditioner, forcing or PCG variant option");
     if (o.preconditioner == MBA_PRECOND_SCHUR_JACOBI && !b->explicit_ok)
         return api_fail(MBA_ERR_INVALID_ARG, "the Schur-Jacobi preconditioner needs the explicit Schur form");
     if (adj && (!adj->grad_cameras || !adj->grad_points || adj->pcg_max_iter < 0 || !(adj->pcg_rel_tol >= 0.0)))
@@ -2152,6 +2306,7 @@ mba_status mba_batch_solve(mba_batch *b, const mba_solver_options *opt, const mb
     bo.explicit_schur = (b->schur == 2 || o.preconditioner == MBA_PRECOND_SCHUR_JACOBI) ? 1 : 0;
     bo.precond = o.preconditioner;
     bo.forcing = o.forcing;
+    bo.pcg_variant = o.pcg_variant;
     BCK(cudaMemcpyAsync(b->opts, &bo, sizeof(bo), cudaMemcpyHostToDevice, s));
     if (adj) {
         BCK(cudaMemcpyAsync(b->gbar_c, adj->grad_cameras, 72 * (size_t)b->nc, cudaMemcpyHostToDevice, s));

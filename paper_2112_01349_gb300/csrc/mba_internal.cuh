@@ -513,8 +513,9 @@ cudaError_t launch_evaluate_slice(const Prob &P, const int32_t *ci, const int32_
 // pcg.cu
 enum PcgMode { PCG_SOLVE = 0, PCG_RHS_ONLY = 1, PCG_MATVEC = 2 };
 cudaError_t launch_damp(const Prob &P, int damping, int precond, const int32_t *cfirst, cudaStream_t s);
+// variant: mba_pcg_variant (STANDARD: Alg. 2; SINGLE_REDUCTION: the Chronopoulos-Gear form)
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
-                       cudaStream_t s, int forcing = 0);
+                       cudaStream_t s, int forcing = 0, int variant = 0);
 int pcg_grid_size(const Prob &P);
 void plan_pcg_smem(Prob &P);
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s);

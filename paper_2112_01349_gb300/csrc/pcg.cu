@@ -958,9 +958,10 @@ __device__ __forceinline__ void camera_acc_stored(const Prob &P, int64_t s, T s0
         acc[a] = fma(__ldcs(Jc + a * P.npad + s), s0, fma(__ldcs(Jc + (9 + a) * P.npad + s), s1, acc[a]));
 }
 
-enum CamMode { CAM_RHS = 0, CAM_ITER = 1, CAM_MATVEC = 2 };
+enum CamMode { CAM_RHS = 0, CAM_ITER = 1, CAM_MATVEC = 2, CAM_SR = 3 };
 
 __device__ __forceinline__ double2 cta_sum2(double x, double y, bool warp_data, double *sb);
+__device__ __forceinline__ double3 cta_sum3(double x, double y, double z, bool warp_data, double *sb);
 
 
 // Camera pass.  Each CTA owns a contiguous run of whole cameras
@@ -970,10 +971,13 @@ __device__ __forceinline__ double2 cta_sum2(double x, double y, bool warp_data, 
 // camera is finalised.  No global atomics or fences; results do not depend on
 // timing.  CAM_RHS: g = v - c, x = 0, r = g, z = B~^-1 g; returns this CTA's
 // (r.r, r.z).  CAM_ITER: p = z + beta p_prev (p = z first), q = B~ p - c;
-// returns (p.q, 0).  CAM_MATVEC: q = B~ p - c with p given.
+// returns (p.q, 0).  CAM_MATVEC: q = B~ p - c with p given.  CAM_SR (the
+// single-reduction PCG): w = B~ u - c with u in P.z, into P.q; returns (r.r,
+// r.u) and w.u in *third.
 template <typename T, int MODE, bool JS>
 __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, const double *p_prev, double *p_cur,
-                               T *pT_cur, double beta, bool first, double *cslot, double *sb) {
+                               T *pT_cur, double beta, bool first, double *cslot, double *sb,
+                               double *third = nullptr) {
     using T2 = typename V2<T>::type;
     constexpr int U = 4;
     constexpr bool FACT = sizeof(T) == 4 && !JS;
@@ -1099,7 +1103,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
     __syncthreads();
     // finalise this CTA's cameras, three per warp (lanes 9s..9s+8 hold rows of
     // camera s): chunk sums added in chunk order
-    double d1 = 0.0, d2 = 0.0;
+    double d1 = 0.0, d2 = 0.0, d3 = 0.0;
     const int sub = lane / 9, row = lane - 9 * sub;
     for (int c0 = cb + 3 * wid; c0 < ce; c0 += 3 * nwarp) {
         const int cam = c0 + sub;
@@ -1113,7 +1117,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         // a fixed camera has no Schur coupling (its Jacobian columns are zero; the
         // factored product forms Jc^T s from the geometry, so it is masked here)
         if (P.has_fixed && act && P.cam_fixed[cm]) cs = 0.0;
-        double v1 = 0.0, v2 = 0.0;
+        double v1 = 0.0, v2 = 0.0, v3 = 0.0;
         if (MODE == CAM_RHS) {
             const double g = act ? P.v[9 * (int64_t)cm + a] - cs : 0.0;
             double z = 0.0;
@@ -1136,6 +1140,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
             double p = 0.0;
             if (act) {
                 if (MODE == CAM_MATVEC) p = P.p[vo];
+                else if (MODE == CAM_SR) p = ldcg(P.z + vo);
                 else p = first ? ldcg(P.z + vo) : fma(beta, ldcg(p_prev + vo), ldcg(P.z + vo));
             }
             double bp = 0.0;
@@ -1144,14 +1149,21 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
                 const double pb = __shfl_sync(full, p, 9 * sub + b);
                 if (act) bp = fma(__ldg(P.Bd + 81 * (int64_t)cm + a * 9 + b), pb, bp);
             }
+            const double q = act ? bp - cs : 0.0;
             if (act) {
-                const double q = bp - cs;
                 stcg(P.q + vo, q);
                 if (MODE == CAM_ITER) {
                     stcg(p_cur + vo, p);
                     if (pT_cur && !FACT) stcg(pT_cur + vo, (T)p);
                 }
-                v1 = p * q;
+                if (MODE == CAM_SR) {
+                    const double rv = ldcg(P.r + vo);
+                    v1 = rv * rv;
+                    v2 = rv * p;
+                    v3 = q * p;
+                } else {
+                    v1 = p * q;
+                }
             }
             if (FACT && MODE == CAM_ITER && pT_cur) fact_row_store(P, (float *)pT_cur, cm, act, p, sub, row, false);
         }
@@ -1159,9 +1171,16 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         for (int d = 16; d > 0; d >>= 1) {
             v1 += __shfl_xor_sync(full, v1, d);
             v2 += __shfl_xor_sync(full, v2, d);
+            if (MODE == CAM_SR) v3 += __shfl_xor_sync(full, v3, d);
         }
         d1 += v1;
         d2 += v2;
+        d3 += v3;
+    }
+    if constexpr (MODE == CAM_SR) {
+        const double3 t = cta_sum3(lane == 0 ? d1 : 0.0, lane == 0 ? d2 : 0.0, lane == 0 ? d3 : 0.0, false, sb);
+        *third = t.z;
+        return make_double2(t.x, t.y);
     }
     // CTA partials in a fixed order (warp w's cameras, then a tree over warps);
     // d1, d2 are already warp-uniform, so no per-warp shuffle tree is needed
@@ -1306,6 +1325,51 @@ __device__ __forceinline__ double sum_parts(const double *parts, int n, double *
     return sum_parts2(parts, nullptr, n, sb).x;
 }
 
+// Three-value forms of cta_sum2 / sum_parts2 (the single-reduction PCG); sb
+// holds 96 doubles.
+__device__ __forceinline__ double3 cta_sum3(double x, double y, double z, bool warp_data, double *sb) {
+    __shared__ double3 s_out3;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (warp_data) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+            z += __shfl_down_sync(0xffffffffu, z, o);
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sb[wid] = x;
+        sb[32 + wid] = y;
+        sb[64 + wid] = z;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        double sx = in ? sb[lane] : 0.0, sy = in ? sb[32 + lane] : 0.0, sz = in ? sb[64 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+            sz += __shfl_down_sync(0xffffffffu, sz, o);
+        }
+        if (lane == 0) s_out3 = make_double3(sx, sy, sz);
+    }
+    __syncthreads();
+    return s_out3;
+}
+
+__device__ __forceinline__ double3 sum_parts3(const double *a, const double *b, const double *c, int n, double *sb) {
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x += ldcg(a + i);
+        y += ldcg(b + i);
+        z += ldcg(c + i);
+    }
+    return cta_sum3(x, y, z, (int)(threadIdx.x & ~31u) < n, sb);
+}
+
 // ---------------------------------------------------------------------------
 // persistent PCG kernel (cooperative launch, one CTA per SM for the whole solve)
 // ---------------------------------------------------------------------------
@@ -1313,13 +1377,14 @@ __device__ __forceinline__ double sum_parts(const double *parts, int n, double *
 // in FP32-mixed when the Jacobian comes from dual numbers).
 // STG: the staged point pass (factored form only, a separate instantiation so
 // that its code does not weigh on the direct pass's registers).
-template <typename T, bool JS, bool STG>
+// SR: the single-reduction recurrence (mba_pcg_variant), also its own instance.
+template <typename T, bool JS, bool STG, bool SR>
 __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
     pcg_kernel(Prob P, int mode, int max_iter, double tol, long long spin, int forcing) {
     using T2 = typename V2<T>::type;
     constexpr bool FACT = sizeof(T) == 4 && !JS;  // FP32-mixed, analytic Jacobian: the factored form
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double sb[64];
+    __shared__ double sb[96];
     DevState *st = P.st;
     if (st->done || st->blockfail) return;  // a failed damping: the LM loop rejects this iteration
     // forcing sequence: the first solve's right-hand side norm as it was before
@@ -1370,13 +1435,15 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                     break;
                 }
     };
-    auto point_pass_iter = [&]() -> bool {
+    // the point pass of one product; rows: the search rows in global memory
+    // (read where they are not in shared memory)
+    auto point_pass_iter = [&](const T *rows) -> bool {
         if constexpr (FACT && STG) {
             if (S)
-                return point_pass_fact_staged(P, (const float *)ps, (const float *)pT, (float2 *)sbuf, stages,
+                return point_pass_fact_staged(P, (const float *)ps, (const float *)rows, (float2 *)sbuf, stages,
                                               s_full, s_empty, s_org, S, my_nt, use, issued);
         }
-        point_pass_any<T, false, FACT>(P, ps, pT, sbuf);
+        point_pass_any<T, false, FACT>(P, ps, rows, sbuf);
         return true;
     };
     // owner phase: p = z + beta p_prev written in FP64 and, for the gathers, as
@@ -1404,7 +1471,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             phase_p(nullptr, nullptr, 0.0, true, P.p);
             if (!(ok = barrier())) return;
         }
-        const bool pok = point_pass_iter();
+        const bool pok = point_pass_iter(pT);
         if (pok && barrier()) camera_pass<T, CAM_MATVEC, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, true, cslot, sb);
         drain();
         return;
@@ -1421,6 +1488,136 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
             stcg(part_rho + blockIdx.x, d.y);
         }
         ok = barrier();
+    }
+
+    if constexpr (SR) {
+        // Single-reduction PCG (Chronopoulos-Gear form; the oracle's
+        // pcg_single_reduction).  Step n: the point pass forms s~ for u_n,
+        // barrier, the camera pass gives w_n = S~ u_n at each camera's owner and
+        // the partials of r.r, r.u and w.u, barrier, then every CTA derives
+        // alpha and beta from the three sums and the owners update p, s, x, r
+        // and u = B~^-1 r and write u's rows, which a third barrier publishes
+        // to the next point pass.  Three barriers and one reduction per step
+        // (the standard loop: three barriers and two reductions with the rows
+        // in shared memory, four barriers otherwise).
+        // Not kept: a two-barrier form in which every CTA formed u's rows from
+        // the recurrence u_{n+1} = u_n - alpha B~^-1 s_n in FP32.  As |u| falls
+        // over the solve, that subtraction cancels and the FP32 rounding of the
+        // earlier, larger terms dominates: 1e-3 relative error in the step after
+        // 10 PCG steps and 0.03 to 0.15 after 30, against 1.5e-5 for the rows
+        // written by the owners.
+        __shared__ double s_alpha, s_beta, s_r0, s_rn, s_stop2, s_gprev, s_aprev;
+        __shared__ int s_go;
+        // where the point pass finds u's rows when they are not in shared memory
+        const T *rows_u = sizeof(T) == 8 ? (const T *)P.z : (const T *)P.zT;
+        int n = 0;
+        while (ok && (n == 0 || n < max_iter)) {
+            if (ps) stage_p<T, FACT>(P, ps, nullptr, nullptr, 0.0, true, nullptr);
+            if (!(ok = point_pass_iter(rows_u))) break;
+            if (!(ok = barrier())) break;
+            {
+                double wu = 0.0;
+                const double2 d =
+                    camera_pass<T, CAM_SR, JS>(P, sbuf, nullptr, nullptr, nullptr, 0.0, false, cslot, sb, &wu);
+                if (threadIdx.x == 0) {
+                    stcg(part_rr + blockIdx.x, d.x);
+                    stcg(part_rho + blockIdx.x, d.y);
+                    stcg(part_pq + blockIdx.x, wu);
+                }
+            }
+            if (!(ok = barrier())) break;
+            const double3 sums = sum_parts3(part_rr, part_rho, part_pq, G, sb);
+            if (threadIdx.x == 0) {
+                // sums: r.r, gamma = r.u, delta = w.u
+                bool go;
+                if (n == 0) {
+                    const double r0 = sqrt(sums.x);
+                    double t = tol;
+                    if (forcing) {  // eta = min(0.1, sqrt(|g| / |g_first|)), |g_first| = r0 in the first solve
+                        const double g0 = s_g0;
+                        t = fmax(t, fmin(0.1, sqrt(r0 / (g0 > 0.0 ? g0 : r0))));
+                    }
+                    s_r0 = r0;
+                    s_stop2 = (t * r0) * (t * r0);
+                    go = r0 > 0.0;
+                } else {
+                    go = !(sums.x <= s_stop2);
+                }
+                s_rn = sqrt(sums.x);
+                go = go && isfinite(sums.y);
+                const double beta = n == 0 ? 0.0 : sums.y / s_gprev;
+                const double den = n == 0 ? sums.z : sums.z - beta * sums.y / s_aprev;  // p.S p
+                go = go && den > 0.0 && isfinite(den);
+                const double alpha = go ? sums.y / den : 0.0;
+                s_gprev = sums.y;
+                s_aprev = alpha;
+                s_alpha = alpha;
+                s_beta = beta;
+                s_go = go ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_go) break;
+            const double alpha = s_alpha, beta = s_beta;
+            // p = u + beta p, s = w + beta s (s in the free second direction buffer),
+            // x += alpha p, r -= alpha s, u = B~^-1 r over this CTA's own cameras
+            const bool last = n + 1 >= max_iter;  // the step cap ends the solve after this update
+            {
+                double *sv = P.p2;
+                double rr = 0.0;  // |r|^2 after the update, taken on the last step only
+                const int cb = P.cta_cam[blockIdx.x], ce = P.cta_cam[blockIdx.x + 1];
+                for (int c0 = cb + 3 * wid; c0 < ce; c0 += 3 * nwarp) {
+                    const int cam = c0 + my_sub;
+                    const bool act = lane < 27 && cam < ce;
+                    const int64_t vo = (int64_t)(act ? cam : c0) * kVec + row;
+                    double rv = 0.0;
+                    if (act) {
+                        const double u = ldcg(P.z + vo), w = ldcg(P.q + vo);
+                        const double pn = n == 0 ? u : fma(beta, ldcg(P.p + vo), u);
+                        const double sn = n == 0 ? w : fma(beta, ldcg(sv + vo), w);
+                        stcg(P.p + vo, pn);
+                        stcg(sv + vo, sn);
+                        stcg(P.x + vo, fma(alpha, pn, ldcg(P.x + vo)));
+                        rv = fma(-alpha, sn, ldcg(P.r + vo));
+                        stcg(P.r + vo, rv);
+                        rr = fma(rv, rv, rr);
+                    }
+                    double z = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        const double rc = __shfl_sync(full, rv, my_sub * 9 + c);
+                        if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c), rc, z);
+                    }
+                    if (FACT) fact_row_store(P, (float *)P.zT, act ? cam : c0, act, z, my_sub, row, true);
+                    if (act) {
+                        stcg(P.z + vo, z);
+                        if (sizeof(T) == 4 && !FACT) stcg((float *)P.zT + vo, (float)z);
+                    }
+                }
+                if (last) {
+                    // the residual norm the solve reports, in its own partials (the
+                    // step's sums may still be read by other CTAs)
+                    const double2 t = cta_sum2(rr, 0.0, true, sb);
+                    if (threadIdx.x == 0) stcg(P.red + 3 * G + blockIdx.x, t.x);
+                }
+            }
+            ++n;
+            if (last) {
+                if (!(ok = barrier())) break;
+                const double rrn = sum_parts(P.red + 3 * G, G, sb);
+                if (threadIdx.x == 0) s_rn = sqrt(rrn);
+                __syncthreads();
+                break;
+            }
+            if (!(ok = barrier())) break;
+        }
+        drain();
+        if (!ok) atomicCAS(&st->err, 0, (int)MBA_ERR_TIMEOUT);
+        if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
+            st->pcg_iters = n;
+            st->pcg_rel_res = s_r0 > 0.0 ? s_rn / s_r0 : 0.0;
+            if (forcing && !(s_g0 > 0.0)) st->g0 = s_r0;
+        }
+        return;
     }
 
     // The scalar recurrences (r0, rho, alpha, beta, the stopping test) run in
@@ -1464,7 +1661,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                 phase_p(p_prev, p_cur, beta, n == 0, nullptr);
                 if (!(ok = barrier())) break;
             }
-            if (!(ok = point_pass_iter())) break;
+            if (!(ok = point_pass_iter(pT))) break;
             if (!(ok = barrier())) break;
             {
                 const double2 d = camera_pass<T, CAM_ITER, JS>(P, sbuf, p_prev, p_cur,
@@ -1781,39 +1978,52 @@ void plan_pcg_smem(Prob &P) {
 
 int pcg_block(const Prob &P) { return P.fp32 ? PcgBlock<float>::value : PcgBlock<double>::value; }
 
-static const void *pcg_fn(const Prob &P) {
-    if (!P.fp32) return (const void *)pcg_kernel<double, true, false>;
-    if (P.autodiff) return (const void *)pcg_kernel<float, true, false>;
-    return P.pcg_stages ? (const void *)pcg_kernel<float, false, true> : (const void *)pcg_kernel<float, false, false>;
+template <bool SR>
+static const void *pcg_fn_v(const Prob &P) {
+    if (!P.fp32) return (const void *)pcg_kernel<double, true, false, SR>;
+    if (P.autodiff) return (const void *)pcg_kernel<float, true, false, SR>;
+    return P.pcg_stages ? (const void *)pcg_kernel<float, false, true, SR>
+                        : (const void *)pcg_kernel<float, false, false, SR>;
+}
+static const void *pcg_fn(const Prob &P, int variant = MBA_PCG_STANDARD) {
+    return variant == MBA_PCG_SINGLE_REDUCTION ? pcg_fn_v<true>(P) : pcg_fn_v<false>(P);
+}
+
+static int resident(const void *fn, int block, size_t smem) {
+    int blocks = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, block, smem) != cudaSuccess) return 0;
+    return blocks;
 }
 
 // One CTA per SM (the camera partition is built for exactly that many);
-// returns 0 if the kernel cannot be resident with its shared memory.
+// returns 0 if either PCG instance (standard, single-reduction) cannot be
+// resident with its shared memory.
 int pcg_grid_size(const Prob &P) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = (size_t)P.pcg_smem;
-    int blocks = 0;
-    const void *fn = pcg_fn(P);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, pcg_block(P), smem);
-    return blocks >= 1 ? sms : 0;
+    const bool ok = resident(pcg_fn(P), pcg_block(P), smem) >= 1 &&
+                    resident(pcg_fn(P, MBA_PCG_SINGLE_REDUCTION), pcg_block(P), smem) >= 1;
+    return ok ? sms : 0;
 }
 
 cudaError_t launch_pcg(const Prob &P, int mode, int max_iter, double tol, long long spin_limit, int grid,
-                       cudaStream_t s, int forcing) {
+                       cudaStream_t s, int forcing, int variant) {
+    // the right-hand-side and product-only modes are the standard kernel's
+    if (mode != PCG_SOLVE) variant = MBA_PCG_STANDARD;
     const size_t smem = (size_t)P.pcg_smem;
     // the barrier targets count arrivals from zero in every launch
     cudaError_t e = cudaMemsetAsync(&P.st->barrier, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     // the shared-memory plan differs between problems (stages, search direction),
     // so the kernel's dynamic shared-memory limit is set for this launch
-    e = cudaFuncSetAttribute(pcg_fn(P), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(pcg_fn(P, variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     Prob Pc = P;
     void *args[] = {(void *)&Pc, (void *)&mode, (void *)&max_iter, (void *)&tol, (void *)&spin_limit, (void *)&forcing};
-    return cudaLaunchCooperativeKernel(pcg_fn(P), dim3(grid), dim3(pcg_block(P)), args, smem, s);
+    return cudaLaunchCooperativeKernel(pcg_fn(P, variant), dim3(grid), dim3(pcg_block(P)), args, smem, s);
 }
 
 cudaError_t launch_backsub(const Prob &P, double *partial, int nb, cudaStream_t s) {

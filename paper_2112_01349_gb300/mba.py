@@ -30,6 +30,8 @@ MBA_JACOBIAN_ANALYTIC, MBA_JACOBIAN_AUTODIFF = 0, 1
 JACOBIAN = {"analytic": MBA_JACOBIAN_ANALYTIC, "autodiff": MBA_JACOBIAN_AUTODIFF}
 MBA_COST_FP64, MBA_COST_FLOAT_FLOAT = 0, 1
 COST_ARITHMETIC = {"fp64": MBA_COST_FP64, "float-float": MBA_COST_FLOAT_FLOAT}
+MBA_PCG_STANDARD, MBA_PCG_SINGLE_REDUCTION = 0, 1
+PCG_VARIANT = {"standard": MBA_PCG_STANDARD, "single_reduction": MBA_PCG_SINGLE_REDUCTION}
 
 
 class MbaError(RuntimeError):
@@ -47,7 +49,8 @@ class SolverOptions(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("pcg_max_iter", C.c_int32), ("pcg_rel_tol", C.c_double),
                 ("damping", C.c_int32), ("initial_radius", C.c_double), ("min_relative_decrease", C.c_double),
                 ("function_tol", C.c_double), ("barrier_spin_limit", C.c_int64), ("collect_timing", C.c_int32),
-                ("preconditioner", C.c_int32), ("forcing", C.c_int32), ("cost_arithmetic", C.c_int32)]
+                ("preconditioner", C.c_int32), ("forcing", C.c_int32), ("cost_arithmetic", C.c_int32),
+                ("pcg_variant", C.c_int32)]
 
 
 class Iteration(C.Structure):
@@ -248,6 +251,8 @@ def solver_options(**kw) -> SolverOptions:
             v = int(bool(v))
         if k == "cost_arithmetic" and isinstance(v, str):
             v = COST_ARITHMETIC[v]
+        if k == "pcg_variant" and isinstance(v, str):
+            v = PCG_VARIANT[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown solver option {k}")
         setattr(o, k, v)

@@ -227,3 +227,37 @@ def test_batch_forcing_matches_oracle(mba):
         ref = _oracle_solve(s, forcing=True)
         rel_close(r["summaries"][w]["final_cost"], ref["final_cost"], 1e-6, f"window {w} final cost")
         assert abs(r["summaries"][w]["pcg_iters_total"] - sum(t["pcg_iters"] for t in ref["trace"])) <= 4
+
+
+@pytest.mark.parametrize("schur", ["implicit", "explicit"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
+def test_batch_single_reduction_pcg_matches_oracle(mba, precision, tol, schur):
+    """The single-reduction PCG (Chronopoulos-Gear form) per window against the
+    oracle's twin of it: iterations, PCG steps, accept decisions (FP64) and
+    final cost; then the adjoint through the same recurrence."""
+    ws = _small(count=8, seed=71)
+    rng = np.random.default_rng(3)
+    with mba.Batch(_tuples(ws), precision=precision) as b:
+        b.set_schedule(schur=schur)
+        r = b.solve(pcg_variant="single_reduction", **OPTS)
+        b.reset()
+        gc = rng.normal(size=(b.info["nc"], 9))
+        gp = rng.normal(size=(b.info["np"], 3))
+        ra = b.solve(gc, gp, adjoint_pcg_max_iter=1000, adjoint_pcg_rel_tol=1e-14, adjoint_mu=1e-2,
+                     pcg_variant="single_reduction", **OPTS)
+        g = b.gradients()
+        cams, pts = b.parameters()
+    co, po, oo = b.offsets
+    for w, s in enumerate(ws):
+        ref = _oracle_solve(s, pcg_variant="single_reduction")
+        sm = r["summaries"][w]
+        assert sm["status"] == 0 and sm["iterations"] == ref["iterations"]
+        rel_close(sm["final_cost"], ref["final_cost"], tol, f"window {w} final cost")
+        if precision == "fp64":
+            assert sm["accepted"] == sum(t["accepted"] for t in ref["trace"])
+            assert abs(sm["pcg_iters_total"] - sum(t["pcg_iters"] for t in ref["trace"])) <= 8
+        c, p = cams[co[w]:co[w + 1]], pts[po[w]:po[w + 1]]
+        adj = oracle.adjoint(c, p, s.observations, s.cam_idx, s.pt_idx, 1e-2, gc[co[w]:co[w + 1]],
+                             gp[po[w]:po[w + 1]], pcg_max=1000, pcg_tol=1e-14, pcg_variant="single_reduction")
+        rel_close(g["grad_obs"][oo[w]:oo[w + 1]], adj["grad_obs"], 1e-6 if precision == "fp64" else 3e-3,
+                  f"window {w} observation gradient")
