@@ -30,17 +30,13 @@
 // Summation orders are fixed by the launch schedule (threads per CTA), so a
 // schedule gives the same bits on every run.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <string>
-#include <thread>
 #include <vector>
 
-#include <sched.h>
 
 #include "mba_internal.cuh"
 
@@ -1685,6 +1681,165 @@ __global__ void __launch_bounds__(NT, MINB) batch_kernel(BatchArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Layout of a batch on the device (mba_batch_create).  The windows' local
+// indices become global ones (window offsets added), and the point-major and
+// camera-major orders are stable sorts of the observations by global point and
+// by global camera: the windows' observations are contiguous and in window
+// order, so these are the per-window stable orders.  Warp chunks and the
+// explicit form's pair lists follow in the order the kernels expect.
+// flags[0] bits: 1 index out of its window's range, 2 non-finite input,
+// 4 a point without observations, 8 a camera without observations.
+// ---------------------------------------------------------------------------
+constexpr int kLayBlock = 256;
+
+__device__ __forceinline__ int window_of(const int32_t *off, int nw, int64_t x) {
+    int lo = 0, hi = nw;  // off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void lay_globalize_kernel(int64_t n, int nw, const int32_t *oo, const int32_t *co, const int32_t *po,
+                                     const int32_t *ci, const int32_t *pi, const double *obs, int32_t *gpt,
+                                     int32_t *gcam, int32_t *flags) {
+    int bad = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int w = window_of(oo, nw, k);
+        const int32_t c = ci[k], q = pi[k], nc = co[w + 1] - co[w], np = po[w + 1] - po[w];
+        if (c < 0 || c >= nc || q < 0 || q >= np) bad |= 1;
+        gpt[k] = po[w] + (q < 0 || q >= np ? 0 : q);
+        gcam[k] = co[w] + (c < 0 || c >= nc ? 0 : c);
+        if (!isfinite(obs[2 * k]) || !isfinite(obs[2 * k + 1])) bad |= 2;
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+__global__ void lay_finite_kernel(const double *a, int64_t m, int32_t *flags) {
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) bad = 2;
+    if (bad) atomicOr(flags, bad);
+}
+
+// point-major copies: perm[i] = input index of point-major position i
+__global__ void lay_gather_pm_kernel(int64_t n, const int32_t *perm, const int32_t *gpt, const int32_t *gcam,
+                                     const double *obs, int2 *pm_pc, double2 *pm_uv, int32_t *pm_orig, int32_t *inv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = perm[i];
+        pm_pc[i] = make_int2(gpt[k], gcam[k]);
+        pm_uv[i] = make_double2(obs[2 * (int64_t)k], obs[2 * (int64_t)k + 1]);
+        pm_orig[i] = k;
+        inv[k] = (int32_t)i;
+    }
+}
+
+// camera-major copies: perm[c] = input index of camera-major position c
+__global__ void lay_gather_cm_kernel(int64_t n, const int32_t *perm, const int32_t *gpt, const int32_t *inv,
+                                     int32_t *cm_pt, int32_t *cm2pm, int32_t *pm2cm) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = perm[c], i = inv[k];
+        cm_pt[c] = gpt[k];
+        cm2pm[c] = i;
+        pm2cm[i] = (int32_t)c;
+    }
+}
+
+__global__ void lay_empty_kernel(const int32_t *ptr, int64_t nseg, int bit, int32_t *flags) {
+    int bad = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nseg; j += (int64_t)gridDim.x * blockDim.x)
+        if (ptr[j + 1] == ptr[j]) bad = bit;
+    if (bad) atomicOr(flags, bad);
+}
+
+// Warp chunks of one window: greedy runs of whole points with <= 32
+// observations (a longer point alone), then the window's end entry.  One
+// thread per window; fill == false only counts (into cnt[w]).
+__global__ void lay_chunks_kernel(int nw, WinDesc *desc, const int32_t *pt_ptr, int32_t *cnt, const int32_t *wch0,
+                                  int2 *wchunk, bool fill) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    WinDesc &d = desc[w];
+    const int32_t p0 = d.pt0, np = d.np;
+    int32_t j = 0, m = 0;
+    const int32_t base = fill ? wch0[w] : 0;
+    while (j < np) {
+        if (fill) wchunk[base + m] = make_int2(p0 + j, pt_ptr[p0 + j]);
+        int32_t len = pt_ptr[p0 + j + 1] - pt_ptr[p0 + j];
+        ++j;
+        if (len <= 32)
+            while (j < np) {
+                const int32_t l2 = pt_ptr[p0 + j + 1] - pt_ptr[p0 + j];
+                if (len + l2 > 32) break;
+                len += l2;
+                ++j;
+            }
+        ++m;
+    }
+    if (fill) {
+        wchunk[base + m] = make_int2(p0 + np, d.obs0 + d.n);
+        d.wch0 = base;
+        d.nwch = m;
+    } else {
+        cnt[w] = m + 1;
+    }
+}
+
+// Schur-block pairs of each point: every ordered pair (u, v) of its
+// observations (point-major positions) with camera(u) <= camera(v), u then v
+// ascending.  Count pass (cnt[j], and the total in 64 bits into *total, so
+// that an int32 overflow of the offsets is seen) and fill pass (pairs in point
+// order at off[j], with the global block key of each).
+__global__ void lay_pairs_kernel(int64_t np_all, int nw, const int32_t *po, const WinDesc *desc,
+                                 const int32_t *pt_ptr, const int2 *pm_pc, const int32_t *pm2cm, int32_t *cnt,
+                                 unsigned long long *total, const int32_t *off, int4 *pairs, int32_t *keys,
+                                 bool fill) {
+    unsigned long long mine = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np_all;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const WinDesc &d = desc[window_of(po, nw, j)];
+        const int32_t a = pt_ptr[j], e = pt_ptr[j + 1];
+        int32_t m = 0, pos = fill ? off[j] : 0;
+        for (int32_t u = a; u < e; ++u) {
+            const int32_t cu = pm_pc[u].y - d.cam0;
+            for (int32_t v = a; v < e; ++v) {
+                const int32_t cv = pm_pc[v].y - d.cam0;
+                if (cu > cv) continue;
+                if (fill) {
+                    pairs[pos] = make_int4(pm2cm[u], pm2cm[v], (int32_t)j, 0);
+                    keys[pos] = d.blk0 + cu * d.nc - (cu * (cu - 1)) / 2 + (cv - cu);
+                    ++pos;
+                } else {
+                    ++m;
+                }
+            }
+        }
+        if (!fill) {
+            cnt[j] = m;
+            mine += (unsigned long long)m;
+        }
+    }
+    if (!fill) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total, mine);
+    }
+}
+
+__global__ void lay_gather_pairs_kernel(int64_t m, const int32_t *perm, const int4 *in, int4 *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+unsigned lay_grid(int64_t n) {
+    int64_t g = (n + kLayBlock - 1) / kLayBlock;
+    if (g > 4096) g = 4096;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
 template <typename T, int NT>
 size_t smem_bytes(int ncmax, int64_t svals) {
     WinMem<T> m;
@@ -1725,6 +1880,7 @@ struct mba_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *pool = nullptr;
+    void *pool2 = nullptr;  // the explicit form's pair lists, J copy and S~ scratch
     BatchArgs A{};
     WinDesc *desc = nullptr;
     int32_t *order = nullptr, *counter = nullptr;
@@ -1830,65 +1986,6 @@ mba_status build_graph(mba_batch *b) {
     return MBA_OK;
 }
 
-// Threads the process may keep busy at once: the smaller of the cores it is
-// allowed to run on (affinity mask) and, where the container sets one, its
-// CFS CPU quota (cgroup v2 cpu.max, or v1 cpu.cfs_quota_us / cfs_period_us).
-// More busy threads than the quota allows get the whole process throttled
-// for the rest of each scheduling period.
-int host_threads() {
-    int n = (int)std::thread::hardware_concurrency();
-    if (n <= 0) n = 4;
-    cpu_set_t set;
-    CPU_ZERO(&set);
-    if (sched_getaffinity(0, sizeof(set), &set) == 0) {
-        const int c = CPU_COUNT(&set);
-        if (c > 0 && c < n) n = c;
-    }
-    long long quota = -1, period = 0;
-    if (FILE *f = std::fopen("/sys/fs/cgroup/cpu.max", "r")) {
-        char q[32] = {0};
-        if (std::fscanf(f, "%31s %lld", q, &period) == 2 && std::strcmp(q, "max") != 0) quota = std::atoll(q);
-        std::fclose(f);
-    } else {
-        FILE *fq = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_quota_us", "r");
-        FILE *fp = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_period_us", "r");
-        if (!fq || !fp || std::fscanf(fq, "%lld", &quota) != 1 || std::fscanf(fp, "%lld", &period) != 1) quota = -1;
-        if (fq) std::fclose(fq);
-        if (fp) std::fclose(fp);
-    }
-    if (quota > 0 && period > 0) {
-        const long long c = quota / period;  // whole cores within the quota
-        if (c < n) n = c > 1 ? (int)c : 1;
-    }
-    return n;
-}
-
-// Runs f(0..n-1) over the host's cores (dynamic claiming; each call of f
-// touches its own data).
-template <typename F>
-void parallel_for(int n, F &&f) {
-    static const int hw = host_threads();
-    int nt = hw;
-    if (nt > 32) nt = 32;
-    if (nt > n) nt = n;
-    if (nt <= 1) {
-        for (int i = 0; i < n; ++i) f(i);
-        return;
-    }
-    std::atomic<int> next{0};
-    std::vector<std::thread> th;
-    th.reserve((size_t)nt);
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&]() {
-            for (;;) {
-                const int i = next.fetch_add(1);
-                if (i >= n) break;
-                f(i);
-            }
-        });
-    for (auto &t : th) t.join();
-}
-
 bool finite_all(const double *a, int64_t m) {
     for (int64_t i = 0; i < m; ++i)
         if (!std::isfinite(a[i])) return false;
@@ -1932,158 +2029,31 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     const int64_t NC = cam_offsets[nw], NP = pt_offsets[nw], N = obs_offsets[nw];
     if (N >= (int64_t(1) << 31) - 64 || NP >= (int64_t(1) << 31) - 64 || NC >= (int64_t(1) << 31) - 64)
         return api_fail(MBA_ERR_INVALID_ARG, "totals must be below 2^31 - 64");
-    if (!finite_all(cameras, 9 * NC) || !finite_all(points, 3 * NP) || !finite_all(observations, 2 * N))
-        return api_fail(MBA_ERR_NONFINITE, "non-finite camera, point or observation");
 
-    // ---- host layout: per window, stable point-major and camera-major orders ----
-    // Windows are independent and each writes its own ranges of the global
-    // arrays, so the work is spread over host threads (window by window).
-    std::vector<int2> pm_pc((size_t)N);
-    std::vector<double2> pm_uv((size_t)N);
-    std::vector<int32_t> pm_orig((size_t)N), cm_pt((size_t)N), cm2pm((size_t)N), pm2cm((size_t)N),
-        cam_ptr((size_t)NC + 1);
+    // Window descriptors (the layout fields wch0 / nwch are filled on the
+    // device), the windows' offsets as int32, the explicit form's block
+    // numbering (window w's upper blocks start at blk0) and the launch order.
     std::vector<WinDesc> desc((size_t)nw);
-    std::vector<std::vector<int2>> wch_w((size_t)nw);   // warp chunks of each window (+ its end entry)
-    std::vector<std::vector<int32_t>> bcnt_w((size_t)nw);  // Schur-block pair offsets of each window
-    std::vector<int64_t> npairs_w((size_t)nw, 0);
-    std::vector<int> err_w((size_t)nw, 0);  // 0, or 1 + index into msgs
-    static const char *msgs[] = {"observation index out of its window's range", "a point without observations",
-                                 "a camera without observations"};
-    parallel_for(nw, [&](int w) {
-        const int32_t c0 = (int32_t)cam_offsets[w], p0 = (int32_t)pt_offsets[w], o0 = (int32_t)obs_offsets[w];
-        const int32_t nc = (int32_t)(cam_offsets[w + 1] - c0), np = (int32_t)(pt_offsets[w + 1] - p0),
-                      n = (int32_t)(obs_offsets[w + 1] - o0);
-        std::vector<int32_t> cntp((size_t)np + 1, 0), cntc((size_t)nc + 1, 0);
-        for (int32_t k = 0; k < n; ++k) {
-            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
-            if (ci < 0 || ci >= nc || pi < 0 || pi >= np) {
-                err_w[w] = 1;
-                return;
-            }
-            cntp[pi + 1]++;
-            cntc[ci + 1]++;
-        }
-        for (int32_t j = 0; j < np; ++j) {
-            if (cntp[j + 1] == 0) {
-                err_w[w] = 2;
-                return;
-            }
-            cntp[j + 1] += cntp[j];
-        }
-        for (int32_t i = 0; i < nc; ++i) {
-            if (cntc[i + 1] == 0) {
-                err_w[w] = 3;
-                return;
-            }
-            cntc[i + 1] += cntc[i];
-        }
-        std::vector<int32_t> posp(cntp.begin(), cntp.end() - 1), posc(cntc.begin(), cntc.end() - 1),
-            pmpos((size_t)n);
-        for (int32_t k = 0; k < n; ++k) {
-            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
-            const int32_t pp = o0 + posp[pi]++;
-            pm_pc[pp] = make_int2(p0 + pi, c0 + ci);
-            pm_uv[pp] = make_double2(observations[2 * (int64_t)(o0 + k)], observations[2 * (int64_t)(o0 + k) + 1]);
-            pm_orig[pp] = o0 + k;
-            pmpos[k] = pp;
-        }
-        for (int32_t k = 0; k < n; ++k) {
-            const int32_t ci = cam_idx[o0 + k], pi = pt_idx[o0 + k];
-            const int32_t cp = o0 + posc[ci]++;
-            cm_pt[cp] = p0 + pi;
-            cm2pm[cp] = pmpos[k];
-            pm2cm[pmpos[k]] = cp;
-        }
-        for (int32_t i = 0; i < nc; ++i) cam_ptr[c0 + i] = o0 + cntc[i];
+    std::vector<int32_t> off32(3 * ((size_t)nw + 1));  // observation, camera, point offsets
+    int64_t nblk = 0;
+    for (int w = 0; w < nw; ++w) {
         WinDesc &d = desc[w];
-        d.cam0 = c0;
-        d.nc = nc;
-        d.pt0 = p0;
-        d.np = np;
-        d.obs0 = o0;
-        d.n = n;
-        // warp chunks: greedy runs of whole points with <= 32 observations
-        std::vector<int2> &wc = wch_w[w];
-        int32_t j = 0;
-        while (j < np) {
-            wc.push_back(make_int2(p0 + j, o0 + cntp[j]));
-            int32_t len = cntp[j + 1] - cntp[j];
-            ++j;
-            if (len <= 32)
-                while (j < np && len + (cntp[j + 1] - cntp[j]) <= 32) {
-                    len += cntp[j + 1] - cntp[j];
-                    ++j;
-                }
-        }
-        d.nwch = (int32_t)wc.size();
-        wc.push_back(make_int2(p0 + np, o0 + n));
-        // Schur-block pair counts (explicit S~): for each point, every ordered
-        // pair (u, v) of its observations with camera(u) < camera(v), or with
-        // the same camera (all ordered pairs), goes to block (camera(u), camera(v))
-        const int32_t nb = nc * (nc + 1) / 2;
-        std::vector<int32_t> &bc = bcnt_w[w];
-        bc.assign((size_t)nb + 1, 0);
-        for (int32_t o = o0; o < o0 + n;) {
-            int32_t e = o;
-            while (e < o0 + n && pm_pc[e].x == pm_pc[o].x) ++e;
-            for (int32_t u = o; u < e; ++u)
-                for (int32_t v = o; v < e; ++v) {
-                    const int32_t cu = pm_pc[u].y - c0, cv = pm_pc[v].y - c0;
-                    if (cu <= cv) ++bc[cu * nc - (cu * (cu - 1)) / 2 + (cv - cu) + 1];
-                }
-            o = e;
-        }
-        for (int32_t q = 0; q < nb; ++q) bc[q + 1] += bc[q];
-        npairs_w[w] = bc[nb];
-    });
-    for (int w = 0; w < nw; ++w)
-        if (err_w[w]) return api_fail(MBA_ERR_INVALID_ARG, msgs[err_w[w] - 1]);
-    cam_ptr[(size_t)NC] = (int32_t)N;
-    std::vector<int2> wchunk;
-    {
-        int64_t tot = 0;
-        for (int w = 0; w < nw; ++w) tot += (int64_t)wch_w[w].size();
-        if (tot >= (int64_t(1) << 31) - 64) return api_fail(MBA_ERR_INVALID_ARG, "too many warp chunks");
-        wchunk.reserve((size_t)tot);
-        for (int w = 0; w < nw; ++w) {
-            desc[w].wch0 = (int32_t)wchunk.size();
-            wchunk.insert(wchunk.end(), wch_w[w].begin(), wch_w[w].end());
-            std::vector<int2>().swap(wch_w[w]);
-        }
+        d.cam0 = (int32_t)cam_offsets[w];
+        d.nc = (int32_t)(cam_offsets[w + 1] - cam_offsets[w]);
+        d.pt0 = (int32_t)pt_offsets[w];
+        d.np = (int32_t)(pt_offsets[w + 1] - pt_offsets[w]);
+        d.obs0 = (int32_t)obs_offsets[w];
+        d.n = (int32_t)(obs_offsets[w + 1] - obs_offsets[w]);
+        d.wch0 = d.nwch = 0;
+        d.blk0 = (int32_t)(nblk < (int64_t(1) << 30) ? nblk : 0);
+        d.pad = 0;
+        nblk += (int64_t)d.nc * (d.nc + 1) / 2;
     }
-    // Schur-block pair lists, in point order inside each block (skipped, and the
-    // explicit form not offered, when they would be too large)
-    std::vector<int4> pairs;
-    std::vector<int32_t> blk_ptr;
-    int64_t total_pairs = 0;
-    for (int w = 0; w < nw; ++w) total_pairs += npairs_w[w];
-    const bool explicit_ok = total_pairs <= (int64_t(1) << 28);
-    if (explicit_ok) {
-        pairs.resize((size_t)total_pairs);
-        std::vector<int64_t> base_w((size_t)nw);
-        int64_t base = 0;
-        for (int w = 0; w < nw; ++w) {
-            desc[w].blk0 = (int32_t)blk_ptr.size();
-            for (const int32_t c : bcnt_w[w]) blk_ptr.push_back((int32_t)(base + c));
-            base_w[w] = base;
-            base += npairs_w[w];
-        }
-        parallel_for(nw, [&](int w) {
-            const WinDesc &d = desc[w];
-            std::vector<int32_t> &pos = bcnt_w[w];
-            for (int32_t o = d.obs0; o < d.obs0 + d.n;) {
-                int32_t e = o;
-                while (e < d.obs0 + d.n && pm_pc[e].x == pm_pc[o].x) ++e;
-                for (int32_t u = o; u < e; ++u)
-                    for (int32_t v = o; v < e; ++v) {
-                        const int32_t cu = pm_pc[u].y - d.cam0, cv = pm_pc[v].y - d.cam0;
-                        if (cu > cv) continue;
-                        pairs[(size_t)(base_w[w] + pos[cu * d.nc - (cu * (cu - 1)) / 2 + (cv - cu)]++)] =
-                            make_int4(pm2cm[u], pm2cm[v], pm_pc[u].x, 0);
-                    }
-                o = e;
-            }
-        });
+    const bool blocks_ok = nblk < (int64_t(1) << 30);  // else no explicit form (int32 block keys)
+    for (int w = 0; w <= nw; ++w) {
+        off32[w] = (int32_t)obs_offsets[w];
+        off32[nw + 1 + w] = (int32_t)cam_offsets[w];
+        off32[2 * (nw + 1) + w] = (int32_t)pt_offsets[w];
     }
     std::vector<int32_t> order((size_t)nw);
     for (int w = 0; w < nw; ++w) order[w] = w;
@@ -2095,12 +2065,15 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     b->nc = NC;
     b->np = NP;
     b->n = N;
-    b->nch = (int64_t)wchunk.size();
+    b->nch = NP + nw;  // bound: every chunk holds a point, plus one end entry per window
     b->fp32 = o.precision == MBA_FP32_MIXED;
     b->loss = o.loss;
     b->delta = o.huber_delta;
-    b->explicit_ok = explicit_ok;
+    void *tmp = nullptr, *tmp2 = nullptr;
     auto fail_free = [&](mba_status st, const std::string &msg) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        if (tmp) cudaFree(tmp);
+        if (tmp2) cudaFree(tmp2);
         mba_batch_destroy(b);
         return api_fail(st, msg.c_str());
     };
@@ -2116,7 +2089,8 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     if (b->sms < 1) return fail_free(MBA_ERR_CUDA, "no CUDA device");
     const size_t w = b->fp32 ? 4 : 8;
-    // one pool for everything
+    // one pool for the batch's lifetime (the explicit form's arrays come in a
+    // second one, once the pair count is known)
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o_ = off;
@@ -2135,18 +2109,26 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
                  o_cmx = take(4 * w * (size_t)N), o_cms = take(2 * w * (size_t)N),
                  o_W = o.loss != MBA_LOSS_NONE ? take(w * (size_t)N) : 0, o_gc = take(72 * (size_t)NC),
                  o_gp = take(24 * (size_t)NP), o_go = take(16 * (size_t)N), o_g0c = take(72 * (size_t)NC),
-                 o_g0p = take(24 * (size_t)NP);
-    const int64_t smax = (int64_t)ncmax * (ncmax + 1) / 2 * 81;
-    const size_t o_pairs = explicit_ok ? take(sizeof(int4) * pairs.size()) : 0,
-                 o_bptr = explicit_ok ? take(4 * blk_ptr.size()) : 0,
-                 o_jcm = explicit_ok ? take(24 * w * (size_t)N) : 0,
-                 o_S = explicit_ok ? take(w * (size_t)smax * (size_t)b->sms * kMaxCtasPerSm) : 0;
-    if (over_memory_limit(off)) return fail_free(MBA_ERR_OOM, "device memory limit: the batch needs more");
-    if (cudaMalloc(&b->pool, off) != cudaSuccess) {
+                 o_g0p = take(24 * (size_t)NP), o_bptr = take(blocks_ok ? 4 * ((size_t)nblk + 1) : 0);
+    const size_t pool_bytes = off;
+    // layout scratch, freed before the call returns
+    off = 0;
+    const int64_t nkey = NP > NC ? NP : NC;
+    const int64_t scan_n = (NP + 1) > (int64_t)(nw + 1) ? (NP + 1) : (int64_t)(nw + 1);
+    const size_t t_obs = take(16 * (size_t)N), t_ci = take(4 * (size_t)N), t_pi = take(4 * (size_t)N),
+                 t_off = take(4 * off32.size()), t_gpt = take(4 * (size_t)N), t_gcam = take(4 * (size_t)N),
+                 t_ppm = take(4 * (size_t)N), t_pcm = take(4 * (size_t)N), t_inv = take(4 * (size_t)N),
+                 t_ptptr = take(4 * ((size_t)NP + 1)), t_flags = take(256), t_ccnt = take(4 * ((size_t)nw + 1)),
+                 t_pcnt = take(4 * ((size_t)NP + 1)), t_scan = take(4 * (size_t)exclusive_scan_tmp_ints(scan_n)),
+                 t_sort = take(stable_sort_tmp_bytes(N, (int32_t)nkey));
+    const size_t tmp_bytes = off;
+    if (over_memory_limit(pool_bytes + tmp_bytes))
+        return fail_free(MBA_ERR_OOM, "device memory limit: the batch needs more");
+    if (cudaMalloc(&b->pool, pool_bytes) != cudaSuccess || cudaMalloc(&tmp, tmp_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail_free(MBA_ERR_OOM, "device allocation of the batch failed");
     }
-    char *base = (char *)b->pool;
+    char *base = (char *)b->pool, *tb = (char *)tmp;
     b->desc = (WinDesc *)(base + o_desc);
     b->order = (int32_t *)(base + o_order);
     b->counter = (int32_t *)(base + o_counter);
@@ -2192,37 +2174,125 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
     A.grad_c0 = (double *)(base + o_g0c);
     A.grad_p0 = (double *)(base + o_g0p);
     A.out = b->out;
-    if (explicit_ok) {
-        A.pairs = (const int4 *)(base + o_pairs);
-        A.blk_ptr = (const int32_t *)(base + o_bptr);
-        A.Jcm = base + o_jcm;
-        A.S = base + o_S;
-        A.smax = smax;
-    }
+    A.blk_ptr = (const int32_t *)(base + o_bptr);
+    double *d_obs = (double *)(tb + t_obs);
+    int32_t *d_ci = (int32_t *)(tb + t_ci), *d_pi = (int32_t *)(tb + t_pi), *d_off = (int32_t *)(tb + t_off),
+            *gpt = (int32_t *)(tb + t_gpt), *gcam = (int32_t *)(tb + t_gcam), *perm_pm = (int32_t *)(tb + t_ppm),
+            *perm_cm = (int32_t *)(tb + t_pcm), *inv = (int32_t *)(tb + t_inv), *pt_ptr = (int32_t *)(tb + t_ptptr),
+            *flags = (int32_t *)(tb + t_flags), *ccnt = (int32_t *)(tb + t_ccnt), *pcnt = (int32_t *)(tb + t_pcnt),
+            *scan_tmp = (int32_t *)(tb + t_scan);
+    void *sort_tmp = tb + t_sort;
+    const size_t sort_bytes = stable_sort_tmp_bytes(N, (int32_t)nkey);
     cudaStream_t s = b->stream;
     auto up = [&](void *dst, const void *src, size_t bytes) { return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s); };
     cudaError_t e = cudaSuccess;
+    // inputs, as given
     if (e == cudaSuccess) e = up(b->desc, desc.data(), sizeof(WinDesc) * nw);
     if (e == cudaSuccess) e = up(b->order, order.data(), 4 * (size_t)nw);
-    if (e == cudaSuccess) e = up((void *)A.wchunk, wchunk.data(), sizeof(int2) * wchunk.size());
-    if (e == cudaSuccess) e = up((void *)A.pm_pc, pm_pc.data(), sizeof(int2) * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.pm_uv, pm_uv.data(), sizeof(double2) * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.pm_orig, pm_orig.data(), 4 * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.cm_pt, cm_pt.data(), 4 * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.cm2pm, cm2pm.data(), 4 * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.pm2cm, pm2cm.data(), 4 * (size_t)N);
-    if (e == cudaSuccess) e = up((void *)A.cam_ptr, cam_ptr.data(), 4 * ((size_t)NC + 1));
-    if (e == cudaSuccess && explicit_ok) e = up((void *)A.pairs, pairs.data(), sizeof(int4) * pairs.size());
-    if (e == cudaSuccess && explicit_ok) e = up((void *)A.blk_ptr, blk_ptr.data(), 4 * blk_ptr.size());
+    if (e == cudaSuccess) e = up(d_off, off32.data(), 4 * off32.size());
+    if (e == cudaSuccess) e = up(d_obs, observations, 16 * (size_t)N);
+    if (e == cudaSuccess) e = up(d_ci, cam_idx, 4 * (size_t)N);
+    if (e == cudaSuccess) e = up(d_pi, pt_idx, 4 * (size_t)N);
     if (e == cudaSuccess) e = up(A.cams, cameras, 72 * (size_t)NC);
-    if (e == cudaSuccess) e = up(b->cams0, cameras, 72 * (size_t)NC);
     if (e == cudaSuccess) e = up(A.pts, points, 24 * (size_t)NP);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 256, s);
+    if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    const int32_t *oo32 = d_off, *co32 = d_off + (nw + 1), *po32 = d_off + 2 * (nw + 1);
+    // global indices, validation, the two stable orders and the copies in them
+    lay_globalize_kernel<<<lay_grid(N), kLayBlock, 0, s>>>(N, nw, oo32, co32, po32, d_ci, d_pi, d_obs, gpt, gcam, flags);
+    lay_finite_kernel<<<lay_grid(9 * NC), kLayBlock, 0, s>>>(A.cams, 9 * NC, flags);
+    lay_finite_kernel<<<lay_grid(3 * NP), kLayBlock, 0, s>>>(A.pts, 3 * NP, flags);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = stable_sort_by_key(gpt, N, (int32_t)NP, perm_pm, pt_ptr, sort_tmp, sort_bytes, s);
+    if (e == cudaSuccess)
+        e = stable_sort_by_key(gcam, N, (int32_t)NC, perm_cm, (int32_t *)A.cam_ptr, sort_tmp, sort_bytes, s);
+    if (e == cudaSuccess) {
+        lay_gather_pm_kernel<<<lay_grid(N), kLayBlock, 0, s>>>(N, perm_pm, gpt, gcam, d_obs, (int2 *)A.pm_pc,
+                                                               (double2 *)A.pm_uv, (int32_t *)A.pm_orig, inv);
+        lay_gather_cm_kernel<<<lay_grid(N), kLayBlock, 0, s>>>(N, perm_cm, gpt, inv, (int32_t *)A.cm_pt,
+                                                               (int32_t *)A.cm2pm, (int32_t *)A.pm2cm);
+        lay_empty_kernel<<<lay_grid(NP), kLayBlock, 0, s>>>(pt_ptr, NP, 4, flags);
+        lay_empty_kernel<<<lay_grid(NC), kLayBlock, 0, s>>>(A.cam_ptr, NC, 8, flags);
+        // warp chunks: count per window, scan, fill (also the descriptors' wch0 / nwch)
+        lay_chunks_kernel<<<(nw + 127) / 128, 128, 0, s>>>(nw, b->desc, pt_ptr, ccnt, nullptr, nullptr, false);
+        e = cudaMemsetAsync(ccnt + nw, 0, 4, s);
+    }
+    if (e == cudaSuccess) e = exclusive_scan_i32(ccnt, ccnt, nw + 1, scan_tmp, s);
+    if (e == cudaSuccess) {
+        lay_chunks_kernel<<<(nw + 127) / 128, 128, 0, s>>>(nw, b->desc, pt_ptr, nullptr, ccnt, (int2 *)A.wchunk, true);
+        // Schur-block pair counts per point, and their prefix (the total last)
+        lay_pairs_kernel<<<lay_grid(NP), kLayBlock, 0, s>>>(NP, nw, po32, b->desc, pt_ptr, A.pm_pc, A.pm2cm, pcnt,
+                                                            (unsigned long long *)(flags + 2), nullptr, nullptr,
+                                                            nullptr, false);
+        e = cudaMemsetAsync(pcnt + NP, 0, 4, s);
+    }
+    if (e == cudaSuccess) e = exclusive_scan_i32(pcnt, pcnt, NP + 1, scan_tmp, s);
+    int32_t hflags = 0;
+    unsigned long long total_pairs = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total_pairs, flags + 2, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("layout: ") + cudaGetErrorString(e));
+    if (hflags & 2) return fail_free(MBA_ERR_NONFINITE, "non-finite camera, point or observation");
+    if (hflags & 1) return fail_free(MBA_ERR_INVALID_ARG, "observation index out of its window's range");
+    if (hflags & 4) return fail_free(MBA_ERR_INVALID_ARG, "a point without observations");
+    if (hflags & 8) return fail_free(MBA_ERR_INVALID_ARG, "a camera without observations");
+    // Schur-block pair lists in point order inside each block: generated in
+    // point order with their block keys, then stably sorted by block (the sort
+    // also yields the blocks' offsets).  Skipped, and the explicit form not
+    // offered, when they would be too large.
+    const bool explicit_ok = blocks_ok && total_pairs <= (1ull << 28);
+    b->explicit_ok = explicit_ok;
+    if (explicit_ok) {
+        const int64_t smax = (int64_t)ncmax * (ncmax + 1) / 2 * 81;
+        const int64_t np2 = (int64_t)total_pairs;
+        off = 0;
+        const size_t o_pairs = take(sizeof(int4) * (size_t)np2), o_jcm = take(24 * w * (size_t)N),
+                     o_S = take(w * (size_t)smax * (size_t)b->sms * kMaxCtasPerSm);
+        const size_t pool2_bytes = off;
+        off = 0;
+        const size_t u_pairs = take(sizeof(int4) * (size_t)np2), u_keys = take(4 * (size_t)np2),
+                     u_perm = take(4 * (size_t)np2), u_sort = take(stable_sort_tmp_bytes(np2, (int32_t)nblk));
+        const size_t tmp2_bytes = off;
+        if (over_memory_limit(pool_bytes + tmp_bytes + pool2_bytes + tmp2_bytes))
+            return fail_free(MBA_ERR_OOM, "device memory limit: the batch needs more");
+        if (cudaMalloc(&b->pool2, pool2_bytes) != cudaSuccess || cudaMalloc(&tmp2, tmp2_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_free(MBA_ERR_OOM, "device allocation of the batch failed");
+        }
+        char *b2 = (char *)b->pool2, *t2 = (char *)tmp2;
+        A.pairs = (const int4 *)(b2 + o_pairs);
+        A.Jcm = b2 + o_jcm;
+        A.S = b2 + o_S;
+        A.smax = smax;
+        int4 *gen = (int4 *)(t2 + u_pairs);
+        int32_t *keys = (int32_t *)(t2 + u_keys), *perm = (int32_t *)(t2 + u_perm);
+        if (np2 > 0) {
+            lay_pairs_kernel<<<lay_grid(NP), kLayBlock, 0, s>>>(NP, nw, po32, b->desc, pt_ptr, A.pm_pc, A.pm2cm,
+                                                                nullptr, nullptr, pcnt, gen, keys, true);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = stable_sort_by_key(keys, np2, (int32_t)nblk, perm, (int32_t *)A.blk_ptr, t2 + u_sort,
+                                       stable_sort_tmp_bytes(np2, (int32_t)nblk), s);
+            if (e == cudaSuccess) {
+                lay_gather_pairs_kernel<<<lay_grid(np2), kLayBlock, 0, s>>>(np2, perm, gen, (int4 *)A.pairs);
+                e = cudaGetLastError();
+            }
+        } else {
+            e = cudaMemsetAsync((void *)A.blk_ptr, 0, 4 * ((size_t)nblk + 1), s);
+        }
+    }
+    if (e == cudaSuccess) e = up(b->cams0, cameras, 72 * (size_t)NC);
     if (e == cudaSuccess) e = up(b->pts0, points, 24 * (size_t)NP);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_obs, 0, 16 * (size_t)N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_c0, 0, 72 * (size_t)NC, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.grad_p0, 0, 24 * (size_t)NP, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail_free(MBA_ERR_CUDA, std::string("layout: ") + cudaGetErrorString(e));
+    cudaFree(tmp);
+    tmp = nullptr;
+    if (tmp2) cudaFree(tmp2);
+    tmp2 = nullptr;
     mba_status st = resolve_schedule(b, 0, 0, 0, &b->nt, &b->cps, &b->schur);
     if (st != MBA_OK) {
         std::string msg = mba_last_error();
@@ -2238,6 +2308,7 @@ void mba_batch_destroy(mba_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->pool) cudaFree(b->pool);
+    if (b->pool2) cudaFree(b->pool2);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

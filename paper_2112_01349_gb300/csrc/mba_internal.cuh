@@ -492,6 +492,8 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t &epoch, long
 cudaError_t stable_sort_by_key(const int32_t *keys_in, int64_t n, int32_t nkeys, int32_t *perm_out,
                                int32_t *ptr_out, void *tmp, size_t tmp_bytes, cudaStream_t s);
 size_t stable_sort_tmp_bytes(int64_t n, int32_t nkeys);
+int64_t exclusive_scan_tmp_ints(int64_t n);
+cudaError_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
 cudaError_t validate_inputs(const double *cams, int32_t nc, const double *pts, int32_t np, const double *obs,
                             const int32_t *ci, const int32_t *pi, int64_t n, int32_t *flags, cudaStream_t s);
 cudaError_t gather_layout(Prob &P, const double *obs_in, const int32_t *ci, const int32_t *pi, int32_t *max_track,

@@ -198,6 +198,13 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 }  // namespace
 
+// exclusive scan of n int32 for other files (in place allowed); tmp holds
+// exclusive_scan_tmp_ints(n) ints
+int64_t exclusive_scan_tmp_ints(int64_t n) { return (n + kTile - 1) / kTile + 1; }
+cudaError_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s) {
+    return exclusive_scan(in, out, n, tmp, s);
+}
+
 // ints of scan scratch for the larger of the two scans a sort performs
 int64_t scan_tmp_count(int64_t n, int32_t nkeys) {
     const int64_t ntiles = (n + kTile - 1) / kTile;

@@ -184,6 +184,44 @@ def test_invalid_batches(mba):
     with pytest.raises(mba.MbaError) as e:
         mba.Batch([(s.cameras, s.points, nan_obs, s.cam_idx, s.pt_idx)])
     assert e.value.status == mba.MBA_ERR_NONFINITE
+    nan_cam = s.cameras.copy()
+    nan_cam[1, 4] = np.inf
+    with pytest.raises(mba.MbaError) as e:
+        mba.Batch([t, (nan_cam, s.points, s.observations, s.cam_idx, s.pt_idx)])
+    assert e.value.status == mba.MBA_ERR_NONFINITE
+    bad_pt = s.pt_idx.copy()
+    bad_pt[7] = -1
+    with pytest.raises(mba.MbaError) as e:
+        mba.Batch([t, (s.cameras, s.points, s.observations, s.cam_idx, bad_pt)])
+    assert e.value.status == mba.MBA_ERR_INVALID_ARG
+    keep_pt = s.pt_idx != 5
+    with pytest.raises(mba.MbaError) as e:  # point 5 loses all of its observations
+        mba.Batch([(s.cameras, s.points, s.observations[keep_pt], s.cam_idx[keep_pt], s.pt_idx[keep_pt]), t])
+    assert e.value.status == mba.MBA_ERR_INVALID_ARG
+    # a valid batch after the failures
+    with mba.Batch([t, t]) as b:
+        r = b.solve(max_iter=2, pcg_max_iter=20)
+    assert r["summaries"][0]["final_cost"] == r["summaries"][1]["final_cost"]
+
+
+def test_device_layout_repeats_bit_for_bit(mba):
+    """The batch's layout (orders, warp chunks, Schur pair lists) is built on the
+    device with stable sorts: two creations of the same batch give the same
+    bits, and a window's result does not depend on the windows around it."""
+    ws = _small(count=10, seed=81)
+    runs = []
+    for _ in range(2):
+        with mba.Batch(_tuples(ws), precision="fp32") as b:
+            b.set_schedule(256, 2, "explicit")
+            r = b.solve(**OPTS)
+            runs.append(([x["final_cost"] for x in r["summaries"]], b.parameters()))
+    assert runs[0][0] == runs[1][0]
+    np.testing.assert_array_equal(runs[0][1][0], runs[1][1][0])
+    np.testing.assert_array_equal(runs[0][1][1], runs[1][1][1])
+    with mba.Batch(_tuples(ws[3:6]), precision="fp32") as b:
+        b.set_schedule(256, 2, "explicit")
+        r = b.solve(**OPTS)
+    assert [x["final_cost"] for x in r["summaries"]] == runs[0][0][3:6]
 
 
 def test_full_batch_sampled_windows(mba):
