@@ -717,6 +717,16 @@ def main():
                      "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"],
                      "pcg_iters_per_solve": a32["pcg_iters"] / max(1, len(s32)),
                      "other_kernels": {
+                         "pcg_single_reduction_fp32": None if not variants else {
+                             "kernel": "pcg_kernel, single-reduction (Chronopoulos-Gear) instance",
+                             "bound": "hbm", "unit": "GB/s",
+                             "us_per_pcg_iter": variants["single_reduction_pcg"]["us_per_pcg_iter"],
+                             "achieved": pcg_bytes_per_iter(sc, 4) / (variants["single_reduction_pcg"]["us_per_pcg_iter"]
+                                                                      / 1e6) / 1e9,
+                             "frac": pcg_bytes_per_iter(sc, 4) / (variants["single_reduction_pcg"]["us_per_pcg_iter"]
+                                                                  / 1e6) / 1e9 / hbm_peak,
+                             "note": "same algorithmic bytes per PCG iteration as the headline kernel; one global "
+                                     "reduction per PCG step instead of two (solver option, not the headline)"},
                          "linearize_fp32": {"kernel": "lin_point + lin_camera + cam_finalize (+ camera table)",
                                             "bound": "hbm", "achieved": a32["lin_gbs"], "unit": "GB/s",
                                             "frac": a32["lin_gbs"] / hbm_peak,
