@@ -130,6 +130,7 @@ def load():
             "mba_batch_set_parameters": (C.c_int, [P, P, P]),
             "mba_batch_reset": (C.c_int, [P]),
             "mba_batch_get_gradients": (C.c_int, [P, P, P, P]),
+            "mba_batch_window_times": (C.c_int, [P, P]),
             "mba_bal_read": (C.c_int, [C.c_char_p, P, P, P, P, P, P, P, P]),
             "mba_bal_write": (C.c_int, [C.c_char_p, i32, i32, i64, P, P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
@@ -563,6 +564,13 @@ def mba_batch_get_gradients(h):
     return dict(grad_obs=go, grad_init_cam=gc, grad_init_pt=gp)
 
 
+def mba_batch_window_times(h):
+    """Milliseconds each window took in the last solve (input order)."""
+    ms = np.zeros(mba_batch_info(h)["n_windows"])
+    _check(load().mba_batch_window_times(h, _vp(ms)))
+    return ms
+
+
 _COMPRESSED = {".bz2": "bz2", ".gz": "gzip", ".xz": "lzma"}
 
 
@@ -769,3 +777,6 @@ class Batch:
 
     def gradients(self):
         return mba_batch_get_gradients(self.handle)
+
+    def window_times(self):
+        return mba_batch_window_times(self.handle)

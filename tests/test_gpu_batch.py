@@ -299,3 +299,22 @@ def test_batch_single_reduction_pcg_matches_oracle(mba, precision, tol, schur):
                              gp[po[w]:po[w + 1]], pcg_max=1000, pcg_tol=1e-14, pcg_variant="single_reduction")
         rel_close(g["grad_obs"][oo[w]:oo[w + 1]], adj["grad_obs"], 1e-6 if precision == "fp64" else 3e-3,
                   f"window {w} observation gradient")
+
+
+def test_measured_order_changes_no_result(mba):
+    """After a solve the next launch claims windows longest-first by their
+    measured times; the results repeat bit for bit in the new order."""
+    ws = _small(count=12, seed=83)
+    with mba.Batch(_tuples(ws), precision="fp32") as b:
+        with pytest.raises(mba.MbaError):
+            b.window_times()
+        r1 = b.solve(**OPTS)
+        p1 = b.parameters()
+        t1 = b.window_times()
+        b.reset()
+        r2 = b.solve(**OPTS)
+        p2 = b.parameters()
+    assert t1.shape == (12,) and np.all(t1 > 0)
+    assert [x["final_cost"] for x in r1["summaries"]] == [x["final_cost"] for x in r2["summaries"]]
+    np.testing.assert_array_equal(p1[0], p2[0])
+    np.testing.assert_array_equal(p1[1], p2[1])
