@@ -2465,6 +2465,15 @@ mba_status mba_batch_autotune(mba_batch *b, const mba_solver_options *opt, mba_b
     const int nt0 = b->nt, cps0 = b->cps, sc0 = b->schur;
     double best = -1.0;
     int bnt = nt0, bcps = cps0, bsc = sc0;
+    // one untimed solve first, so that every timed schedule claims the windows in
+    // the order of measured times (and none pays the first launch's set-up)
+    {
+        mba_status st = mba_batch_solve(b, opt, nullptr, nullptr, nullptr);
+        BCK(cudaMemcpyAsync(b->A.cams, b->cams_bak, 72 * (size_t)b->nc, cudaMemcpyDeviceToDevice, s));
+        BCK(cudaMemcpyAsync(b->A.pts, b->pts_bak, 24 * (size_t)b->np, cudaMemcpyDeviceToDevice, s));
+        BCK(cudaStreamSynchronize(s));
+        if (st != MBA_OK && st != MBA_ERR_NONFINITE) return st;
+    }
     const int nts[2] = {256, 512};
     for (int sch = b->explicit_ok ? 2 : 1; sch >= 1; --sch)
     for (int a = 0; a < 2; ++a) {
