@@ -423,6 +423,11 @@ mba_status mba_batch_get_gradients(const mba_batch *batch, double *grad_obs, dou
 mba_status mba_batch_window_times(const mba_batch *batch, double *ms);
 
 const char *mba_status_string(mba_status status);
+/* Name of the edge type the library's dual-number path evaluates: "BalEdge" (the
+ * BAL camera of Sec. 6, Eq. 1's residual), or the user type given at build time
+ * (a g2o / Ceres-style user edge, Sec. 5.3).  A library built with a user edge
+ * accepts MBA_JACOBIAN_AUTODIFF problems only and no batches. */
+const char *mba_edge_name(void);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mba_last_error(void);
 

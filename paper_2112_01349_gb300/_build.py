@@ -42,16 +42,36 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libmba.so if any source changed; return its path."""
-    if not force and not _stale():
+def edge_lib(edge_type: str) -> str:
+    """Path of the library built with the user edge type edge_type."""
+    return os.path.join(BUILD, "edge_" + edge_type, "libmba.so")
+
+
+def build(force: bool = False, verbose: bool = False, edge: tuple[str, str] | None = None) -> str:
+    """Compile and link libmba.so if any source changed; return its path.
+
+    edge = (header path, type name): a library whose dual-number path evaluates
+    that user edge type instead of the BAL edge (see csrc/edge_bal.cuh), built
+    into its own folder (edge_lib(type name)); the default library is untouched.
+    """
+    out_dir, lib, defs = BUILD, LIB, []
+    if edge is not None:
+        header, name = os.path.abspath(edge[0]), edge[1]
+        if not name.replace("_", "").replace(":", "").isalnum():
+            raise ValueError("edge type must be a C++ identifier")
+        out_dir, lib = os.path.dirname(edge_lib(name)), edge_lib(name)
+        defs = [f'-DMBA_EDGE_HEADER="{header}"', f"-DMBA_EDGE_TYPE={name}"]
+        if not force and os.path.exists(lib) and not _stale() and os.path.getmtime(lib) >= max(
+                os.path.getmtime(header), os.path.getmtime(LIB)):
+            return lib
+    elif not force and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -61,12 +81,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def declared_functions() -> list[str]:

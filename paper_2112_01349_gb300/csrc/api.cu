@@ -105,6 +105,8 @@ void mba_solver_options_default(mba_solver_options *o) {
     o->pcg_variant = MBA_PCG_STANDARD;
 }
 
+const char *mba_edge_name(void) { return kUserEdge ? MBA_STR(MBA_EDGE_TYPE) : "BalEdge"; }
+
 const char *mba_status_string(mba_status s) {
     switch (s) {
         case MBA_OK: return "MBA_OK";
@@ -150,6 +152,8 @@ mba_status mba_problem_create(const double *cameras, int32_t nc, const double *p
     if (o.loss == MBA_LOSS_HUBER && !(o.huber_delta > 0.0)) return fail(MBA_ERR_INVALID_ARG, "huber_delta must be > 0");
     if (o.jacobian != MBA_JACOBIAN_ANALYTIC && o.jacobian != MBA_JACOBIAN_AUTODIFF)
         return fail(MBA_ERR_INVALID_ARG, "bad jacobian source");
+    if (kUserEdge && o.jacobian != MBA_JACOBIAN_AUTODIFF)
+        return fail(MBA_ERR_INVALID_ARG, "this library evaluates a user edge type: use MBA_JACOBIAN_AUTODIFF");
 
     mba_problem *pr = new mba_problem();
     Prob &P = pr->P;

@@ -2025,6 +2025,7 @@ mba_status mba_batch_create(int32_t n_windows, const int64_t *cam_offsets, const
         return api_fail(MBA_ERR_INVALID_ARG, "huber_delta must be > 0");
     if (o.jacobian != MBA_JACOBIAN_ANALYTIC)
         return api_fail(MBA_ERR_INVALID_ARG, "batched windows use the analytic Jacobian only");
+    if (kUserEdge) return api_fail(MBA_ERR_INVALID_ARG, "batched windows use the BAL edge; this library has a user edge");
     const int nw = n_windows;
     if (cam_offsets[0] != 0 || pt_offsets[0] != 0 || obs_offsets[0] != 0)
         return api_fail(MBA_ERR_INVALID_ARG, "offset arrays must start at 0");

@@ -62,3 +62,31 @@ struct BalEdge {
 };
 
 }  // namespace mba
+
+// A user edge type replaces BalEdge in every dual-number path when the library
+// is compiled with -DMBA_EDGE_HEADER="path/to/edge.cuh" -DMBA_EDGE_TYPE=Name
+// (_build.build(edge=(path, Name))): the graph's edges are then the user's
+// functor, with the same interface as BalEdge (a 9-parameter camera block, a
+// 3-parameter point block, a 2-vector prediction subtracted from the
+// observation, and a templated operator() that also runs on mba::Jet).  The
+// analytic kernels (the "-m" form, the factored FP32 product, batched windows
+// and the allocation-free cost) are the BAL camera's own derivation, so such a
+// library accepts MBA_JACOBIAN_AUTODIFF problems only.
+#ifdef MBA_EDGE_HEADER
+#include MBA_EDGE_HEADER
+#endif
+#ifndef MBA_EDGE_TYPE
+#define MBA_EDGE_TYPE ::mba::BalEdge
+#define MBA_USER_EDGE 0
+#else
+#define MBA_USER_EDGE 1
+#endif
+#define MBA_STR2(x) #x
+#define MBA_STR(x) MBA_STR2(x)
+
+namespace mba {
+using Edge = MBA_EDGE_TYPE;
+static_assert(Edge::kCam == 9 && Edge::kPt == 3 && Edge::kOut == 2,
+              "an edge type has a 9-parameter camera, a 3-parameter point and a 2-vector residual");
+constexpr bool kUserEdge = MBA_USER_EDGE != 0;
+}  // namespace mba

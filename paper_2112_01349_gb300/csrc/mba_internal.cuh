@@ -352,7 +352,7 @@ __device__ __forceinline__ void edge_eval(const T *__restrict__ ct, T X0, T X1, 
     const T cam[9] = {ct[25], ct[26], ct[27], ct[18], ct[19], ct[20], ct[21], ct[22], ct[23]};
     const T X[3] = {X0, X1, X2};
     T pix[2];
-    jet_jacobian<(CAM && PT) ? kJetK : (CAM ? 9 : 3), CAM, PT>(BalEdge{}, cam, X, pix, Jc, Jp);
+    jet_jacobian<(CAM && PT) ? kJetK : (CAM ? 9 : 3), CAM, PT>(Edge{}, cam, X, pix, Jc, Jp);
     e[0] = pix[0] - u0;
     e[1] = pix[1] - u1;
 }
@@ -366,7 +366,7 @@ __device__ __forceinline__ void edge_residual(const T *__restrict__ ct, T X0, T 
     const T cam[9] = {ct[25], ct[26], ct[27], ct[18], ct[19], ct[20], ct[21], ct[22], ct[23]};
     const T X[3] = {X0, X1, X2};
     T pix[2];
-    BalEdge{}(cam, X, pix);
+    Edge{}(cam, X, pix);
     e[0] = pix[0] - u0;
     e[1] = pix[1] - u1;
 }

@@ -90,6 +90,7 @@ extern "C" mba_status mba_cost_noalloc(const double *d_cameras, int32_t nc, cons
                                        double *d_cost, void *cuda_stream) {
     if (!d_cameras || !d_points || !d_observations || !d_cam_idx || !d_pt_idx || !d_cost) return MBA_ERR_INVALID_ARG;
     if (nc < 1 || np < 1 || n < 1) return MBA_ERR_INVALID_ARG;
+    if (kUserEdge) return MBA_ERR_INVALID_ARG;  // the BAL camera's cost only
     if (nc > kNaMaxCameras) return MBA_ERR_INVALID_ARG;  // beyond the fixed scratch
     if (loss != MBA_LOSS_NONE && loss != MBA_LOSS_HUBER) return MBA_ERR_INVALID_ARG;
     if (loss == MBA_LOSS_HUBER && !(huber_delta > 0.0)) return MBA_ERR_INVALID_ARG;

@@ -88,19 +88,28 @@ _lock = threading.Lock()
 _lib = None
 
 
+_lib_path = None
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _lib_path or _build.LIB
 
 
-def load():
-    """Load libmba.so (built in-tree by __graft_entry__.build())."""
-    global _lib
+def load(path: str | None = None):
+    """Load libmba.so (built in-tree by __graft_entry__.build()), or the
+    library at path (a build with a user edge type, _build.build(edge=...)),
+    once per process."""
+    global _lib, _lib_path
     with _lock:
         if _lib is not None:
+            if path is not None and os.path.abspath(path) != os.path.abspath(library_path()):
+                raise RuntimeError(f"{library_path()} is already loaded in this process")
             return _lib
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first (__graft_entry__.build())")
-        lib = C.CDLL(_build.LIB)
+        target = path or _build.LIB
+        if not os.path.exists(target):
+            raise RuntimeError(f"{target} is missing: build the CUDA library first (__graft_entry__.build())")
+        lib = C.CDLL(target)
+        _lib_path = target
         P, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
         sig = {
             "mba_problem_options_default": (None, [P]),
@@ -134,6 +143,7 @@ def load():
             "mba_bal_read": (C.c_int, [C.c_char_p, P, P, P, P, P, P, P, P]),
             "mba_bal_write": (C.c_int, [C.c_char_p, i32, i32, i64, P, P, P, P, P]),
             "mba_status_string": (C.c_char_p, [C.c_int]),
+            "mba_edge_name": (C.c_char_p, []),
             "mba_last_error": (C.c_char_p, []),
             "mba_set_device_memory_limit": (C.c_int, [C.c_size_t]),
             "mba_set_fixed": (C.c_int, [P, P, P]),
@@ -562,6 +572,11 @@ def mba_batch_get_gradients(h):
     go, gc, gp = np.zeros((info["n"], 2)), np.zeros((info["nc"], 9)), np.zeros((info["np"], 3))
     _check(load().mba_batch_get_gradients(h, _vp(go), _vp(gc), _vp(gp)))
     return dict(grad_obs=go, grad_init_cam=gc, grad_init_pt=gp)
+
+
+def mba_edge_name() -> str:
+    """The edge type of the loaded library's dual-number path ("BalEdge" or a user type)."""
+    return load().mba_edge_name().decode()
 
 
 def mba_batch_window_times(h):
