@@ -396,9 +396,18 @@ __device__ void point_pass(const Prob &P, const T *ps, const T *pT, typename V2<
                     gather_p(ps, pT, cam, pa);
                     et_p(Jc, Jp, pa, u);
                 }
-                // inclusive segmented scan keyed by point (segments are contiguous)
+                // inclusive segmented scan keyed by point (segments are contiguous).
+                // FP64: only as many levels as the chunk's longest point needs
+                // (each level is three warp-wide FP64 adds on the FP64 pipe)
+                int span = 32;
+                if constexpr (sizeof(T) == 8) {
+                    const int nrs = __shfl_down_sync(full, rs, 1);
+                    const int len = lane < npts ? (lane + 1 < npts ? nrs : m) - rs : 0;
+                    span = __reduce_max_sync(full, len);
+                }
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
+                    if (d >= span) break;
                     const int kp = __shfl_up_sync(full, pt, d);
                     const T v0 = __shfl_up_sync(full, u[0], d), v1 = __shfl_up_sync(full, u[1], d),
                             v2 = __shfl_up_sync(full, u[2], d);
