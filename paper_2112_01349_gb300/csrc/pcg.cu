@@ -1697,6 +1697,10 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
                     const int cam = c0 + my_sub;
                     const bool act = lane < 27 && cam < ce;
                     const int64_t vo = (int64_t)(act ? cam : c0) * kVec + row;
+                    // this lane's row of B~^-1, loaded beside (not after) the r update
+                    double bi[9];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) bi[c] = act ? __ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c) : 0.0;
                     double rv = 0.0;
                     if (act) {
                         stcg(P.x + vo, fma(alpha, ldcg(p_cur + vo), ldcg(P.x + vo)));
@@ -1707,7 +1711,7 @@ __global__ void __launch_bounds__(PcgBlock<T>::value, 1)
 #pragma unroll
                     for (int c = 0; c < 9; ++c) {
                         const double rc = __shfl_sync(full, rv, my_sub * 9 + c);
-                        if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cam + row * 9 + c), rc, z);
+                        z = fma(bi[c], rc, z);
                     }
                     if (FACT) fact_row_store(P, (float *)P.zT, act ? cam : c0, act, z, my_sub, row, true);
                     if (act) {
