@@ -1120,6 +1120,16 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
         const int a = act ? row : 0;
         const int cm = act ? cam : c0;
         const int64_t vo = (int64_t)cm * kVec + a;
+        // this lane's row of B~^-1 (right-hand side) or B~ (products): in the
+        // factored form's standard iterations loaded before the chunk sums, so
+        // that its latency overlaps them (109.9 -> 109.3 us per PCG iteration);
+        // elsewhere loaded where it is used (the early load raised the
+        // single-reduction instance's spills and slowed it, and the FP64 one)
+        constexpr bool kEarly = FACT && MODE == CAM_ITER;
+        const double *Mrow = (MODE == CAM_RHS ? P.Binv : P.Bd) + 81 * (int64_t)cm + a * 9;
+        double brow[9];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) brow[b] = (kEarly && act) ? __ldg(Mrow + b) : 0.0;
         double cs = 0.0;
         if (act)
             for (int k = P.cfirst[cm]; k < P.cfirst[cm + 1]; ++k) cs += cslot[(k - k0) * 9 + a];
@@ -1133,7 +1143,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 #pragma unroll
             for (int b = 0; b < 9; ++b) {
                 const double gb = __shfl_sync(full, g, 9 * sub + b);
-                if (act) z = fma(__ldg(P.Binv + 81 * (int64_t)cm + a * 9 + b), gb, z);
+                if (act) z = fma(kEarly ? brow[b] : __ldg(Mrow + b), gb, z);
             }
             if (act) {
                 stcg(P.g + vo, g);
@@ -1156,7 +1166,7 @@ __device__ double2 camera_pass(const Prob &P, const typename V2<T>::type *sbuf, 
 #pragma unroll
             for (int b = 0; b < 9; ++b) {
                 const double pb = __shfl_sync(full, p, 9 * sub + b);
-                if (act) bp = fma(__ldg(P.Bd + 81 * (int64_t)cm + a * 9 + b), pb, bp);
+                if (act) bp = fma(kEarly ? brow[b] : __ldg(Mrow + b), pb, bp);
             }
             const double q = act ? bp - cs : 0.0;
             if (act) {
