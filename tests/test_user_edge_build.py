@@ -47,3 +47,13 @@ def test_user_edge_library_builds_and_reports_its_edge():
     assert _create(user, mba.JACOBIAN["analytic"]) == mba.MBA_ERR_INVALID_ARG
     default = _lib(_build.build())
     assert default.mba_edge_name() == b"BalEdge"
+    # the binding holds one library per process: the default one here, so a
+    # request for the user-edge library is refused rather than mixed in
+    mba.load()
+    assert mba.mba_edge_name() == "BalEdge"
+    try:
+        mba.load(path)
+        raised = False
+    except RuntimeError:
+        raised = True
+    assert raised
