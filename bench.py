@@ -127,8 +127,13 @@ def batch_flops(ws, summaries, schur: str) -> float:
 # iterations plus the right-hand-side pass, 5,004,484 observations), FP32-mixed
 # and FP64.  Traffic grows with the observation count, so a launch moves this
 # many bytes per observation per pass; None once the kernel has changed since
-# the capture.
-PCG_TRAFFIC_B_PER_OBS_PASS = {4: (9407.0e6 + 103.7e6) / 31 / 5004484, 8: (63436.1e6 + 3459.4e6) / 31 / 5004484}
+# the capture.  The last full-size capture gave 61.3 B (FP32-mixed) and 431.1 B
+# (FP64); both kernels have changed since (the FP32 one loads its B~ rows
+# earlier, the FP64 one runs fewer scan levels), so no figure is claimed.
+PCG_TRAFFIC_B_PER_OBS_PASS = {}
+PCG_TRAFFIC_NOTE = ("null: the kernel changed after the last full-size DRAM capture (61.3 B per observation per "
+                    "pass FP32-mixed, 431.1 B FP64); the FP32 change loads the same rows earlier, the FP64 one "
+                    "runs fewer FP64 scan levels; not re-taken")
 
 
 def oracle_sample_time(threads: int, scale: float) -> dict:
@@ -714,6 +719,7 @@ def main():
                                  "iteration, 28 B per point, 1.9 KB per camera",
                      "dram_gbs": a32["dram_gbs"],
                      "dram_frac": None if a32["dram_gbs"] is None else a32["dram_gbs"] / hbm_peak,
+                     "traffic_note": PCG_TRAFFIC_NOTE if a32["traffic_per_launch"] is None else None,
                      "us_per_pcg_iter": a32["us_per_pcg_iter"], "share_of_solve": a32["pcg_share"],
                      "pcg_iters_per_solve": a32["pcg_iters"] / max(1, len(s32)),
                      "other_kernels": {
